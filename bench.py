@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the 3DGS training hot path on one GB300 (per rank).
+
+A step is one whole training iteration (gs_train_step: transformation,
+binning, sort, compositing, L1 + SSIM loss, backward, Adam) over one batch of
+views of a seeded synthetic scene resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c1|c2|c0] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
+path is not sharded, so there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2406_18533_gb300 import synth  # noqa: E402
+
+METRIC = "train views/s batched vs per-view at 1e-4 img err; serve p50/p99 ms"
+UNIT = "views/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+# per-group Adam learning rates (3DGS defaults; the mean's is scaled by the scene extent)
+def lr_groups(extent):
+    return (1.6e-4 * extent, 5e-3, 1e-3, 5e-2, 2.5e-3, 2.5e-4)
+
+
+def make_workload(name):
+    if name == "c0":
+        sc, cams, _ = synth.workload_c0()
+        rng = np.random.default_rng(7)
+        tg = np.stack([synth.blurred_noise_target(rng, cams[0].H, cams[0].W)])
+        return "c0_plain_10k_256", sc, cams, tg, 3.0
+    if name == "c1":
+        sc, cams, tg = synth.workload_c1()
+        return "c1_train_1m_1080p", sc, cams, tg, 71.4
+    if name == "c2":
+        sc, cams, tg = synth.workload_c2()
+        return "c2_batch16_4m_1080p", sc, cams, tg, 71.4
+    raise SystemExit(f"unknown workload {name}")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "50"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.06)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle sample (CPU baseline / reference arm)
+
+class OracleSample:
+    """A bounded sample of the workload for the FP64 CPU oracle: a tile-aligned
+    crop window of each view with exactly the Gaussians whose footprint meets
+    it, stepped through the whole pipeline (transformation, lists,
+    compositing, loss, backward, Adam).  views/s counts the crop as its pixel
+    fraction of a full view."""
+
+    def __init__(self, sc, cams, tg, lr6, crop):
+        import oracle
+        self.o = oracle
+        self.lr6 = lr6
+        cam = cams[0]
+        w, h = crop
+        x0 = ((cam.W - w) // 2) // 16 * 16
+        y0 = ((cam.H - h) // 2) // 16 * 16
+        self.frac = (w * h) / float(cam.W * cam.H)
+        pr = oracle.project(sc, cam)
+        u, v, r = pr["xy"][:, 0], pr["xy"][:, 1], pr["radius"]
+        keep = (r > 0) & (u + r >= x0) & (u - r < x0 + w) & (v + r >= y0) & (v - r < y0 + h)
+        idx = np.nonzero(keep)[0]
+        self.sub = synth.Scene(sc.mo[idx].copy(), sc.ls[idx].copy(), sc.q[idx].copy(), sc.sh[:, idx].copy())
+        self.cam = synth.Camera(R=cam.R, t=cam.t, fx=cam.fx, fy=cam.fy, cx=np.float32(cam.cx - x0),
+                                cy=np.float32(cam.cy - y0), W=w, H=h, near=cam.near)
+        self.tg = tg[0][:, y0:y0 + h, x0:x0 + w].copy()
+        self.crop = (x0, y0, w, h)
+        self.m = np.zeros((len(idx), 60))
+        self.v = np.zeros((len(idx), 60))
+        self.n_gauss = len(idx)
+
+    def step(self, k=1):
+        p, self.m, self.v, losses, _ = self.o.train_step(self.sub, [self.cam], self.tg[None], self.m, self.v, k,
+                                                         self.lr6)
+        return float(losses[0])
+
+    def describe(self):
+        x0, y0, w, h = self.crop
+        return (f"{w}x{h} crop at ({x0},{y0}) of view 0 with the {self.n_gauss} Gaussians whose footprint "
+                f"meets it, full FP64 train step (project, lists, composite, L1+SSIM, backward, Adam); "
+                f"views/s = crop fraction {self.frac:.4f} / step time")
+
+
+def pick_crop(sc, cams, tg, lr6, budget_s):
+    """Tile-aligned crop whose oracle step takes about budget_s seconds."""
+    cam = cams[0]
+    side = 128
+    s = OracleSample(sc, cams, tg, lr6, (min(side, cam.W), min(side, cam.H)))
+    t0 = time.perf_counter()
+    s.step(1)
+    t = time.perf_counter() - t0
+    scale = math.sqrt(max(budget_s, 0.05) / max(t, 1e-3))
+    w = int(min(cam.W, max(32, side * scale)) // 16 * 16)
+    h = int(min(cam.H, max(32, side * scale * cam.H / cam.W * 1.7)) // 16 * 16)
+    return (max(w, 32), max(h, 32))
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    name, sc, cams, tg, extent = make_workload(args.workload)
+    lr6 = lr_groups(extent)
+    budget = 100.0 / max(1, args.steps + args.warmup)
+    crop = pick_crop(sc, cams, tg, lr6, budget)
+    smp = OracleSample(sc, cams, tg, lr6, crop)
+    for k in range(args.warmup):
+        smp.step(k + 1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        smp.step(args.warmup + k + 1)
+    dt = time.perf_counter() - t0
+    views = args.steps * smp.frac
+    value = views / dt
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": smp.describe()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def stage_roofline(stage, ms, counters, N, Bv, pixels, passes, peaks, clock_mhz):
+    """Algorithmic work of one launch of a stage, and the matching peak."""
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    F, Ef, Eb = counters["F"], counters["evals_fwd"], counters["evals_bwd"]
+    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    sec = ms * 1e-3
+    if stage == "blend_bwd":
+        work = 70.0 * Eb
+        return dict(bound="alu", achieved=work / sec / 1e12, peak=alu_peak, unit="TFLOP/s",
+                    work_desc=f"70 FP32 flop x {Eb} backward (pixel, fragment) evaluations")
+    if stage == "blend_fwd":
+        work = 22.0 * Ef
+        return dict(bound="alu", achieved=work / sec / 1e12, peak=alu_peak, unit="TFLOP/s",
+                    work_desc=f"22 FP32 flop x {Ef} forward (pixel, fragment) evaluations")
+    if stage == "sort":
+        byt = passes * F * 24.0
+    elif stage == "adam":
+        byt = 59 * 28.0 * N
+    elif stage == "preprocess":
+        byt = N * 240.0 + Bv * N * 52.0
+    elif stage == "preprocess_bwd":
+        byt = N * 240.0 * 2 + Bv * N * 68.0
+    elif stage == "loss":
+        byt = pixels * 3 * 44.0
+    elif stage == "emit":
+        byt = F * 12.0 + Bv * N * 16.0
+    else:
+        byt = Bv * N * 8.0
+    return dict(bound="hbm", achieved=byt / sec / 1e9, peak=hbm, unit="GB/s", work_desc=f"{byt:.3e} bytes")
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2406_18533_gb300 import binding, engine
+
+    torch.cuda.set_device(local_rank)
+    peaks, peak_kind = load_peaks()
+    name, sc, cams, tg, extent = make_workload(args.workload)
+    lr6 = lr_groups(extent)
+    Bv = len(cams)
+    H, W = cams[0].H, cams[0].W
+    ctx = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch)
+    P = engine.DeviceScene.from_host(sc)
+    G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
+    targets = torch.from_numpy(tg).cuda()
+    loss = torch.empty(Bv, dtype=torch.float32, device="cuda")
+    cam_arr = binding.camera_array(cams)
+    step = 0
+
+    def train_once():
+        nonlocal step
+        step += 1
+        ctx.train_step(P, G, M, V, step, cams, targets, loss_out=loss, cam_arr=cam_arr)
+
+    for _ in range(args.warmup):
+        train_once()
+    torch.cuda.synchronize()
+    code, needed = ctx.status()
+    if code != 0:
+        raise SystemExit(f"device status {code} (needed {needed}) after warm-up")
+    binding.call("gs_trace_enable", ctx.h, args.steps, ctx=ctx.h)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.15)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = binding.lib().gs_kernel_launches()
+    e0.record(st)
+    for _ in range(args.steps):
+        train_once()
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = int(binding.lib().gs_kernel_launches() - l0)
+    ms_total = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        tdist.barrier()
+    code, needed = ctx.status()
+    if code != 0:
+        raise SystemExit(f"device status {code} (needed {needed}) in the timed region")
+    # per-stage times of the timed steps (events on the launching stream)
+    import ctypes
+    buf = (ctypes.c_float * (args.steps * binding.GS_TRACE_STAGES))()
+    nst = ctypes.c_int32(0)
+    binding.call("gs_trace_read", ctx.h, buf, ctypes.byref(nst), ctx=ctx.h)
+    binding.call("gs_trace_enable", ctx.h, 0, ctx=ctx.h)
+    arr = np.frombuffer(buf, dtype=np.float32).reshape(args.steps, binding.GS_TRACE_STAGES)[:nst.value]
+    stage_ms = {s: float(arr[:, i].mean()) for i, s in enumerate(binding.TRACE_STAGES)}
+    counters = ctx.counters()
+
+    # end to end through the public API with host buffers
+    pinned = torch.from_numpy(tg).pin_memory()
+    loss_host = torch.empty(Bv, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        targets.copy_(pinned, non_blocking=True)
+        train_once()
+        loss_host.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        _ = float(loss_host[0])
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    views = args.steps * Bv * world
+    value = views / (ms_total * 1e-3)
+    e2e_value = views / e2e_s
+    if rank != 0:
+        return 0
+    dom = max(stage_ms, key=stage_ms.get)
+    high = 0
+    while (1 << high) < engine.total_tiles(cams, args.tile):
+        high += 1
+    passes = 4 + (high + 7) // 8
+    clk = clocks.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    rf = stage_roofline(dom, stage_ms[dom], counters, sc.N, Bv, Bv * H * W, passes, peaks, clk)
+    roofline = {"kernel": dom, "bound": rf["bound"], "achieved": rf["achieved"], "peak": rf["peak"],
+                "unit": rf["unit"], "frac": rf["achieved"] / rf["peak"], "traffic": None,
+                "peak_source": peak_kind, "work": rf["work_desc"]}
+    per_stage_roofline = {}
+    for s, ms in stage_ms.items():
+        r = stage_roofline(s, ms, counters, sc.N, Bv, Bv * H * W, passes, peaks, clk)
+        per_stage_roofline[s] = {"ms": ms, "bound": r["bound"], "frac": r["achieved"] / r["peak"]}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        crop = pick_crop(sc, cams, tg, lr6, 8.0)
+        smp = OracleSample(sc, cams, tg, lr6, crop)
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            smp.step(n + 1)
+            n += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": n * smp.frac / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": smp.describe() + f"; {n} steps in {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": name, "gaussians": sc.N, "views_per_step": Bv, "resolution": f"{W}x{H}",
+                   "tile": args.tile, "smem_batch": args.batch, "sh_degree": 3,
+                   "l2": "no flush: params + grad + Adam moments resident in HBM exceed the 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "mpix_per_s": value * H * W / 1e6},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tg.nbytes), "d2h_bytes_per_step": 4 * Bv,
+                "api": "gs_train_step with a pinned-host target upload and a loss readback every step"},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "stages": per_stage_roofline,
+        "counters": counters,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

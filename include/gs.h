@@ -1,0 +1,275 @@
+/*
+ * gs.h - C ABI of libgs, the GB300 (sm_103a) hot path of 3D Gaussian
+ * Splatting training (arXiv 2406.18533, "On Scaling Up 3D Gaussian Splatting
+ * Training").
+ *
+ * The paper splits one training iteration into four steps (Sec. 2.1):
+ * Gaussian transformation, rendering, loss calculation and backpropagation,
+ * followed by the Adam update of every Gaussian (Sec. 4, Eq. 1-2 for batched
+ * training).  Each entry point below is one of those steps, or the whole
+ * iteration (gs_train_step), or a forward-only batch of novel views
+ * (gs_render).
+ *
+ * Conventions shared by every call
+ *  - Pointers inside gs_scene, gs_proj, gs_proj_grad, gs_bins and the image
+ *    arguments are DEVICE pointers owned by the caller (the library never
+ *    frees them).  gs_camera and gs_hparams arrays are HOST memory, read
+ *    during the call only.
+ *  - Every call is asynchronous on the caller's CUDA stream (cudaStream_t
+ *    passed as void*; NULL = legacy default stream) unless it says otherwise.
+ *  - The library owns only scratch memory inside the opaque gs_ctx, grown on
+ *    demand with cudaMalloc (which synchronises the device) or reserved up
+ *    front with gs_reserve.  Calls on one context must not overlap on the GPU
+ *    (one stream per context).
+ *  - Every call returns a gs_status.  Host-side argument errors return at
+ *    once.  Errors found by kernels (fragment capacity overflow, non-finite
+ *    parameters in strict mode) are written to a device status word and
+ *    reported by gs_get_status.  gs_last_error gives a text for the last
+ *    non-OK status.  No exception or abort crosses the ABI.
+ *  - Camera model (a reading of the 3DGS projection the paper builds on):
+ *    OpenCV axes (x right, y down, z forward), p_cam = R p_world + t, pixel
+ *    (i, j) has centre (i + 0.5, j + 0.5), u = fx x/z + cx, v = fy y/z + cy.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_ABI_VERSION 1
+#define GS_MAX_VIEWS 32   /* views per call (training batch or render batch) */
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,  /* null pointer, bad size, B outside 1..GS_MAX_VIEWS, ... */
+    GS_ERR_CAPACITY = 2,     /* fragment buffer too small; the needed count is reported */
+    GS_ERR_CUDA = 3,         /* a CUDA runtime call failed (text in gs_last_error) */
+    GS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    GS_ERR_NONFINITE = 5,    /* non-finite parameters met in strict mode */
+    GS_ERR_OOM = 6           /* scratch allocation failed */
+} gs_status;
+
+/* Pinhole camera; 80 bytes. */
+typedef struct gs_camera {
+    float R[9];        /* world -> camera rotation, row-major */
+    float t[3];        /* translation: p_cam = R p_world + t */
+    float fx, fy;      /* focal lengths in pixels */
+    float cx, cy;      /* principal point in pixels */
+    int32_t W, H;      /* image size in pixels, each >= 1 */
+    float near_z;      /* a Gaussian with z_cam <= near_z is culled (> 0) */
+    int32_t reserved;
+} gs_camera;
+
+/*
+ * Gaussian parameters (Sec. 2: position x in R^3, scale s in R^3, rotation
+ * q in R^4, opacity, 48 SH coefficients), structure-of-arrays float4 planes,
+ * 60 floats per Gaussian.  The same struct describes gradients and the two
+ * Adam moments (same layout).  All four planes must be 16-byte aligned.
+ */
+typedef struct gs_scene {
+    float *mo;         /* [N] float4: x, y, z, opacity logit (opacity = sigmoid) */
+    float *ls;         /* [N] float4: log sx, log sy, log sz, unused (kept 0) */
+    float *q;          /* [N] float4: w, x, y, z (normalised inside) */
+    float *sh;         /* [12][N] float4: SH coefficient k (0..15), channel c at flat
+                          index j = 3k + c, stored in plane j/4, lane j%4 */
+    int64_t N;         /* number of Gaussians, >= 0 */
+    int32_t sh_degree; /* 0..3 */
+    int32_t reserved;
+} gs_scene;
+
+/* Hyperparameters (host struct, copied into the context). */
+typedef struct gs_hparams {
+    int32_t tile;             /* screen tile edge: 8, 16 (paper's 16x16 blocks) or 32 */
+    int32_t smem_batch;       /* Gaussians staged per shared-memory batch: 128, 256 or 512 */
+    int32_t strict_nonfinite; /* 1: report GS_ERR_NONFINITE; 0: cull silently */
+    float alpha_min;          /* skip a Gaussian at a pixel below this alpha (1/255) */
+    float alpha_max;          /* alpha is clamped to this (0.99) */
+    float T_min;              /* stop before a Gaussian that would take T below this (1e-4) */
+    float bg[3];              /* background colour added as T_final * bg (0) */
+    float lr[6];              /* Adam learning rates: mean, scale, quat, opacity, sh_dc, sh_rest */
+    float beta1, beta2, eps;  /* Adam (0.9, 0.999, 1e-15) */
+    int32_t scale_lr_sqrt_b;  /* Eq. 1: lr' = lr * sqrt(B) */
+    int32_t scale_beta_pow_b; /* Eq. 2: beta' = beta^B */
+    float lambda_dssim;       /* loss = (1-l) L1 + l (1 - SSIM), l = 0.2 */
+    int32_t reserved[2];
+} gs_hparams;
+
+/*
+ * Per (view, Gaussian) output of the Gaussian transformation (Sec. 2.1 step
+ * 1: projected centre x_{v,i}, depth, footprint radius, colour c_{v,i}),
+ * index v * N + g.  Caller-owned device arrays of B * N entries.
+ */
+typedef struct gs_proj {
+    float *xy;         /* float2 (u, v) pixel centre */
+    float *conic_o;    /* float4 (a, b, c, opacity): inverse 2D covariance [[a,b],[b,c]] */
+    float *rgb_d;      /* float4 (r, g, b, depth): view-dependent colour, camera-space z */
+    int32_t *radius;   /* footprint radius in whole pixels; 0 = touches no tile */
+    int64_t N;
+    int32_t B;
+    int32_t reserved;
+} gs_proj;
+
+/* Gradients with respect to gs_proj entries (float4 each, B * N entries). */
+typedef struct gs_proj_grad {
+    float *d_xy_o;     /* (dL/du, dL/dv, dL/dopacity, 0) */
+    float *d_conic;    /* (dL/da, dL/db, dL/dc, 0) */
+    float *d_rgb;      /* (dL/dr, dL/dg, dL/db, 0) */
+} gs_proj_grad;
+
+/*
+ * Depth-sorted fragments ("Z-buffer", Appendix A.2): one entry per
+ * (view, tile, Gaussian) whose footprint rectangle covers the tile, sorted by
+ * key = (tile_id << 32) | float_bits(depth); equal keys keep ascending
+ * Gaussian index.  tile_id = sum of tile counts of earlier views + ty * TX + tx.
+ */
+typedef struct gs_bins {
+    uint64_t *keys;    /* [capacity] sorted keys */
+    uint32_t *vals;    /* [capacity] Gaussian index within its view */
+    uint32_t *ranges;  /* [2 * total_tiles] uint2 [start, end) per tile_id */
+    uint32_t *count;   /* [1] device: number of fragments F */
+    uint64_t capacity; /* entries allocated in keys / vals */
+} gs_bins;
+
+typedef struct gs_ctx gs_ctx;
+
+/* Context: hyperparameters, scratch, device status word.  hp == NULL takes the
+ * 3DGS defaults.  Returns GS_ERR_INVALID_ARG for an unsupported tile size. */
+gs_status gs_create(gs_ctx **ctx, const gs_hparams *hp);
+gs_status gs_destroy(gs_ctx *ctx);
+gs_status gs_default_hparams(gs_hparams *hp);
+gs_status gs_set_hparams(gs_ctx *ctx, const gs_hparams *hp);
+const char *gs_last_error(const gs_ctx *ctx);
+int32_t gs_abi_version(void);
+
+/* Pre-size the context scratch for gs_train_step / gs_render so that no later
+ * call allocates (needed before stream capture into a CUDA graph). */
+gs_status gs_reserve(gs_ctx *ctx, int64_t N, const gs_camera *cams, int32_t B, uint64_t frag_capacity);
+
+/* Bytes of scratch gs_train_step would hold for these sizes. */
+gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *cams, int32_t B,
+                            uint64_t frag_capacity, size_t *bytes);
+
+/* Synchronise `stream`, then read and clear the device status word.
+ * *status gets GS_OK or the first device-side error; *needed (optional) the
+ * fragment count the last binning asked for. */
+gs_status gs_get_status(gs_ctx *ctx, void *stream, int32_t *status, uint64_t *needed);
+
+/* Counters of the last forward / backward render (device, read after sync):
+ * out[0] = fragments F, out[1] = (pixel, fragment) evaluations in the forward,
+ * out[2] = (pixel, fragment) evaluations in the backward. */
+gs_status gs_get_counters(gs_ctx *ctx, void *stream, uint64_t out[3]);
+
+/*
+ * Tracing (profiling aid, no paper counterpart): when enabled with
+ * gs_trace_enable(ctx, max_steps) (> 0; 0 disables), every gs_train_step
+ * records CUDA events on its stream around its GS_TRACE_STAGES stages, for
+ * up to max_steps steps.  gs_trace_read synchronises and writes, for each
+ * recorded step s and stage k, the elapsed milliseconds to
+ * ms[s * GS_TRACE_STAGES + k] (ms holds max_steps * GS_TRACE_STAGES floats),
+ * sets *steps to the number of recorded steps and restarts recording.
+ * Stage order: preprocess, scan, emit, sort, ranges, blend_fwd, loss,
+ * zero_grad, blend_bwd, preprocess_bwd, adam.
+ */
+#define GS_TRACE_STAGES 11
+gs_status gs_trace_enable(gs_ctx *ctx, int32_t max_steps);
+gs_status gs_trace_read(gs_ctx *ctx, float *ms, int32_t *steps);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all contexts); differences count the kernels of a region. */
+uint64_t gs_kernel_launches(void);
+
+/*
+ * Sec. 2.1 step 1 (Gaussian transformation), fused over B views: reads each
+ * Gaussian's parameters once, writes gs_proj for every view.  A Gaussian is
+ * culled in a view (radius 0) when z_cam <= near_z, its 2D covariance is
+ * singular, or its footprint rectangle misses the image.
+ */
+gs_status gs_preprocess(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cams, int32_t B,
+                        gs_proj *out, void *stream);
+
+/*
+ * Sec. 2.1 step 2, first half (Fig. 2 16x16 blocks; "iterates over
+ * intersecting Gaussians in increasing depth"): counts the tiles each
+ * (view, Gaussian) footprint rectangle covers, scans, emits one key per
+ * covered tile and radix-sorts them (8-bit digits, LSD, stable), then writes
+ * per-tile ranges.  If F > out->capacity nothing beyond capacity is written,
+ * the status word gets GS_ERR_CAPACITY and *needed_host (if given: this call
+ * then synchronises the stream) gets F and the call returns GS_ERR_CAPACITY.
+ */
+gs_status gs_bin(gs_ctx *ctx, const gs_proj *proj, const gs_camera *cams, int32_t B, gs_bins *out,
+                 uint64_t *needed_host, void *stream);
+
+/*
+ * Sec. 2.1 step 2, second half: per pixel, front-to-back alpha compositing
+ * over its tile's sorted list until transmittance would fall below T_min.
+ * img: [B][3][H][W] float; T_final: [B][H][W] float; n_contrib: [B][H][W]
+ * uint32 (1 + list position of the last blended Gaussian).  All views of one
+ * call must share W and H here (mixed sizes: gs_render).
+ */
+gs_status gs_render_fwd(gs_ctx *ctx, const gs_proj *proj, const gs_bins *bins, const gs_camera *cams,
+                        int32_t B, float *img, float *T_final, uint32_t *n_contrib, void *stream);
+
+/*
+ * Backward of the compositing (the paper's "standard approaches to
+ * backpropagation", Sec. 2.1): walks each pixel's contributors back to front,
+ * recovering transmittance from T_final by division (no per-fragment state),
+ * and accumulates dL/d(gs_proj) for every (view, Gaussian).  `out` is
+ * overwritten.  d_img has the layout of img.
+ */
+gs_status gs_render_bwd(gs_ctx *ctx, const gs_proj *proj, const gs_bins *bins, const gs_camera *cams,
+                        int32_t B, const float *T_final, const uint32_t *n_contrib, const float *d_img,
+                        gs_proj_grad *out, void *stream);
+
+/*
+ * Backward of the Gaussian transformation: chain rule from dL/d(gs_proj) to
+ * the 59 parameters of every Gaussian, summed over the B views and divided by
+ * B (the batch gradient is the mean of the per-view gradients, Sec. 4).
+ * `grad` is overwritten (its unused lane ls.w is written 0).
+ */
+gs_status gs_preprocess_bwd(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cams, int32_t B,
+                            const gs_proj *proj, const gs_proj_grad *dproj, gs_scene *grad, void *stream);
+
+/*
+ * Sec. 2.1 step 3: loss = (1 - l) mean|I - I*| + l (1 - mean SSIM(I, I*)),
+ * SSIM with an 11x11 Gaussian window (sigma 1.5), zero padding, per view.
+ * img, target, d_img: [B][3][H][W]; loss_out: [B] float (device).  d_img is
+ * dL_v/dI_v for each view v (not divided by B).
+ */
+gs_status gs_loss(gs_ctx *ctx, const float *img, const float *target, int32_t B, int32_t W, int32_t H,
+                  float *loss_out, float *d_img, void *stream);
+
+/*
+ * Adam over all 60 N floats (Sec. 4): m = b1' m + (1-b1') g, v = b2' v +
+ * (1-b2') g^2, p -= lr' m_hat / (sqrt(v_hat) + eps), bias correction with
+ * b' at `step` (>= 1), lr' = lr sqrt(B) (Eq. 1) and b' = b^B (Eq. 2) when the
+ * hyperparameter flags ask for them.  In place on p, m, v.
+ */
+gs_status gs_adam_step(gs_ctx *ctx, gs_scene *p, const gs_scene *g, gs_scene *m, gs_scene *v,
+                       int64_t step, int32_t B, void *stream);
+
+/*
+ * One whole training iteration over a batch of B views (Fig. 1(a) pipeline,
+ * batched as in Sec. 4): transformation, binning, compositing, loss,
+ * backward, Adam.  targets: [B][3][H][W] float device; loss_out: [B] float
+ * device.  Scratch comes from the context.  g receives the batch gradient.
+ */
+gs_status gs_train_step(gs_ctx *ctx, gs_scene *p, gs_scene *g, gs_scene *m, gs_scene *v, int64_t step,
+                        const gs_camera *cams, int32_t B, const float *targets, float *loss_out,
+                        void *stream);
+
+/*
+ * Forward-only render of B novel views of possibly different sizes (serving):
+ * imgs[b] (host array of device pointers) receives view b as [3][H_b][W_b].
+ */
+gs_status gs_render(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cams, int32_t B,
+                    float *const *imgs, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

@@ -1,0 +1,70 @@
+// K9: Adam over every Gaussian parameter (Sec. 4), with the batch-size
+// scaling of Eq. 1 (lr' = lr sqrt(B)) and Eq. 2 (beta' = beta^B) folded into
+// the arguments by the host.  A pure streaming kernel: per float4 it reads
+// p, g, m, v and writes p, m, v (112 bytes), coalesced and vectorised;
+// gridDim.y selects one of the 15 float4 planes (mo, ls, q, sh[0..11]).
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+__device__ __forceinline__ float4 *plane_ptr(const SceneMut &s, int pl)
+{
+    return pl == 0 ? s.mo : pl == 1 ? s.ls : pl == 2 ? s.q : s.sh + (int64_t)(pl - 3) * s.N;
+}
+
+__device__ __forceinline__ const float4 *plane_ptr(const SceneView &s, int pl)
+{
+    return pl == 0 ? s.mo : pl == 1 ? s.ls : pl == 2 ? s.q : s.sh + (int64_t)(pl - 3) * s.N;
+}
+
+__device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, float lr, const AdamArgs &a)
+{
+    m = a.b1 * m + (1.f - a.b1) * g;
+    v = a.b2 * v + (1.f - a.b2) * g * g;
+    const float mh = m / a.bc1, vh = v / a.bc2;
+    p -= lr * mh / (sqrtf(vh) + a.eps);
+}
+
+__global__ void __launch_bounds__(256) k_adam(SceneMut P, SceneView G, SceneMut M, SceneMut V, AdamArgs a,
+                                              const DevStatus *status)
+{
+    if (status->code == GS_ERR_CAPACITY) return;   // the step's gradient is incomplete: skip the update
+    const int pl = blockIdx.y;
+    float4 *pp = plane_ptr(P, pl);
+    const float4 *gp = plane_ptr(G, pl);
+    float4 *mp = plane_ptr(M, pl);
+    float4 *vp = plane_ptr(V, pl);
+    const float *lr = a.lr[pl];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.N; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 p = pp[i], m = mp[i], v = vp[i];
+        const float4 g = gp[i];
+        adam1(p.x, g.x, m.x, v.x, lr[0], a);
+        adam1(p.y, g.y, m.y, v.y, lr[1], a);
+        adam1(p.z, g.z, m.z, v.z, lr[2], a);
+        adam1(p.w, g.w, m.w, v.w, lr[3], a);
+        pp[i] = p;
+        mp[i] = m;
+        vp[i] = v;
+    }
+}
+
+}  // namespace
+
+void launch_adam(const SceneMut &p, const SceneView &g, const SceneMut &m, const SceneMut &v, const AdamArgs &a,
+                 const DevStatus *status, cudaStream_t st)
+{
+    if (p.N == 0) return;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // ~8 resident blocks of 256 per SM spread over the 15 planes
+    int64_t bx = ((int64_t)sms * 8 + 14) / 15;
+    const int64_t need = (p.N + 255) / 256;
+    if (bx > need) bx = need;
+    if (bx < 1) bx = 1;
+    k_adam<<<dim3((unsigned)bx, 15), 256, 0, st>>>(p, g, m, v, a, status);
+    count_launches(1);
+}
+
+}  // namespace gs

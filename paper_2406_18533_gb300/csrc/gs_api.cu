@@ -1,0 +1,736 @@
+// C ABI of libgs (declared in include/gs.h): argument checks, the context and
+// its scratch memory, and the sequencing of the kernels of one training
+// iteration (Sec. 2.1 steps 1-3 + backward, Sec. 4 Adam).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+using namespace gs;
+
+namespace gs {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace gs
+
+namespace {
+
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct gs_ctx {
+    gs_hparams hp;
+    DevStatus *status = nullptr;       // device
+    DevStatus *h_status = nullptr;     // pinned host mirror
+    char err[512];
+    // binning scratch
+    DBuf ntiles, offsets, scan_tmp, total, keys_alt, vals_alt, sort_tmp;
+    // iteration scratch (gs_train_step / gs_render)
+    DBuf xy, conic_o, rgb_d, radius, g_xy, g_co, g_rgb, keys, vals, ranges, count;
+    DBuf img, dimg, T_final, n_contrib, maps, acc;
+    uint64_t frag_cap = 0;
+    // tracing: events around the stages of gs_train_step
+    int trace_max = 0, trace_step = 0;
+    bool trace_on = false;
+    std::vector<cudaEvent_t> trace_ev;
+};
+
+namespace {
+
+gs_status fail(gs_ctx *c, gs_status s, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+gs_status cuda_check(gs_ctx *c, const char *where)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, GS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+    return GS_OK;
+}
+
+gs_status ensure(gs_ctx *c, DBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (bytes <= b.cap) return GS_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    const size_t nb = ((bytes + bytes / 8) + 255) & ~(size_t)255;
+    if (cudaMalloc(&b.p, nb) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(c, GS_ERR_OOM, "cudaMalloc of %zu bytes failed", nb);
+    }
+    b.cap = nb;
+    return GS_OK;
+}
+
+template <class T> T *ptr(DBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+bool finite_f(float x) { return std::isfinite(x); }
+
+int ilog2_exact(int t) { return t == 8 ? 3 : t == 16 ? 4 : t == 32 ? 5 : -1; }
+
+int bits_for(uint32_t n)   // bits needed to hold values 0 .. n-1
+{
+    int b = 0;
+    while (b < 32 && ((uint64_t)1 << b) < (uint64_t)n) ++b;
+    return b;
+}
+
+// Validates host cameras and builds the kernel-parameter view batch.
+gs_status make_views(gs_ctx *c, const gs_camera *cams, int32_t B, ViewBatch &vb, bool uniform)
+{
+    if (!cams) return fail(c, GS_ERR_INVALID_ARG, "cams is NULL");
+    if (B < 1 || B > GS_MAX_VIEWS) return fail(c, GS_ERR_INVALID_ARG, "B=%d outside 1..%d", B, GS_MAX_VIEWS);
+    memset(&vb, 0, sizeof vb);
+    vb.B = B;
+    vb.tile = c->hp.tile;
+    vb.log2_tile = ilog2_exact(c->hp.tile);
+    uint64_t base = 0;
+    for (int v = 0; v < B; ++v) {
+        const gs_camera &k = cams[v];
+        if (k.W < 1 || k.H < 1 || k.W > 65536 || k.H > 65536)
+            return fail(c, GS_ERR_INVALID_ARG, "view %d: bad size %dx%d", v, k.W, k.H);
+        if (!(k.near_z > 0.f) || !(k.fx > 0.f) || !(k.fy > 0.f))
+            return fail(c, GS_ERR_INVALID_ARG, "view %d: near_z, fx, fy must be > 0", v);
+        bool ok = finite_f(k.fx) && finite_f(k.fy) && finite_f(k.cx) && finite_f(k.cy) && finite_f(k.near_z);
+        for (int i = 0; i < 9; ++i) ok = ok && finite_f(k.R[i]);
+        for (int i = 0; i < 3; ++i) ok = ok && finite_f(k.t[i]);
+        if (!ok) return fail(c, GS_ERR_INVALID_ARG, "view %d: non-finite camera", v);
+        if (uniform && (k.W != cams[0].W || k.H != cams[0].H))
+            return fail(c, GS_ERR_INVALID_ARG, "view %d: all views of this call must share W and H", v);
+        ViewCam &o = vb.v[v];
+        memcpy(o.R, k.R, sizeof o.R);
+        memcpy(o.t, k.t, sizeof o.t);
+        o.fx = k.fx; o.fy = k.fy; o.cx = k.cx; o.cy = k.cy;
+        o.near_z = k.near_z;
+        o.limx = 1.3f * (0.5f * (float)k.W / k.fx);
+        o.limy = 1.3f * (0.5f * (float)k.H / k.fy);
+        for (int i = 0; i < 3; ++i)
+            o.C[i] = -(k.R[0 * 3 + i] * k.t[0] + k.R[1 * 3 + i] * k.t[1] + k.R[2 * 3 + i] * k.t[2]);
+        o.W = k.W; o.H = k.H;
+        o.TX = (k.W + c->hp.tile - 1) / c->hp.tile;
+        o.TY = (k.H + c->hp.tile - 1) / c->hp.tile;
+        o.tile_base = (uint32_t)base;
+        base += (uint64_t)o.TX * o.TY;
+    }
+    if (base >= ((uint64_t)1 << 31)) return fail(c, GS_ERR_INVALID_ARG, "too many tiles in one call");
+    vb.total_tiles = (uint32_t)base;
+    return GS_OK;
+}
+
+void set_images(ViewBatch &vb, float *img, float *T_final, uint32_t *n_contrib, const float *d_img)
+{
+    for (int v = 0; v < vb.B; ++v) {
+        const int64_t hw = (int64_t)vb.v[v].W * vb.v[v].H;
+        vb.v[v].img = img ? img + 3 * hw * v : nullptr;
+        vb.v[v].T_final = T_final ? T_final + hw * v : nullptr;
+        vb.v[v].n_contrib = n_contrib ? n_contrib + hw * v : nullptr;
+        vb.v[v].d_img = d_img ? d_img + 3 * hw * v : nullptr;
+    }
+}
+
+bool scene_ok(const gs_scene *s)
+{
+    if (!s || s->N < 0 || s->sh_degree < 0 || s->sh_degree > 3) return false;
+    if (s->N == 0) return true;
+    if (!s->mo || !s->ls || !s->q || !s->sh) return false;
+    const uintptr_t a = (uintptr_t)s->mo | (uintptr_t)s->ls | (uintptr_t)s->q | (uintptr_t)s->sh;
+    return (a & 15) == 0;
+}
+
+SceneView view_of(const gs_scene *s)
+{
+    return SceneView{reinterpret_cast<const float4 *>(s->mo), reinterpret_cast<const float4 *>(s->ls),
+                     reinterpret_cast<const float4 *>(s->q), reinterpret_cast<const float4 *>(s->sh), s->N,
+                     s->sh_degree};
+}
+
+SceneMut mut_of(gs_scene *s)
+{
+    return SceneMut{reinterpret_cast<float4 *>(s->mo), reinterpret_cast<float4 *>(s->ls),
+                    reinterpret_cast<float4 *>(s->q), reinterpret_cast<float4 *>(s->sh), s->N};
+}
+
+ProjView proj_of(const gs_proj *p)
+{
+    return ProjView{reinterpret_cast<float2 *>(p->xy), reinterpret_cast<float4 *>(p->conic_o),
+                    reinterpret_cast<float4 *>(p->rgb_d), p->radius, p->N};
+}
+
+BlendParams blend_of(const gs_hparams &hp)
+{
+    return BlendParams{hp.alpha_min, hp.alpha_max, hp.T_min, {hp.bg[0], hp.bg[1], hp.bg[2]}};
+}
+
+cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+constexpr int NSTAGE = GS_TRACE_STAGES;
+
+// Records the boundary event `k` (0 .. NSTAGE) of the current traced step.
+void mark(gs_ctx *c, cudaStream_t st, int k)
+{
+    if (c->trace_on) cudaEventRecord(c->trace_ev[(size_t)c->trace_step * (NSTAGE + 1) + k], st);
+}
+
+void trace_free(gs_ctx *c)
+{
+    for (cudaEvent_t e : c->trace_ev) cudaEventDestroy(e);
+    c->trace_ev.clear();
+    c->trace_max = 0;
+    c->trace_step = 0;
+    c->trace_on = false;
+}
+
+// Count, scan, emit, sort and range the fragments of `p` into (keys, vals,
+// ranges, count).  `ntiles` may already hold the per-(view, Gaussian) tile
+// counts (the transformation kernel writes them); otherwise pass nullptr.
+gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, const uint32_t *ntiles_in, uint64_t *keys,
+                      uint32_t *vals, uint2 *ranges, uint32_t *count, uint64_t capacity, cudaStream_t st)
+{
+    const int64_t n = (int64_t)vb.B * p.N;
+    gs_status r;
+    if ((r = ensure(c, c->offsets, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1))) != GS_OK) return r;
+    if ((r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) != GS_OK) return r;
+    if ((r = ensure(c, c->total, 64)) != GS_OK) return r;
+    const uint32_t *ntiles = ntiles_in;
+    if (!ntiles) {
+        if ((r = ensure(c, c->ntiles, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1))) != GS_OK) return r;
+        launch_count_tiles(vb, p, ptr<uint32_t>(c->ntiles), st);
+        ntiles = ptr<uint32_t>(c->ntiles);
+    }
+    const int high = bits_for(vb.total_tiles);
+    const int passes = 4 + (high + 7) / 8;
+    if ((r = ensure(c, c->keys_alt, sizeof(uint64_t) * (size_t)(capacity ? capacity : 1))) != GS_OK) return r;
+    if ((r = ensure(c, c->vals_alt, sizeof(uint32_t) * (size_t)(capacity ? capacity : 1))) != GS_OK) return r;
+    if ((r = ensure(c, c->sort_tmp, sort_temp_bytes(capacity))) != GS_OK) return r;
+    uint64_t *k_emit = (passes % 2 == 0) ? keys : ptr<uint64_t>(c->keys_alt);
+    uint32_t *v_emit = (passes % 2 == 0) ? vals : ptr<uint32_t>(c->vals_alt);
+    uint64_t *k_other = (passes % 2 == 0) ? ptr<uint64_t>(c->keys_alt) : keys;
+    uint32_t *v_other = (passes % 2 == 0) ? ptr<uint32_t>(c->vals_alt) : vals;
+    auto *total = ptr<unsigned long long>(c->total);
+    launch_exclusive_scan(ntiles, ptr<uint32_t>(c->offsets), n, total, c->scan_tmp.p, st);
+    mark(c, st, 2);
+    launch_emit_keys(vb, p, ntiles, ptr<uint32_t>(c->offsets), k_emit, v_emit, capacity, total, c->status, count,
+                     st);
+    mark(c, st, 3);
+    launch_radix_sort(k_emit, v_emit, k_other, v_other, capacity, count, high, c->sort_tmp.p, st);
+    mark(c, st, 4);
+    launch_tile_ranges(keys, count, capacity, ranges, vb.total_tiles, st);
+    mark(c, st, 5);
+    return cuda_check(c, "binning");
+}
+
+// Iteration scratch for B views of N Gaussians with a fragment capacity.
+gs_status ensure_iter(gs_ctx *c, int64_t N, const ViewBatch &vb, uint64_t cap)
+{
+    const size_t n = (size_t)vb.B * (size_t)(N > 0 ? N : 1);
+    size_t pix = 0;
+    for (int v = 0; v < vb.B; ++v) pix += (size_t)vb.v[v].W * vb.v[v].H;
+    gs_status r;
+    if ((r = ensure(c, c->xy, 8 * n)) || (r = ensure(c, c->conic_o, 16 * n)) || (r = ensure(c, c->rgb_d, 16 * n)) ||
+        (r = ensure(c, c->radius, 4 * n)) || (r = ensure(c, c->ntiles, 4 * n)) || (r = ensure(c, c->offsets, 4 * n)))
+        return r;
+    if ((r = ensure(c, c->keys, 8 * (size_t)(cap ? cap : 1))) || (r = ensure(c, c->vals, 4 * (size_t)(cap ? cap : 1))) ||
+        (r = ensure(c, c->ranges, 8 * (size_t)vb.total_tiles)) || (r = ensure(c, c->count, 64)))
+        return r;
+    if ((r = ensure(c, c->T_final, 4 * pix)) || (r = ensure(c, c->n_contrib, 4 * pix))) return r;
+    return GS_OK;
+}
+
+gs_status ensure_train(gs_ctx *c, int64_t N, const ViewBatch &vb)
+{
+    const size_t n = (size_t)vb.B * (size_t)(N > 0 ? N : 1);
+    const size_t pix = (size_t)vb.B * vb.v[0].W * vb.v[0].H;
+    gs_status r;
+    if ((r = ensure(c, c->g_xy, 16 * n)) || (r = ensure(c, c->g_co, 16 * n)) || (r = ensure(c, c->g_rgb, 16 * n)))
+        return r;
+    if ((r = ensure(c, c->img, 12 * pix)) || (r = ensure(c, c->dimg, 12 * pix)) || (r = ensure(c, c->maps, 36 * pix)) ||
+        (r = ensure(c, c->acc, 16 * (size_t)vb.B + 64)))
+        return r;
+    return GS_OK;
+}
+
+// Reads the fragment total of the scan just issued on `st` (synchronises).
+gs_status read_total(gs_ctx *c, cudaStream_t st, uint64_t *F)
+{
+    unsigned long long h = 0;
+    if (cudaMemcpyAsync(&c->h_status->needed, c->total.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_check(c, "read_total");
+    h = c->h_status->needed;
+    *F = h;
+    return GS_OK;
+}
+
+AdamArgs adam_args(const gs_hparams &hp, int64_t step, int32_t B)
+{
+    AdamArgs a;
+    const double b1 = hp.scale_beta_pow_b ? pow((double)hp.beta1, B) : hp.beta1;
+    const double b2 = hp.scale_beta_pow_b ? pow((double)hp.beta2, B) : hp.beta2;
+    const double lf = hp.scale_lr_sqrt_b ? sqrt((double)B) : 1.0;
+    a.b1 = (float)b1;
+    a.b2 = (float)b2;
+    a.eps = hp.eps;
+    a.bc1 = (float)(1.0 - pow(b1, (double)step));
+    a.bc2 = (float)(1.0 - pow(b2, (double)step));
+    const float lm = (float)(hp.lr[0] * lf), lsc = (float)(hp.lr[1] * lf), lq = (float)(hp.lr[2] * lf);
+    const float lo = (float)(hp.lr[3] * lf), ldc = (float)(hp.lr[4] * lf), lrest = (float)(hp.lr[5] * lf);
+    const float planes[3][4] = {{lm, lm, lm, lo}, {lsc, lsc, lsc, 0.f}, {lq, lq, lq, lq}};
+    for (int p = 0; p < 3; ++p)
+        for (int l = 0; l < 4; ++l) a.lr[p][l] = planes[p][l];
+    for (int p = 3; p < 15; ++p)
+        for (int l = 0; l < 4; ++l) {
+            const int j = 4 * (p - 3) + l;   // flat SH index; 0..2 are the DC coefficients
+            a.lr[p][l] = j < 3 ? ldc : lrest;
+        }
+    return a;
+}
+
+gs_status check_hparams(gs_ctx *c, const gs_hparams *hp)
+{
+    if (ilog2_exact(hp->tile) < 0) return fail(c, GS_ERR_INVALID_ARG, "tile must be 8, 16 or 32");
+    if (hp->smem_batch != 128 && hp->smem_batch != 256 && hp->smem_batch != 512)
+        return fail(c, GS_ERR_INVALID_ARG, "smem_batch must be 128, 256 or 512");
+    if (!(hp->alpha_max > 0.f && hp->alpha_max < 1.f) || !(hp->alpha_min >= 0.f) || !(hp->T_min >= 0.f))
+        return fail(c, GS_ERR_INVALID_ARG, "blend thresholds out of range");
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t gs_abi_version(void) { return GS_ABI_VERSION; }
+
+uint64_t gs_kernel_launches(void) { return gs::g_launches.load(); }
+
+gs_status gs_trace_enable(gs_ctx *c, int32_t max_steps)
+{
+    if (!c || max_steps < 0) return GS_ERR_INVALID_ARG;
+    trace_free(c);
+    if (max_steps == 0) return GS_OK;
+    c->trace_ev.resize((size_t)max_steps * (NSTAGE + 1));
+    for (auto &e : c->trace_ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            trace_free(c);
+            return cuda_check(c, "gs_trace_enable");
+        }
+    c->trace_max = max_steps;
+    c->trace_step = 0;
+    return GS_OK;
+}
+
+gs_status gs_trace_read(gs_ctx *c, float *ms, int32_t *steps)
+{
+    if (!c || !ms || !steps) return GS_ERR_INVALID_ARG;
+    *steps = 0;
+    for (int s = 0; s < c->trace_step; ++s) {
+        cudaEvent_t *e = &c->trace_ev[(size_t)s * (NSTAGE + 1)];
+        if (cudaEventSynchronize(e[NSTAGE]) != cudaSuccess) return cuda_check(c, "gs_trace_read");
+        for (int k = 0; k < NSTAGE; ++k) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, e[k], e[k + 1]) != cudaSuccess) return cuda_check(c, "gs_trace_read");
+            ms[(size_t)s * NSTAGE + k] = t;
+        }
+    }
+    *steps = c->trace_step;
+    c->trace_step = 0;
+    return GS_OK;
+}
+
+gs_status gs_default_hparams(gs_hparams *hp)
+{
+    if (!hp) return GS_ERR_INVALID_ARG;
+    memset(hp, 0, sizeof *hp);
+    hp->tile = 16;
+    hp->smem_batch = 256;
+    hp->strict_nonfinite = 0;
+    hp->alpha_min = 1.0f / 255.0f;
+    hp->alpha_max = 0.99f;
+    hp->T_min = 1e-4f;
+    const float lr[6] = {1.6e-4f, 5e-3f, 1e-3f, 5e-2f, 2.5e-3f, 2.5e-4f};
+    memcpy(hp->lr, lr, sizeof lr);
+    hp->beta1 = 0.9f;
+    hp->beta2 = 0.999f;
+    hp->eps = 1e-15f;
+    hp->scale_lr_sqrt_b = 1;
+    hp->scale_beta_pow_b = 1;
+    hp->lambda_dssim = 0.2f;
+    return GS_OK;
+}
+
+gs_status gs_create(gs_ctx **out, const gs_hparams *hp)
+{
+    if (!out) return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    gs_ctx *c = new (std::nothrow) gs_ctx();
+    if (!c) return GS_ERR_OOM;
+    c->err[0] = 0;
+    if (hp) c->hp = *hp; else gs_default_hparams(&c->hp);
+    gs_status r = check_hparams(c, &c->hp);
+    if (r != GS_OK) { delete c; return r; }
+    if (cudaMalloc(&c->status, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMallocHost(&c->h_status, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->status) cudaFree(c->status);
+        delete c;
+        return GS_ERR_CUDA;
+    }
+    cudaMemset(c->status, 0, sizeof(DevStatus));
+    memset(c->h_status, 0, sizeof(DevStatus));
+    if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); }
+    *out = c;
+    return GS_OK;
+}
+
+gs_status gs_destroy(gs_ctx *c)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    DBuf *bufs[] = {&c->ntiles, &c->offsets, &c->scan_tmp, &c->total, &c->keys_alt, &c->vals_alt, &c->sort_tmp,
+                    &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_xy, &c->g_co, &c->g_rgb, &c->keys,
+                    &c->vals, &c->ranges, &c->count, &c->img, &c->dimg, &c->T_final, &c->n_contrib, &c->maps,
+                    &c->acc};
+    for (DBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    trace_free(c);
+    if (c->status) cudaFree(c->status);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    delete c;
+    return GS_OK;
+}
+
+gs_status gs_set_hparams(gs_ctx *c, const gs_hparams *hp)
+{
+    if (!c || !hp) return GS_ERR_INVALID_ARG;
+    gs_status r = check_hparams(c, hp);
+    if (r != GS_OK) return r;
+    c->hp = *hp;
+    return GS_OK;
+}
+
+const char *gs_last_error(const gs_ctx *c) { return c ? c->err : "null context"; }
+
+gs_status gs_get_status(gs_ctx *c, void *stream, int32_t *status, uint64_t *needed)
+{
+    if (!c || !status) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    if (cudaMemcpyAsync(c->h_status, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_check(c, "gs_get_status");
+    *status = c->h_status->code;
+    if (needed) *needed = c->h_status->needed;
+    if (c->h_status->code != 0) {
+        cudaMemsetAsync(c->status, 0, sizeof(int32_t), st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "gs_get_status clear");
+    }
+    return GS_OK;
+}
+
+gs_status gs_get_counters(gs_ctx *c, void *stream, uint64_t out[3])
+{
+    if (!c || !out) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    if (cudaMemcpyAsync(c->h_status, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_check(c, "gs_get_counters");
+    for (int i = 0; i < 3; ++i) out[i] = c->h_status->counters[i];
+    return GS_OK;
+}
+
+gs_status gs_reserve(gs_ctx *c, int64_t N, const gs_camera *cams, int32_t B, uint64_t frag_capacity)
+{
+    if (!c || N < 0) return GS_ERR_INVALID_ARG;
+    ViewBatch vb;
+    gs_status r = make_views(c, cams, B, vb, false);
+    if (r != GS_OK) return r;
+    if (frag_capacity > 0xffffffffull) return fail(c, GS_ERR_INVALID_ARG, "fragment capacity above 2^32-1");
+    if (frag_capacity > c->frag_cap) c->frag_cap = frag_capacity;
+    const int64_t n = (int64_t)B * (N > 0 ? N : 1);
+    if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
+    if ((r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) || (r = ensure(c, c->total, 64)) ||
+        (r = ensure(c, c->keys_alt, 8 * (size_t)(c->frag_cap ? c->frag_cap : 1))) ||
+        (r = ensure(c, c->vals_alt, 4 * (size_t)(c->frag_cap ? c->frag_cap : 1))) ||
+        (r = ensure(c, c->sort_tmp, sort_temp_bytes(c->frag_cap))))
+        return r;
+    bool uniform = true;
+    for (int v = 1; v < B; ++v) uniform = uniform && cams[v].W == cams[0].W && cams[v].H == cams[0].H;
+    if (uniform && (r = ensure_train(c, N, vb)) != GS_OK) return r;
+    return GS_OK;
+}
+
+gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *cams, int32_t B,
+                            uint64_t frag_capacity, size_t *bytes)
+{
+    if (!bytes || !cams || B < 1 || B > GS_MAX_VIEWS || N < 0) return GS_ERR_INVALID_ARG;
+    gs_hparams h;
+    if (hp) h = *hp; else gs_default_hparams(&h);
+    const int t = h.tile;
+    if (ilog2_exact(t) < 0) return GS_ERR_INVALID_ARG;
+    size_t tiles = 0, pix = 0;
+    for (int v = 0; v < B; ++v) {
+        tiles += (size_t)((cams[v].W + t - 1) / t) * ((cams[v].H + t - 1) / t);
+        pix += (size_t)cams[v].W * cams[v].H;
+    }
+    const size_t n = (size_t)B * (size_t)N;
+    size_t s = n * (8 + 16 + 16 + 4 + 4 + 4 + 48) + frag_capacity * (12 * 2) + sort_temp_bytes(frag_capacity) +
+               scan_temp_bytes((int64_t)n) + tiles * 8 + pix * (4 + 4 + 12 + 12 + 36) + 4096;
+    *bytes = s;
+    return GS_OK;
+}
+
+gs_status gs_preprocess(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int32_t B, gs_proj *out,
+                        void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(scene)) return fail(c, GS_ERR_INVALID_ARG, "bad scene (null/unaligned planes or sh_degree)");
+    if (!out || out->N != scene->N || out->B != B) return fail(c, GS_ERR_INVALID_ARG, "gs_proj N/B mismatch");
+    if (scene->N > 0 && (!out->xy || !out->conic_o || !out->rgb_d || !out->radius))
+        return fail(c, GS_ERR_INVALID_ARG, "gs_proj has null arrays");
+    ViewBatch vb;
+    gs_status r = make_views(c, cams, B, vb, false);
+    if (r != GS_OK) return r;
+    const int64_t n = (int64_t)B * scene->N;
+    if ((r = ensure(c, c->ntiles, 4 * (size_t)(n > 0 ? n : 1))) != GS_OK) return r;
+    launch_preprocess_fwd(view_of(scene), vb, proj_of(out), ptr<uint32_t>(c->ntiles), c->status,
+                          c->hp.strict_nonfinite, S(stream));
+    return cuda_check(c, "gs_preprocess");
+}
+
+gs_status gs_bin(gs_ctx *c, const gs_proj *proj, const gs_camera *cams, int32_t B, gs_bins *out,
+                 uint64_t *needed_host, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!proj || proj->B != B || proj->N < 0) return fail(c, GS_ERR_INVALID_ARG, "bad gs_proj");
+    if (!out || !out->ranges || !out->count || (out->capacity > 0 && (!out->keys || !out->vals)))
+        return fail(c, GS_ERR_INVALID_ARG, "bad gs_bins");
+    if (out->capacity > 0xffffffffull) return fail(c, GS_ERR_INVALID_ARG, "capacity above 2^32-1");
+    ViewBatch vb;
+    gs_status r = make_views(c, cams, B, vb, false);
+    if (r != GS_OK) return r;
+    cudaStream_t st = S(stream);
+    r = run_binning(c, vb, proj_of(proj), nullptr, out->keys, out->vals, reinterpret_cast<uint2 *>(out->ranges),
+                    out->count, out->capacity, st);
+    if (r != GS_OK) return r;
+    if (needed_host) {
+        uint64_t F = 0;
+        if ((r = read_total(c, st, &F)) != GS_OK) return r;
+        *needed_host = F;
+        if (F > out->capacity) return fail(c, GS_ERR_CAPACITY, "need %llu fragments, capacity %llu",
+                                           (unsigned long long)F, (unsigned long long)out->capacity);
+    }
+    return GS_OK;
+}
+
+gs_status gs_render_fwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, const gs_camera *cams, int32_t B,
+                        float *img, float *T_final, uint32_t *n_contrib, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!proj || proj->B != B || !bins || !img || !T_final || !n_contrib)
+        return fail(c, GS_ERR_INVALID_ARG, "null argument");
+    ViewBatch vb;
+    gs_status r = make_views(c, cams, B, vb, true);
+    if (r != GS_OK) return r;
+    set_images(vb, img, T_final, n_contrib, nullptr);
+    launch_blend_fwd(vb, proj_of(proj), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges), blend_of(c->hp),
+                     c->hp.smem_batch, c->status, S(stream));
+    return cuda_check(c, "gs_render_fwd");
+}
+
+gs_status gs_render_bwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, const gs_camera *cams, int32_t B,
+                        const float *T_final, const uint32_t *n_contrib, const float *d_img, gs_proj_grad *out,
+                        void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!proj || proj->B != B || !bins || !T_final || !n_contrib || !d_img || !out)
+        return fail(c, GS_ERR_INVALID_ARG, "null argument");
+    if (proj->N > 0 && (!out->d_xy_o || !out->d_conic || !out->d_rgb))
+        return fail(c, GS_ERR_INVALID_ARG, "null gradient arrays");
+    ViewBatch vb;
+    gs_status r = make_views(c, cams, B, vb, true);
+    if (r != GS_OK) return r;
+    set_images(vb, nullptr, const_cast<float *>(T_final), const_cast<uint32_t *>(n_contrib), d_img);
+    cudaStream_t st = S(stream);
+    const size_t bytes = 16 * (size_t)B * (size_t)proj->N;
+    if (bytes) {
+        cudaMemsetAsync(out->d_xy_o, 0, bytes, st);
+        cudaMemsetAsync(out->d_conic, 0, bytes, st);
+        cudaMemsetAsync(out->d_rgb, 0, bytes, st);
+    }
+    GradView gv{reinterpret_cast<float4 *>(out->d_xy_o), reinterpret_cast<float4 *>(out->d_conic),
+                reinterpret_cast<float4 *>(out->d_rgb)};
+    launch_blend_bwd(vb, proj_of(proj), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges), blend_of(c->hp),
+                     c->hp.smem_batch, gv, c->status, st);
+    return cuda_check(c, "gs_render_bwd");
+}
+
+gs_status gs_preprocess_bwd(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int32_t B, const gs_proj *proj,
+                            const gs_proj_grad *dproj, gs_scene *grad, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(scene) || !scene_ok(grad) || grad->N != scene->N)
+        return fail(c, GS_ERR_INVALID_ARG, "bad scene or gradient planes");
+    if (!proj || proj->B != B || proj->N != scene->N || !dproj) return fail(c, GS_ERR_INVALID_ARG, "bad gs_proj");
+    ViewBatch vb;
+    gs_status r = make_views(c, cams, B, vb, false);
+    if (r != GS_OK) return r;
+    GradView gv{reinterpret_cast<float4 *>(dproj->d_xy_o), reinterpret_cast<float4 *>(dproj->d_conic),
+                reinterpret_cast<float4 *>(dproj->d_rgb)};
+    launch_preprocess_bwd(view_of(scene), vb, proj_of(proj), gv, mut_of(grad), S(stream));
+    return cuda_check(c, "gs_preprocess_bwd");
+}
+
+gs_status gs_loss(gs_ctx *c, const float *img, const float *target, int32_t B, int32_t W, int32_t H,
+                  float *loss_out, float *d_img, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!img || !target || !loss_out || !d_img || B < 1 || B > GS_MAX_VIEWS || W < 1 || H < 1)
+        return fail(c, GS_ERR_INVALID_ARG, "bad loss arguments");
+    const size_t pix = (size_t)B * W * H;
+    gs_status r;
+    if ((r = ensure(c, c->maps, 36 * pix)) || (r = ensure(c, c->acc, 16 * (size_t)B + 64))) return r;
+    launch_loss(img, target, B, W, H, c->hp.lambda_dssim, loss_out, d_img, ptr<float>(c->maps), ptr<double>(c->acc),
+                S(stream));
+    return cuda_check(c, "gs_loss");
+}
+
+gs_status gs_adam_step(gs_ctx *c, gs_scene *p, const gs_scene *g, gs_scene *m, gs_scene *v, int64_t step, int32_t B,
+                       void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(p) || !scene_ok(g) || !scene_ok(m) || !scene_ok(v) || g->N != p->N || m->N != p->N ||
+        v->N != p->N)
+        return fail(c, GS_ERR_INVALID_ARG, "bad parameter / moment planes");
+    if (step < 1 || B < 1) return fail(c, GS_ERR_INVALID_ARG, "step and B must be >= 1");
+    launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), adam_args(c->hp, step, B), c->status, S(stream));
+    return cuda_check(c, "gs_adam_step");
+}
+
+gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_scene *v, int64_t step,
+                        const gs_camera *cams, int32_t B, const float *targets, float *loss_out, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(p) || !scene_ok(g) || !scene_ok(m) || !scene_ok(v) || g->N != p->N || m->N != p->N ||
+        v->N != p->N)
+        return fail(c, GS_ERR_INVALID_ARG, "bad parameter / moment planes");
+    if (!targets || !loss_out || step < 1) return fail(c, GS_ERR_INVALID_ARG, "bad targets / loss_out / step");
+    ViewBatch vb;
+    gs_status r = make_views(c, cams, B, vb, true);
+    if (r != GS_OK) return r;
+    cudaStream_t st = S(stream);
+    const int64_t N = p->N;
+    const int64_t n = (int64_t)B * N;
+    if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
+    if ((r = ensure_train(c, N, vb)) != GS_OK) return r;
+    gs_proj pr{ptr<float>(c->xy), ptr<float>(c->conic_o), ptr<float>(c->rgb_d), ptr<int32_t>(c->radius), N, B, 0};
+    const ProjView pv = proj_of(&pr);
+    const SceneView sv = view_of(p);
+    c->trace_on = c->trace_max > 0 && c->trace_step < c->trace_max;
+    mark(c, st, 0);
+    launch_preprocess_fwd(sv, vb, pv, ptr<uint32_t>(c->ntiles), c->status, c->hp.strict_nonfinite, st);
+    mark(c, st, 1);
+    if (c->frag_cap == 0) {
+        // first call on this context: size the fragment buffers from an exact count
+        if ((r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) || (r = ensure(c, c->total, 64))) return r;
+        launch_exclusive_scan(ptr<uint32_t>(c->ntiles), ptr<uint32_t>(c->offsets), n,
+                              ptr<unsigned long long>(c->total), c->scan_tmp.p, st);
+        uint64_t F = 0;
+        if ((r = read_total(c, st, &F)) != GS_OK) return r;
+        uint64_t cap = F + F / 4 + 4096;
+        if (cap > 0xffffffffull) cap = 0xffffffffull;
+        c->frag_cap = cap;
+        if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
+    }
+    r = run_binning(c, vb, pv, ptr<uint32_t>(c->ntiles), ptr<uint64_t>(c->keys), ptr<uint32_t>(c->vals),
+                    ptr<uint2>(c->ranges), ptr<uint32_t>(c->count), c->frag_cap, st);
+    if (r != GS_OK) return r;
+    set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
+    const BlendParams bp = blend_of(c->hp);
+    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->status, st);
+    mark(c, st, 6);
+    launch_loss(ptr<float>(c->img), targets, B, vb.v[0].W, vb.v[0].H, c->hp.lambda_dssim, loss_out,
+                ptr<float>(c->dimg), ptr<float>(c->maps), ptr<double>(c->acc), st);
+    mark(c, st, 7);
+    const size_t gbytes = 16 * (size_t)n;
+    if (gbytes) {
+        cudaMemsetAsync(c->g_xy.p, 0, gbytes, st);
+        cudaMemsetAsync(c->g_co.p, 0, gbytes, st);
+        cudaMemsetAsync(c->g_rgb.p, 0, gbytes, st);
+    }
+    mark(c, st, 8);
+    const GradView gv{ptr<float4>(c->g_xy), ptr<float4>(c->g_co), ptr<float4>(c->g_rgb)};
+    launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, gv, c->status, st);
+    mark(c, st, 9);
+    launch_preprocess_bwd(sv, vb, pv, gv, mut_of(g), st);
+    mark(c, st, 10);
+    launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), adam_args(c->hp, step, B), c->status, st);
+    mark(c, st, 11);
+    if (c->trace_on) ++c->trace_step;
+    c->trace_on = false;
+    return cuda_check(c, "gs_train_step");
+}
+
+gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int32_t B, float *const *imgs,
+                    void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(scene) || !imgs) return fail(c, GS_ERR_INVALID_ARG, "bad scene or image array");
+    ViewBatch vb;
+    gs_status r = make_views(c, cams, B, vb, false);
+    if (r != GS_OK) return r;
+    for (int v = 0; v < B; ++v)
+        if (!imgs[v]) return fail(c, GS_ERR_INVALID_ARG, "imgs[%d] is NULL", v);
+    cudaStream_t st = S(stream);
+    const int64_t N = scene->N;
+    const int64_t n = (int64_t)B * N;
+    if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
+    gs_proj pr{ptr<float>(c->xy), ptr<float>(c->conic_o), ptr<float>(c->rgb_d), ptr<int32_t>(c->radius), N, B, 0};
+    const ProjView pv = proj_of(&pr);
+    launch_preprocess_fwd(view_of(scene), vb, pv, ptr<uint32_t>(c->ntiles), c->status, c->hp.strict_nonfinite, st);
+    if (c->frag_cap == 0) {
+        if ((r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) || (r = ensure(c, c->total, 64))) return r;
+        launch_exclusive_scan(ptr<uint32_t>(c->ntiles), ptr<uint32_t>(c->offsets), n,
+                              ptr<unsigned long long>(c->total), c->scan_tmp.p, st);
+        uint64_t F = 0;
+        if ((r = read_total(c, st, &F)) != GS_OK) return r;
+        uint64_t cap = F + F / 4 + 4096;
+        if (cap > 0xffffffffull) cap = 0xffffffffull;
+        c->frag_cap = cap;
+        if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
+    }
+    r = run_binning(c, vb, pv, ptr<uint32_t>(c->ntiles), ptr<uint64_t>(c->keys), ptr<uint32_t>(c->vals),
+                    ptr<uint2>(c->ranges), ptr<uint32_t>(c->count), c->frag_cap, st);
+    if (r != GS_OK) return r;
+    size_t off = 0;
+    for (int v = 0; v < B; ++v) {
+        const size_t hw = (size_t)vb.v[v].W * vb.v[v].H;
+        vb.v[v].img = imgs[v];
+        vb.v[v].T_final = ptr<float>(c->T_final) + off;
+        vb.v[v].n_contrib = ptr<uint32_t>(c->n_contrib) + off;
+        off += hw;
+    }
+    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), blend_of(c->hp), c->hp.smem_batch,
+                     c->status, st);
+    return cuda_check(c, "gs_render");
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Internal declarations shared by the libgs translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr int MAXV = GS_MAX_VIEWS;
+
+// Per-view state passed by value in kernel parameters (no device copy of the
+// camera array is needed, and CUDA-graph capture records it with the launch).
+struct ViewCam {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float near_z;
+    float limx, limy;      // 1.3 * tan(fov/2): off-axis clamp of x/z and y/z
+    float C[3];            // camera centre in world space
+    int32_t W, H, TX, TY;  // image and tile-grid size
+    uint32_t tile_base;    // first global tile id of this view
+    uint32_t pix_base;     // unused for per-view pointers; kept for packed layouts
+    float *img;            // [3][H][W]
+    float *T_final;        // [H][W]
+    uint32_t *n_contrib;   // [H][W]
+    const float *d_img;    // [3][H][W]
+};
+
+struct ViewBatch {
+    int32_t B;
+    int32_t tile;
+    int32_t log2_tile;
+    uint32_t total_tiles;
+    ViewCam v[MAXV];
+};
+
+struct BlendParams {
+    float alpha_min, alpha_max, T_min;
+    float bg[3];
+};
+
+struct SceneView {     // read-only parameter planes
+    const float4 *mo, *ls, *q, *sh;
+    int64_t N;
+    int32_t deg;
+};
+
+struct SceneMut {
+    float4 *mo, *ls, *q, *sh;
+    int64_t N;
+};
+
+struct ProjView {
+    float2 *xy;
+    float4 *conic_o;
+    float4 *rgb_d;
+    int32_t *radius;
+    int64_t N;
+};
+
+struct GradView {
+    float4 *d_xy_o, *d_conic, *d_rgb;
+};
+
+// Device status word layout (one per context).
+struct DevStatus {
+    int32_t code;          // first gs_status error, 0 = OK
+    int32_t pad;
+    unsigned long long needed;  // fragments requested by the last binning
+    unsigned long long counters[4];  // F, fwd evaluations, bwd evaluations, culled non-finite
+};
+
+// Process-wide count of kernel launches (incremented by every launcher).
+void count_launches(int n);
+
+// Launchers (all asynchronous on `st`).
+void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, uint32_t *ntiles,
+                           DevStatus *status, int strict, cudaStream_t st);
+void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
+                           const SceneMut &out, cudaStream_t st);
+
+// Exclusive scan of n uint32 values (n < 2^31); total (uint64) to *total.
+size_t scan_temp_bytes(int64_t n);
+void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *total, void *temp,
+                           cudaStream_t st);
+
+void launch_count_tiles(const ViewBatch &vb, const ProjView &p, uint32_t *ntiles, cudaStream_t st);
+void launch_emit_keys(const ViewBatch &vb, const ProjView &p, const uint32_t *ntiles, const uint32_t *offsets,
+                      uint64_t *keys, uint32_t *vals, uint64_t capacity, const unsigned long long *total,
+                      DevStatus *status, uint32_t *count_out, cudaStream_t st);
+
+size_t sort_temp_bytes(uint64_t capacity);
+// Sorts keys/vals (count on device, <= capacity) on bits [0, 32 + high_bits).
+// Result lands in keys/vals; alt buffers are scratch of the same capacity.
+void launch_radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
+                       const uint32_t *count, int high_bits, void *temp, cudaStream_t st);
+
+void launch_tile_ranges(const uint64_t *keys, const uint32_t *count, uint64_t capacity, uint2 *ranges,
+                        uint32_t total_tiles, cudaStream_t st);
+
+// batch: Gaussians staged per shared-memory batch (128, 256 or 512).
+void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
+                      const BlendParams &bp, int batch, DevStatus *status, cudaStream_t st);
+void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
+                      const BlendParams &bp, int batch, const GradView &g, DevStatus *status, cudaStream_t st);
+
+void launch_loss(const float *img, const float *target, int B, int W, int H, float lambda, float *loss_out,
+                 float *d_img, float *maps, double *acc, cudaStream_t st);
+
+struct AdamArgs {
+    float lr[15][4];   // per plane, per lane (already times sqrt(B) when asked)
+    float b1, b2, eps;
+    float bc1, bc2;    // 1 - b1^t, 1 - b2^t
+};
+void launch_adam(const SceneMut &p, const SceneView &g, const SceneMut &m, const SceneMut &v, const AdamArgs &a,
+                 const DevStatus *status, cudaStream_t st);
+
+}  // namespace gs

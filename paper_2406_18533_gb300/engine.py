@@ -1,0 +1,300 @@
+"""PyTorch glue around libgs: device memory (torch tensors), streams, and a
+``torch.autograd.Function`` whose backward is the library's hand-written
+backward kernels.  No arithmetic of the method happens here; every step runs
+in libgs's CUDA kernels through the C ABI (``binding``).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check_f32(t: torch.Tensor, name: str):
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+
+
+@dataclasses.dataclass
+class DeviceScene:
+    """Parameter planes (or gradients / Adam moments) on the GPU."""
+    mo: torch.Tensor      # [N, 4]
+    ls: torch.Tensor      # [N, 4]
+    q: torch.Tensor       # [N, 4]
+    sh: torch.Tensor      # [12, N, 4]
+    sh_degree: int = 3
+
+    @property
+    def N(self) -> int:
+        return int(self.mo.shape[0])
+
+    @classmethod
+    def from_host(cls, sc, device="cuda", pin=False):
+        f = (lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device, non_blocking=pin))
+        return cls(f(sc.mo), f(sc.ls), f(sc.q), f(sc.sh), sc.sh_degree)
+
+    @classmethod
+    def zeros(cls, N, device="cuda", sh_degree=3):
+        z = lambda *s: torch.zeros(*s, dtype=torch.float32, device=device)
+        return cls(z(N, 4), z(N, 4), z(N, 4), z(12, N, 4), sh_degree)
+
+    def zeros_like(self):
+        return DeviceScene.zeros(self.N, self.mo.device, self.sh_degree)
+
+    def struct(self) -> B.gs_scene:
+        for n in ("mo", "ls", "q", "sh"):
+            _check_f32(getattr(self, n), n)
+        return B.gs_scene(_ptr(self.mo), _ptr(self.ls), _ptr(self.q), _ptr(self.sh), self.N, self.sh_degree, 0)
+
+    def flat(self) -> torch.Tensor:
+        """[N, 60] copy in the (mo, ls, q, sh) float order."""
+        return torch.cat([self.mo, self.ls, self.q, self.sh.permute(1, 0, 2).reshape(self.N, 48)], 1)
+
+    def clone(self):
+        return DeviceScene(self.mo.clone(), self.ls.clone(), self.q.clone(), self.sh.clone(), self.sh_degree)
+
+
+@dataclasses.dataclass
+class Proj:
+    xy: torch.Tensor       # [B, N, 2]
+    conic_o: torch.Tensor  # [B, N, 4]
+    rgb_d: torch.Tensor    # [B, N, 4]
+    radius: torch.Tensor   # [B, N] int32
+
+    @classmethod
+    def empty(cls, Bv, N, device="cuda"):
+        e = lambda *s, dt=torch.float32: torch.empty(*s, dtype=dt, device=device)
+        return cls(e(Bv, N, 2), e(Bv, N, 4), e(Bv, N, 4), e(Bv, N, dt=torch.int32))
+
+    def struct(self) -> B.gs_proj:
+        Bv, N = self.radius.shape
+        return B.gs_proj(_ptr(self.xy), _ptr(self.conic_o), _ptr(self.rgb_d), _ptr(self.radius), N, Bv, 0)
+
+
+@dataclasses.dataclass
+class ProjGrad:
+    d_xy_o: torch.Tensor   # [B, N, 4]
+    d_conic: torch.Tensor
+    d_rgb: torch.Tensor
+
+    @classmethod
+    def empty(cls, Bv, N, device="cuda"):
+        e = lambda: torch.empty(Bv, N, 4, dtype=torch.float32, device=device)
+        return cls(e(), e(), e())
+
+    def struct(self) -> B.gs_proj_grad:
+        return B.gs_proj_grad(_ptr(self.d_xy_o), _ptr(self.d_conic), _ptr(self.d_rgb))
+
+
+@dataclasses.dataclass
+class Bins:
+    keys: torch.Tensor     # [cap] int64 (uint64 bits)
+    vals: torch.Tensor     # [cap] int32 (uint32 bits)
+    ranges: torch.Tensor   # [tiles, 2] int32 (uint32 bits)
+    count: torch.Tensor    # [1] int32
+    F: int = 0
+
+    @classmethod
+    def empty(cls, cap, tiles, device="cuda"):
+        return cls(torch.empty(max(cap, 1), dtype=torch.int64, device=device),
+                   torch.empty(max(cap, 1), dtype=torch.int32, device=device),
+                   torch.zeros(max(tiles, 1), 2, dtype=torch.int32, device=device),
+                   torch.zeros(1, dtype=torch.int32, device=device))
+
+    @property
+    def capacity(self) -> int:
+        return int(self.keys.shape[0])
+
+    def struct(self) -> B.gs_bins:
+        return B.gs_bins(_ptr(self.keys), _ptr(self.vals), _ptr(self.ranges), _ptr(self.count), self.capacity)
+
+
+def total_tiles(cams, tile):
+    return sum(((c.W + tile - 1) // tile) * ((c.H + tile - 1) // tile) for c in cams)
+
+
+class Context:
+    """One libgs context (hyperparameters + scratch), used from one stream."""
+
+    def __init__(self, **hparams):
+        self.hp = B.default_hparams(**hparams)
+        h = ctypes.c_void_p()
+        B.call("gs_create", ctypes.byref(h), ctypes.byref(self.hp))
+        self.h = h
+        self._bins_cap = 0
+
+    def close(self):
+        if self.h:
+            B.lib().gs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def tile(self) -> int:
+        return int(self.hp.tile)
+
+    def set_hparams(self, **kw):
+        for k, v in kw.items():
+            if k in ("bg", "lr"):
+                arr = getattr(self.hp, k)
+                for i, x in enumerate(v):
+                    arr[i] = float(x)
+            else:
+                setattr(self.hp, k, v)
+        B.call("gs_set_hparams", self.h, ctypes.byref(self.hp), ctx=self.h)
+
+    def _c(self, name, *args):
+        return B.call(name, *args, ctx=self.h)
+
+    # ---------------------------------------------------------------- steps
+    def preprocess(self, scene: DeviceScene, cams, out: Proj | None = None) -> Proj:
+        out = out or Proj.empty(len(cams), scene.N, scene.mo.device)
+        cs = B.camera_array(cams)
+        s, p = scene.struct(), out.struct()
+        self._c("gs_preprocess", self.h, ctypes.byref(s), cs, len(cams), ctypes.byref(p), _stream())
+        return out
+
+    def bin(self, proj: Proj, cams, capacity: int | None = None) -> Bins:
+        tiles = total_tiles(cams, self.tile)
+        cap = capacity if capacity is not None else max(self._bins_cap, 1 << 16)
+        while True:
+            bins = Bins.empty(cap, tiles, proj.xy.device)
+            needed = ctypes.c_uint64(0)
+            ps, bs = proj.struct(), bins.struct()
+            st = B.lib().gs_bin(self.h, ctypes.byref(ps), B.camera_array(cams), len(cams), ctypes.byref(bs),
+                                ctypes.byref(needed), _stream())
+            if st == B.GS_ERR_CAPACITY and capacity is None:
+                self.status()      # clear the device status word
+                cap = int(needed.value * 1.25) + 1024
+                continue
+            if st != B.GS_OK:
+                raise B.GSError("gs_bin", st, B.lib().gs_last_error(self.h).decode())
+            bins.F = int(needed.value)
+            self._bins_cap = max(self._bins_cap, cap)
+            return bins
+
+    def render_fwd(self, proj: Proj, bins: Bins, cams):
+        Bv = len(cams)
+        H, W = cams[0].H, cams[0].W
+        dev = proj.xy.device
+        img = torch.empty(Bv, 3, H, W, dtype=torch.float32, device=dev)
+        T = torch.empty(Bv, H, W, dtype=torch.float32, device=dev)
+        nc = torch.empty(Bv, H, W, dtype=torch.int32, device=dev)
+        ps, bs = proj.struct(), bins.struct()
+        self._c("gs_render_fwd", self.h, ctypes.byref(ps), ctypes.byref(bs), B.camera_array(cams), Bv, _ptr(img),
+                _ptr(T), _ptr(nc), _stream())
+        return img, T, nc
+
+    def render_bwd(self, proj: Proj, bins: Bins, cams, T, nc, dimg) -> ProjGrad:
+        _check_f32(dimg, "d_img")
+        Bv, N = proj.radius.shape
+        g = ProjGrad.empty(Bv, N, proj.xy.device)
+        ps, bs, gs = proj.struct(), bins.struct(), g.struct()
+        self._c("gs_render_bwd", self.h, ctypes.byref(ps), ctypes.byref(bs), B.camera_array(cams), Bv, _ptr(T),
+                _ptr(nc), _ptr(dimg), ctypes.byref(gs), _stream())
+        return g
+
+    def preprocess_bwd(self, scene: DeviceScene, cams, proj: Proj, pg: ProjGrad, out: DeviceScene | None = None):
+        out = out or scene.zeros_like()
+        s, p, g, o = scene.struct(), proj.struct(), pg.struct(), out.struct()
+        self._c("gs_preprocess_bwd", self.h, ctypes.byref(s), B.camera_array(cams), len(cams), ctypes.byref(p),
+                ctypes.byref(g), ctypes.byref(o), _stream())
+        return out
+
+    def loss(self, img: torch.Tensor, target: torch.Tensor):
+        _check_f32(img, "img")
+        _check_f32(target, "target")
+        Bv, _, H, W = img.shape
+        loss = torch.empty(Bv, dtype=torch.float32, device=img.device)
+        dimg = torch.empty_like(img)
+        self._c("gs_loss", self.h, _ptr(img), _ptr(target), Bv, W, H, _ptr(loss), _ptr(dimg), _stream())
+        return loss, dimg
+
+    def adam_step(self, p: DeviceScene, g: DeviceScene, m: DeviceScene, v: DeviceScene, step: int, batch: int):
+        sp, sg, sm, sv = p.struct(), g.struct(), m.struct(), v.struct()
+        self._c("gs_adam_step", self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm), ctypes.byref(sv),
+                int(step), int(batch), _stream())
+
+    def train_step(self, p, g, m, v, step, cams, targets, loss_out=None, cam_arr=None):
+        Bv = len(cams)
+        loss_out = loss_out if loss_out is not None else torch.empty(Bv, dtype=torch.float32, device=targets.device)
+        sp, sg, sm, sv = p.struct(), g.struct(), m.struct(), v.struct()
+        self._c("gs_train_step", self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm), ctypes.byref(sv),
+                int(step), cam_arr if cam_arr is not None else B.camera_array(cams), Bv, _ptr(targets),
+                _ptr(loss_out), _stream())
+        return loss_out
+
+    def render(self, scene: DeviceScene, cams, imgs=None, cam_arr=None):
+        if imgs is None:
+            imgs = [torch.empty(3, c.H, c.W, dtype=torch.float32, device=scene.mo.device) for c in cams]
+        arr = (ctypes.c_void_p * len(cams))(*[t.data_ptr() for t in imgs])
+        s = scene.struct()
+        self._c("gs_render", self.h, ctypes.byref(s), cam_arr if cam_arr is not None else B.camera_array(cams),
+                len(cams), arr, _stream())
+        return imgs
+
+    def reserve(self, N, cams, frag_capacity):
+        self._c("gs_reserve", self.h, int(N), B.camera_array(cams), len(cams), int(frag_capacity))
+
+    # ---------------------------------------------------------------- status
+    def status(self):
+        code = ctypes.c_int32(0)
+        needed = ctypes.c_uint64(0)
+        self._c("gs_get_status", self.h, _stream(), ctypes.byref(code), ctypes.byref(needed))
+        return int(code.value), int(needed.value)
+
+    def counters(self):
+        out = (ctypes.c_uint64 * 3)()
+        self._c("gs_get_counters", self.h, _stream(), out)
+        return dict(F=int(out[0]), evals_fwd=int(out[1]), evals_bwd=int(out[2]))
+
+
+class RasterizeGaussians(torch.autograd.Function):
+    """image[B,3,H,W] = render(params) with a hand-written backward.
+
+    Forward: gs_preprocess -> gs_bin -> gs_render_fwd.  Saved for backward:
+    the per-(view, Gaussian) screen-space state, the sorted fragments and the
+    per-pixel T_final / n_contrib; no per-fragment state.  Backward:
+    gs_render_bwd -> gs_preprocess_bwd (mean over the views)."""
+
+    @staticmethod
+    def forward(ctx, mo, ls, q, sh, gsctx: Context, cams, sh_degree: int):
+        if len(cams) != 1:
+            raise ValueError("the autograd path renders one view; batches go through Context.train_step")
+        scene = DeviceScene(mo.detach().contiguous(), ls.detach().contiguous(), q.detach().contiguous(),
+                            sh.detach().contiguous(), sh_degree)
+        proj = gsctx.preprocess(scene, cams)
+        bins = gsctx.bin(proj, cams)
+        img, T, nc = gsctx.render_fwd(proj, bins, cams)
+        ctx.gsctx, ctx.cams, ctx.scene, ctx.proj, ctx.bins = gsctx, cams, scene, proj, bins
+        ctx.save_for_backward(T, nc)
+        return img
+
+    @staticmethod
+    def backward(ctx, dimg):
+        T, nc = ctx.saved_tensors
+        pg = ctx.gsctx.render_bwd(ctx.proj, ctx.bins, ctx.cams, T, nc, dimg.contiguous())
+        g = ctx.gsctx.preprocess_bwd(ctx.scene, ctx.cams, ctx.proj, pg)
+        return g.mo, g.ls, g.q, g.sh, None, None, None
+
+
+def rasterize(scene_tensors, gsctx: Context, cams, sh_degree=3):
+    mo, ls, q, sh = scene_tensors
+    return RasterizeGaussians.apply(mo, ls, q, sh, gsctx, tuple(cams), sh_degree)

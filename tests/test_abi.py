@@ -1,0 +1,93 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/gs.h declares; the ctypes mirror of every struct has the C size.
+No compute call is made (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libgs():
+    from paper_2406_18533_gb300 import build, binding
+    build.build()
+    return binding.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:gs_status|const char \*|int32_t|uint64_t)\s*\*?\s*(gs_\w+)\s*\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported(libgs):
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(libgs, n), n
+
+
+def test_binding_covers_every_entry_point(libgs):
+    from paper_2406_18533_gb300 import binding
+    assert set(_declared()) == set(binding.SIGNATURES)
+
+
+def test_abi_version_and_defaults(libgs):
+    from paper_2406_18533_gb300 import binding
+    assert libgs.gs_abi_version() == 1
+    hp = binding.default_hparams()
+    assert hp.tile == 16 and hp.smem_batch == 256
+    assert abs(hp.alpha_min - 1 / 255) < 1e-9 and abs(hp.alpha_max - 0.99) < 1e-7 and abs(hp.T_min - 1e-4) < 1e-10
+    assert hp.scale_lr_sqrt_b == 1 and hp.scale_beta_pow_b == 1 and abs(hp.lambda_dssim - 0.2) < 1e-7
+
+
+def test_struct_layout_matches_c(tmp_path):
+    """sizeof and every field offset of the ctypes mirrors equal what gcc
+    computes from include/gs.h."""
+    from paper_2406_18533_gb300 import binding as b
+    structs = [b.gs_camera, b.gs_scene, b.gs_hparams, b.gs_proj, b.gs_proj_grad, b.gs_bins]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs.h"', 'int main(void) {']
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(out[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(out[f"{n}.{f}"]) == getattr(st, f).offset, (n, f)
+    assert ctypes.sizeof(b.gs_camera) == 80
+
+
+def test_invalid_arguments_rejected_on_host(libgs):
+    """Host-side checks return GS_ERR_INVALID_ARG before any CUDA call."""
+    from paper_2406_18533_gb300 import binding as b
+    hp = b.default_hparams(tile=12)
+    h = ctypes.c_void_p()
+    assert libgs.gs_create(ctypes.byref(h), ctypes.byref(hp)) == b.GS_ERR_INVALID_ARG
+    hp = b.default_hparams(smem_batch=100)
+    assert libgs.gs_create(ctypes.byref(h), ctypes.byref(hp)) == b.GS_ERR_INVALID_ARG
+    assert libgs.gs_create(None, None) == b.GS_ERR_INVALID_ARG
+    assert libgs.gs_destroy(None) == b.GS_ERR_INVALID_ARG
+    size = ctypes.c_size_t(0)
+    assert libgs.gs_workspace_size(None, 10, None, 1, 0, ctypes.byref(size)) == b.GS_ERR_INVALID_ARG
+
+
+def test_workspace_size_grows_with_problem(libgs):
+    from paper_2406_18533_gb300 import binding as b, synth
+    cams = b.camera_array([synth.test_camera(64, 48)])
+    s1, s2 = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert libgs.gs_workspace_size(None, 1000, cams, 1, 10000, ctypes.byref(s1)) == 0
+    assert libgs.gs_workspace_size(None, 100000, cams, 1, 10000, ctypes.byref(s2)) == 0
+    assert s2.value > s1.value > 0
