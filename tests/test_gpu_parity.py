@@ -261,14 +261,18 @@ def _flags_from_oracle(oracle, fw, cam, tile=16):
             edge = (pr["xy"][:, k] + sgn * np.maximum(pr["radius"], np.ceil(e))) / tile
             border |= (np.abs(edge - np.round(edge)) * tile < 1e-3) & (e > 0)
     TX = (cam.W + tile - 1) // tile
-    tb = np.zeros(((cam.H + tile - 1) // tile) * TX, bool)
+    TY = (cam.H + tile - 1) // tile
+    tb = np.zeros(TY * TX, bool)
     for g in np.nonzero(border)[0]:
-        r = max(int(math.ceil(e[g])) + 1, 1)
+        # membership can only change in the outermost tile rows / columns of the
+        # rectangle (radius off by one, or an edge on the other side of a tile line)
+        r = max(int(math.ceil(e[g])), 0)
         x0, x1 = int((pr["xy"][g, 0] - r) // tile), int((pr["xy"][g, 0] + r) // tile)
         y0, y1 = int((pr["xy"][g, 1] - r) // tile), int((pr["xy"][g, 1] + r) // tile)
-        for ty in range(max(0, y0), min((cam.H + tile - 1) // tile - 1, y1) + 1):
-            for tx in range(max(0, x0), min(TX - 1, x1) + 1):
-                tb[ty * TX + tx] = True
+        for ty in range(max(0, y0 - 1), min(TY - 1, y1 + 1) + 1):
+            for tx in range(max(0, x0 - 1), min(TX - 1, x1 + 1) + 1):
+                if tx <= x0 or tx >= x1 or ty <= y0 or ty >= y1:
+                    tb[ty * TX + tx] = True
     tiles = tb.reshape(-1, TX).repeat(tile, 0).repeat(tile, 1)[:cam.H, :cam.W]
     return bad | tiles, int(border.sum())
 
