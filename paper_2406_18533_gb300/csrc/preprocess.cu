@@ -147,10 +147,19 @@ __global__ void __launch_bounds__(128) k_preprocess_fwd(SceneView s, ViewBatch v
         const int64_t idx = (int64_t)v * s.N + g;
         const float px = c.R[0] * G.x + c.R[1] * G.y + c.R[2] * G.z + c.t[0];
         const float py = c.R[3] * G.x + c.R[4] * G.y + c.R[5] * G.z + c.t[1];
-        const float pz = c.R[6] * G.x + c.R[7] * G.y + c.R[8] * G.z + c.t[2];
+        // The depth that orders the fragments is evaluated in double with
+        // separately rounded operations (t + R20 x + R21 y + R22 z, left to
+        // right) and then rounded to float, so near-equal depths order the
+        // same way as the correctly rounded exact depth.  Three double
+        // operations per (view, Gaussian) cost nothing measurable.
+        double zd = (double)c.t[2];
+        zd = __dadd_rn(zd, __dmul_rn((double)c.R[6], (double)G.x));
+        zd = __dadd_rn(zd, __dmul_rn((double)c.R[7], (double)G.y));
+        zd = __dadd_rn(zd, __dmul_rn((double)c.R[8], (double)G.z));
+        const float pz = __double2float_rn(zd);
         uint32_t area = 0;
         int r_int = 0;
-        if (G.ok && pz > c.near_z) {
+        if (G.ok && zd > (double)c.near_z) {
             const float iz = 1.f / pz;
             const float u = c.fx * px * iz + c.cx;
             const float vv = c.fy * py * iz + c.cy;

@@ -262,7 +262,7 @@ def _flags_from_oracle(oracle, fw, cam, tile=16):
             border |= (np.abs(edge - np.round(edge)) * tile < 1e-3) & (e > 0)
     TX = (cam.W + tile - 1) // tile
     TY = (cam.H + tile - 1) // tile
-    tb = np.zeros(TY * TX, bool)
+    tiles_px = np.zeros((cam.H, cam.W), bool)
     for g in np.nonzero(border)[0]:
         # membership can only change in the outermost tile rows / columns of the
         # rectangle (radius off by one, or an edge on the other side of a tile line)
@@ -272,9 +272,15 @@ def _flags_from_oracle(oracle, fw, cam, tile=16):
         for ty in range(max(0, y0 - 1), min(TY - 1, y1 + 1) + 1):
             for tx in range(max(0, x0 - 1), min(TX - 1, x1 + 1) + 1):
                 if tx <= x0 or tx >= x1 or ty <= y0 or ty >= y1:
-                    tb[ty * TX + tx] = True
-    tiles = tb.reshape(-1, TX).repeat(tile, 0).repeat(tile, 1)[:cam.H, :cam.W]
-    return bad | tiles, int(border.sum())
+                    # only pixels where this Gaussian could reach half the alpha cut
+                    ys = np.arange(ty * tile, min(cam.H, (ty + 1) * tile)) + 0.5 - pr["xy"][g, 1]
+                    xs = np.arange(tx * tile, min(cam.W, (tx + 1) * tile)) + 0.5 - pr["xy"][g, 0]
+                    DX, DY = np.meshgrid(xs, ys)
+                    a, b, c, o = pr["conic_o"][g]
+                    reach = o * np.exp(-0.5 * (a * DX * DX + c * DY * DY) - b * DX * DY) >= 0.5 / 255
+                    sub = tiles_px[ty * tile:ty * tile + DX.shape[0], tx * tile:tx * tile + DX.shape[1]]
+                    sub |= reach
+    return bad | tiles_px, int(border.sum())
 
 
 def test_end_to_end_c0_autograd(eng, oracle):
@@ -396,11 +402,15 @@ def test_train_step_c1_full_size(eng, oracle):
     lr6 = (1.6e-4 * 70, 5e-3, 1e-3, 5e-2, 2.5e-3, 2.5e-4)
     ctx = eng.Context(lr=lr6)
     P = eng.DeviceScene.from_host(sc)
+    img0 = ctx.render(P, cams)[0].cpu().numpy()
     G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
     loss = ctx.train_step(P, G, M, V, 1, cams, torch.from_numpy(tg).cuda())
     torch.cuda.synchronize()
     assert ctx.status()[0] == 0
     fw = oracle.render(sc, cams[0])
+    flag, nborder = _flags_from_oracle(oracle, fw, cams[0])
+    assert flag.mean() < 0.05, (flag.mean(), nborder)
+    assert np.abs(img0 - fw["img"])[:, ~flag].max() <= IMG_TOL
     L, dimg, _, _ = oracle.ssim_loss(fw["img"], tg[0])
     assert abs(float(loss[0]) - L) < 1e-4 * abs(L)
     pr = fw["proj"]
@@ -410,6 +420,8 @@ def test_train_step_c1_full_size(eng, oracle):
     groups = dict(mean=slice(0, 3), opacity=slice(3, 4), scale=slice(4, 7), quat=slice(8, 12),
                   sh_dc=slice(12, 15), sh_rest=slice(15, 60))
     for name, s in groups.items():
-        assert rel_l2(grad[:, s], ref[:, s]) < 5 * GRAD_TOL, name
+        err = rel_l2(grad[:, s], ref[:, s])
+        print(f"C1 {name} rel-L2 {err:.2e}")
+        assert err < GRAD_TOL, name
     m = M.flat().cpu().numpy()
     assert rel_l2(m, 0.1 * grad) < 1e-6
