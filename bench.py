@@ -361,7 +361,41 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def ncu_summary(path, steps=None):
+    """Per-kernel launches, total device time and share from an ncu CSV
+    launch list (gpu__time_duration.sum); prints a markdown table."""
+    import csv
+    import re
+    rows = []
+    with open(path) as f:
+        lines = [l for l in f if l.startswith('"')]
+    for r in csv.DictReader(lines):
+        if r.get("Metric Name") != "gpu__time_duration.sum":
+            continue
+        name = re.sub(r"\(.*", "", r["Kernel Name"]).replace("void ", "")
+        name = re.sub(r"gs::\(anonymous namespace\)::", "", name)
+        ns = float(r["Metric Value"].replace(",", ""))
+        if r.get("Metric Unit") == "us":
+            ns *= 1e3
+        elif r.get("Metric Unit") == "ms":
+            ns *= 1e6
+        rows.append((name, ns))
+    tot = sum(ns for _, ns in rows)
+    agg = {}
+    for n, ns in rows:
+        a = agg.setdefault(n, [0, 0.0])
+        a[0] += 1
+        a[1] += ns
+    print("| kernel | launches | total ms | share |")
+    print("|---|---:|---:|---:|")
+    for n, (c, ns) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        print(f"| `{n}` | {c} | {ns / 1e6:.3f} | {100 * ns / tot:.1f}% |")
+    print(f"| total | {len(rows)} | {tot / 1e6:.3f} | 100% |")
+
+
 def main():
+    if len(sys.argv) >= 3 and sys.argv[1] == "--ncu-summary":
+        return ncu_summary(sys.argv[2])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
