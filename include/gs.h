@@ -204,6 +204,31 @@ gs_status gs_bin(gs_ctx *ctx, const gs_proj *proj, const gs_camera *cams, int32_
                  uint64_t *needed_host, void *stream);
 
 /*
+ * gs_bin_noalloc: the binning of gs_bin (tile counts, scan, key emission,
+ * radix sort, tile ranges) without any device memory allocation.  The paper
+ * has no counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: code that owns a fixed device-memory budget handed out by a
+ * host application's own allocator, latency-critical loops that cannot
+ * afford cudaMalloc/cudaFree (both synchronise the device), and callers
+ * without a gs_ctx (creating one allocates).
+ *
+ * All scratch lives in one static device array of 14.5 MiB that every GPU on
+ * which the library's kernels are loaded holds until the process exits.
+ * Limits: B * proj->N <= 262144 (view, Gaussian) pairs and out->capacity <=
+ * 1048576 fragments; larger sizes, an unsupported tile (8, 16, 32) or a bad
+ * pointer return GS_ERR_INVALID_ARG before any work.  Inputs and outputs are
+ * the caller's, exactly as for gs_bin; a capacity overflow is handled as in
+ * gs_bin (nothing written past capacity; with needed_host the call
+ * synchronises the stream and returns GS_ERR_CAPACITY with the needed count).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current), so make that first call before any
+ * stream capture.  Every call uses the same array: calls that overlap on the
+ * GPU (other streams, other threads) race and corrupt each other's results.
+ */
+gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, int32_t B, int32_t tile, gs_bins *out,
+                         uint64_t *needed_host, void *stream);
+
+/*
  * Sec. 2.1 step 2, second half: per pixel, front-to-back alpha compositing
  * over its tile's sorted list until transmittance would fall below T_min.
  * img: [B][3][H][W] float; T_final: [B][H][W] float; n_contrib: [B][H][W]

@@ -85,7 +85,10 @@ SIGNATURES = {
     "gs_trace_enable": [_vp, _i32],
     "gs_trace_read": [_vp, P(ctypes.c_float), P(_i32)],
     "gs_kernel_launches": [],
+    "gs_bin_noalloc": [P(gs_proj), P(gs_camera), _i32, _i32, P(gs_bins), P(ctypes.c_uint64), _vp],
 }
+NOALLOC_MAX_PAIRS = 1 << 18
+NOALLOC_MAX_FRAGS = 1 << 20
 GS_TRACE_STAGES = 11
 TRACE_STAGES = ("preprocess", "scan", "emit", "sort", "ranges", "blend_fwd", "loss", "zero_grad", "blend_bwd",
                 "preprocess_bwd", "adam")
