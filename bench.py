@@ -190,16 +190,19 @@ def stage_roofline(stage, ms, counters, N, Bv, pixels, passes, peaks, clock_mhz)
     """Algorithmic work of one launch of a stage, and the matching peak."""
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     F, Ef, Eb = counters["F"], counters["evals_fwd"], counters["evals_bwd"]
+    Wb = counters.get("walked_bwd", Eb)
     alu_peak = N_SM * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     sec = ms * 1e-3
+    # FP32 flops of the method per (pixel, list position) examined and per
+    # blended (pixel, Gaussian) pair; an FMA counts 2, the exponential 1
     if stage == "blend_bwd":
-        work = 70.0 * Eb
+        work = 7.0 * Wb + 50.0 * Eb
         return dict(bound="alu", achieved=work / sec / 1e12, peak=alu_peak, unit="TFLOP/s",
-                    work_desc=f"70 FP32 flop x {Eb} backward (pixel, fragment) evaluations")
+                    work_desc=f"7 flop x {Wb} walked (pixel, position) + 50 flop x {Eb} blended pairs")
     if stage == "blend_fwd":
-        work = 22.0 * Ef
+        work = 7.0 * Ef + 14.0 * Eb
         return dict(bound="alu", achieved=work / sec / 1e12, peak=alu_peak, unit="TFLOP/s",
-                    work_desc=f"22 FP32 flop x {Ef} forward (pixel, fragment) evaluations")
+                    work_desc=f"7 flop x {Ef} evaluated (pixel, position) + 14 flop x {Eb} blended pairs")
     if stage == "sort":
         byt = passes * F * 24.0
     elif stage == "adam":
@@ -403,7 +406,7 @@ def main():
     ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -84,7 +84,8 @@ typedef struct gs_scene {
 /* Hyperparameters (host struct, copied into the context). */
 typedef struct gs_hparams {
     int32_t tile;             /* screen tile edge: 8, 16 (paper's 16x16 blocks) or 32 */
-    int32_t smem_batch;       /* Gaussians staged per shared-memory batch: 128, 256 or 512 */
+    int32_t smem_batch;       /* list entries a warp stages per shared-memory refill: 32, 64
+                                 or 128 (tile 32: 32 or 64) */
     int32_t strict_nonfinite; /* 1: report GS_ERR_NONFINITE; 0: cull silently */
     float alpha_min;          /* skip a Gaussian at a pixel below this alpha (1/255) */
     float alpha_max;          /* alpha is clamped to this (0.99) */
@@ -158,10 +159,12 @@ gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *ca
  * fragment count the last binning asked for. */
 gs_status gs_get_status(gs_ctx *ctx, void *stream, int32_t *status, uint64_t *needed);
 
-/* Counters of the last forward / backward render (device, read after sync):
- * out[0] = fragments F, out[1] = (pixel, fragment) evaluations in the forward,
- * out[2] = (pixel, fragment) evaluations in the backward. */
-gs_status gs_get_counters(gs_ctx *ctx, void *stream, uint64_t out[3]);
+/* Counters of the last binning / forward / backward render (synchronises):
+ * out[0] = fragments F, out[1] = (pixel, fragment) evaluations in the
+ * forward, out[2] = (pixel, Gaussian) pairs blended in the backward,
+ * out[3] = (pixel, list position) pairs the backward walked, out[4] =
+ * Gaussians culled for non-finite parameters (cumulative). */
+gs_status gs_get_counters(gs_ctx *ctx, void *stream, uint64_t out[5]);
 
 /*
  * Tracing (profiling aid, no paper counterpart): when enabled with

@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, ProjView p, con
         status->counters[0] = F;
         status->counters[1] = 0ull;
         status->counters[2] = 0ull;
+        status->counters[4] = 0ull;
         if (F > capacity) {
             atomicCAS(&status->code, 0, (int)GS_ERR_CAPACITY);
             *count_out = 0u;

@@ -308,8 +308,8 @@ AdamArgs adam_args(const gs_hparams &hp, int64_t step, int32_t B)
 gs_status check_hparams(gs_ctx *c, const gs_hparams *hp)
 {
     if (ilog2_exact(hp->tile) < 0) return fail(c, GS_ERR_INVALID_ARG, "tile must be 8, 16 or 32");
-    if (hp->smem_batch != 128 && hp->smem_batch != 256 && hp->smem_batch != 512)
-        return fail(c, GS_ERR_INVALID_ARG, "smem_batch must be 128, 256 or 512");
+    if (!blend_config_ok(hp->tile, hp->smem_batch))
+        return fail(c, GS_ERR_INVALID_ARG, "smem_batch must be 32, 64 or 128 (32 or 64 with tile 32)");
     if (!(hp->alpha_max > 0.f && hp->alpha_max < 1.f) || !(hp->alpha_min >= 0.f) || !(hp->T_min >= 0.f))
         return fail(c, GS_ERR_INVALID_ARG, "blend thresholds out of range");
     return GS_OK;
@@ -363,7 +363,7 @@ gs_status gs_default_hparams(gs_hparams *hp)
     if (!hp) return GS_ERR_INVALID_ARG;
     memset(hp, 0, sizeof *hp);
     hp->tile = 16;
-    hp->smem_batch = 256;
+    hp->smem_batch = 64;
     hp->strict_nonfinite = 0;
     hp->alpha_min = 1.0f / 255.0f;
     hp->alpha_max = 0.99f;
@@ -446,14 +446,18 @@ gs_status gs_get_status(gs_ctx *c, void *stream, int32_t *status, uint64_t *need
     return GS_OK;
 }
 
-gs_status gs_get_counters(gs_ctx *c, void *stream, uint64_t out[3])
+gs_status gs_get_counters(gs_ctx *c, void *stream, uint64_t out[5])
 {
     if (!c || !out) return GS_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
     if (cudaMemcpyAsync(c->h_status, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return cuda_check(c, "gs_get_counters");
-    for (int i = 0; i < 3; ++i) out[i] = c->h_status->counters[i];
+    out[0] = c->h_status->counters[0];
+    out[1] = c->h_status->counters[1];
+    out[2] = c->h_status->counters[2];
+    out[3] = c->h_status->counters[4];
+    out[4] = c->h_status->counters[3];
     return GS_OK;
 }
 
@@ -665,7 +669,8 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     if (r != GS_OK) return r;
     set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
     const BlendParams bp = blend_of(c->hp);
-    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->status, st);
+    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch,
+                     c->status, st);
     mark(c, st, 6);
     launch_loss(ptr<float>(c->img), targets, B, vb.v[0].W, vb.v[0].H, c->hp.lambda_dssim, loss_out,
                 ptr<float>(c->dimg), ptr<float>(c->maps), ptr<double>(c->acc), st);
@@ -678,7 +683,8 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     }
     mark(c, st, 8);
     const GradView gv{ptr<float4>(c->g_xy), ptr<float4>(c->g_co), ptr<float4>(c->g_rgb)};
-    launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, gv, c->status, st);
+    launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch,
+                     gv, c->status, st);
     mark(c, st, 9);
     launch_preprocess_bwd(sv, vb, pv, gv, mut_of(g), st);
     mark(c, st, 10);

@@ -69,7 +69,9 @@ struct DevStatus {
     int32_t code;          // first gs_status error, 0 = OK
     int32_t pad;
     unsigned long long needed;  // fragments requested by the last binning
-    unsigned long long counters[4];  // F, fwd evaluations, bwd evaluations, culled non-finite
+    // F, forward (pixel, fragment) evaluations, backward blended pairs,
+    // Gaussians culled as non-finite, backward walked (pixel, position) pairs
+    unsigned long long counters[6];
 };
 
 // Process-wide count of kernel launches (incremented by every launcher).
@@ -100,11 +102,13 @@ void launch_radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint3
 void launch_tile_ranges(const uint64_t *keys, const uint32_t *count, uint64_t capacity, uint2 *ranges,
                         uint32_t total_tiles, cudaStream_t st);
 
-// batch: Gaussians staged per shared-memory batch (128, 256 or 512).
+// chunk: list entries a warp gathers and filters per shared-memory refill
+// (blend_config_ok says which (tile, chunk) pairs are built).
+bool blend_config_ok(int tile, int chunk);
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                      const BlendParams &bp, int batch, DevStatus *status, cudaStream_t st);
+                      const BlendParams &bp, int chunk, DevStatus *status, cudaStream_t st);
 void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                      const BlendParams &bp, int batch, const GradView &g, DevStatus *status, cudaStream_t st);
+                      const BlendParams &bp, int chunk, const GradView &g, DevStatus *status, cudaStream_t st);
 
 void launch_loss(const float *img, const float *target, int B, int W, int H, float lambda, float *loss_out,
                  float *d_img, float *maps, double *acc, cudaStream_t st);

@@ -1,17 +1,23 @@
 // K6 (front-to-back compositing, Sec. 2.1 step 2) and K7 (its backward).
 //
-// One CTA per screen tile (tile x tile pixels, one pixel per thread).  The
-// tile's depth-sorted fragment list is walked in batches of BATCH Gaussians
-// staged into shared memory (coalesced 8/16-byte gathers of the screen-space
-// state), so every Gaussian is read from global memory once per tile.
-// Forward: a warp stops iterating once all of its pixels have saturated, and
-// the CTA stops fetching batches once __syncthreads_count says every pixel
-// has (early termination on transmittance).
-// Backward: walks the same list back to front from the tile's largest
-// n_contrib, recovers the transmittance before each contributor by division
-// from T_final (no per-fragment state is stored), reduces the nine gradient
-// components across the warp with shuffles, and issues three float4 atomics
-// per (warp, Gaussian) instead of 9 scalar atomics per (pixel, Gaussian).
+// One CTA per screen tile of TILE x TILE pixels, one pixel per thread; warp w
+// owns an 8 x 4 block of the tile.  Warps work independently (no block-wide
+// barrier inside the walk): a warp refills its own chunk of CH entries of the
+// tile's depth-sorted list (lane i gathers entry i with coalesced 8/16-byte
+// loads; the warps of a tile hit the same L1 lines), keeps only the Gaussians
+// whose alpha >= alpha_min ellipse meets the warp's block (ballot + prefix
+// compaction into the warp's slice of shared memory, order preserved), and
+// walks those.  So a warp spends nothing on list entries that cannot reach its
+// pixels, and finishes as soon as its own pixels do.  The staged record holds
+// the exponent below which alpha < alpha_min, so most (pixel, Gaussian) pairs
+// are rejected before the exponential.
+// Forward: a lane stops once its pixel saturates; the warp stops refilling
+// when all its lanes have (early termination on transmittance).
+// Backward: each warp walks back to front from its own largest n_contrib,
+// recovers the transmittance before each contributor by division from
+// T_final (no per-fragment state is stored), reduces a Gaussian's nine
+// gradient components over the warp with a reduce-scatter (14 shuffles) and
+// adds them with one 9-lane atomic instruction per (warp, Gaussian).
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -19,24 +25,55 @@ namespace {
 
 constexpr float LOG2E = 1.4426950408889634f;
 
-struct SmemG {        // one staged Gaussian (forward)
-    float2 xy;
-    float4 q;         // (-a/2, -b, -c/2) * log2(e), opacity
-    float4 rgb;
-};
-
-// Exponent (base 2) of the Gaussian at offset (dx, dy); written with explicit
-// round-to-nearest operations so the forward and the backward evaluate it to
-// the same bits whatever the compiler fuses around it.
+// Base-2 exponent of the Gaussian at offset (dx, dy), evaluated as
+// dy (C dy + B dx) + A dx^2 with explicitly rounded operations, so the
+// forward and the backward get the same bits whatever the compiler fuses
+// around it; q = (A, B, C, o) = (-a/2, -b, -c/2) log2(e), opacity.
 __device__ __forceinline__ float power2(const float4 &q, float dx, float dy)
 {
-    const float dxdx = __fmul_rn(dx, dx), dydy = __fmul_rn(dy, dy), dxdy = __fmul_rn(dx, dy);
-    return __fmaf_rn(q.x, dxdx, __fmaf_rn(q.z, dydy, __fmul_rn(q.y, dxdy)));
+    const float adx2 = __fmul_rn(q.x, __fmul_rn(dx, dx));
+    const float bdx = __fmul_rn(q.y, dx);
+    return __fmaf_rn(dy, __fmaf_rn(q.z, dy, bdx), adx2);
+}
+
+__device__ __forceinline__ float ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 __device__ __forceinline__ float4 stage_q(const float4 &co)
 {
     return make_float4(-0.5f * LOG2E * co.x, -LOG2E * co.y, -0.5f * LOG2E * co.z, co.w);
+}
+
+// Below this exponent o * 2^pw < alpha_min: the exponential need not be taken.
+// Forward and backward use the same cut, so their decisions agree exactly.
+__device__ __forceinline__ float exponent_cut(float o, float alpha_min)
+{
+    return o > alpha_min ? __log2f(__fdividef(alpha_min, o)) : 1.f;
+}
+
+// Does the ellipse {d : d^T Q d <= 2 ln(o / alpha_min)} around (u, v) -- the
+// only offsets at which alpha can reach alpha_min -- meet the pixel-centre
+// box [x0, x1] x [y0, y1]?  Its bounding half-widths are sqrt(2 L Q^-1_xx)
+// and sqrt(2 L Q^-1_yy), padded (0.1 % + 0.05 px) so float rounding never
+// drops a pixel the per-pixel test would accept; the determinant uses
+// Kahan's form (no cancellation loss); a determinant that rounds to <= 0 keeps
+// the Gaussian.
+__device__ __forceinline__ bool alpha_box_hits(const float4 &co, float u, float v, float alpha_min, float x0,
+                                               float x1, float y0, float y1)
+{
+    if (!(co.w > alpha_min)) return false;                 // never reaches alpha_min
+    const float w = co.y * co.y;
+    const float e = __fmaf_rn(-co.y, co.y, w);
+    const float det = __fmaf_rn(co.x, co.z, -w) + e;
+    if (!(det > 0.f)) return true;
+    const float L2 = 2.f * __logf(co.w / alpha_min);
+    const float rx = sqrtf(L2 * co.z / det) * 1.001f + 0.05f;
+    const float ry = sqrtf(L2 * co.x / det) * 1.001f + 0.05f;
+    return !(u + rx < x0 || u - rx > x1 || v + ry < y0 || v - ry > y1);
 }
 
 __device__ __forceinline__ int find_view(const ViewBatch &vb, uint32_t tile_id)
@@ -46,279 +83,392 @@ __device__ __forceinline__ int find_view(const ViewBatch &vb, uint32_t tile_id)
     return v;
 }
 
-template <int TILE, int BATCH>
+// Sums 8 per-lane values over the warp with a reduce-scatter: at each level
+// a lane keeps half of its values and ships the other half, so the 8 sums
+// take 4 + 2 + 1 + 1 + 1 = 9 shuffles.  On return the lanes with lane % 4 == 0
+// hold the total of value ((lane >> 2) & 7).
+__device__ __forceinline__ float warp_reduce_scatter8(const float v[8], int lane)
+{
+    float w[4], x[2];
+    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float send = b4 ? v[j] : v[j + 4];
+        const float keep = b4 ? v[j + 4] : v[j];
+        w[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float send = b3 ? w[j] : w[j + 2];
+        const float keep = b3 ? w[j + 2] : w[j];
+        x[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const float send = b2 ? x[0] : x[1];
+    float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    return y;
+}
+
+// Tile-local geometry of this thread's pixel and its warp's 8 x 4 block.
+struct PixelSite {
+    int px, py;
+    bool inside;
+    float fx, fy;             // pixel centre
+    float bx0, bx1, by0, by1; // pixel-centre extent of the warp's block
+};
+
+template <int TILE>
+__device__ __forceinline__ PixelSite pixel_site(const ViewCam &c, uint32_t local, int warp, int lane)
+{
+    PixelSite s;
+    const int ty = (int)(local / (uint32_t)c.TX), tx = (int)(local % (uint32_t)c.TX);
+    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 4;
+    s.px = tx * TILE + wx + (lane & 7);
+    s.py = ty * TILE + wy + (lane >> 3);
+    s.inside = s.px < c.W && s.py < c.H;
+    s.fx = (float)s.px + 0.5f;
+    s.fy = (float)s.py + 0.5f;
+    s.bx0 = (float)(tx * TILE + wx) + 0.5f;
+    s.bx1 = s.bx0 + 7.f;
+    s.by0 = (float)(ty * TILE + wy) + 0.5f;
+    s.by1 = s.by0 + 3.f;
+    return s;
+}
+
+// Bytes of dynamic shared memory per CTA.
+template <int TILE, int CH, bool BWD>
+constexpr size_t smem_bytes()
+{
+    return (size_t)(TILE * TILE / 32) * CH * ((BWD ? 4 : 3) * sizeof(float4) + sizeof(uint32_t));
+}
+
+template <int TILE, int CH>
 __global__ void __launch_bounds__(TILE *TILE) k_blend_fwd(ViewBatch vb, ProjView p, const uint32_t *vals,
                                                           const uint2 *ranges, BlendParams bp, DevStatus *status)
 {
-    constexpr int NT = TILE * TILE;
-    __shared__ SmemG sg[BATCH];
-    __shared__ uint32_t s_red[NT / 32];
+    constexpr int NW = TILE * TILE / 32;
+    extern __shared__ float4 smem[];
+    __shared__ uint32_t s_red[NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *s_xyc = smem + warp * CH;              // u, v, exponent cut, -
+    float4 *s_q = smem + (NW + warp) * CH;         // A, B, C, opacity
+    float4 *s_rgb = smem + (2 * NW + warp) * CH;
+    uint32_t *s_pos = reinterpret_cast<uint32_t *>(smem + 3 * NW * CH) + warp * CH;
+
     const uint32_t tile_id = blockIdx.x;
     const int v = find_view(vb, tile_id);
     const ViewCam &c = vb.v[v];
-    const uint32_t local = tile_id - c.tile_base;
-    const int ty = (int)(local / (uint32_t)c.TX), tx = (int)(local % (uint32_t)c.TX);
-    const int px = tx * TILE + (int)(threadIdx.x % TILE);
-    const int py = ty * TILE + (int)(threadIdx.x / TILE);
-    const bool inside = px < c.W && py < c.H;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const PixelSite ps = pixel_site<TILE>(c, tile_id - c.tile_base, warp, lane);
     const uint2 rg = ranges[tile_id];
     const int64_t vbase = (int64_t)v * p.N;
+    const uint32_t lt = (1u << lane) - 1u;
 
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t nc = 0, ne = 0;
-    bool done = !inside;
-    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += BATCH) {
-        if (__syncthreads_count(done) == NT) break;
-        for (int t = threadIdx.x; t < BATCH; t += NT) {
-            const uint32_t j = b0 + t;
+    bool done = !ps.inside;
+    for (uint32_t base = rg.x; base < rg.y; base += CH) {
+        if (__all_sync(0xffffffffu, done)) break;
+        // refill: gather CH entries, keep those that can reach this warp's block
+        int n = 0;
+#pragma unroll
+        for (int r = 0; r < CH; r += 32) {
+            const uint32_t j = base + r + lane;
+            bool hit = false;
+            int64_t idx = 0;
+            float2 xy = make_float2(0.f, 0.f);
+            float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
             if (j < rg.y) {
-                const int64_t idx = vbase + vals[j];
-                SmemG s;
-                s.xy = p.xy[idx];
-                s.q = stage_q(p.conic_o[idx]);
-                s.rgb = p.rgb_d[idx];
-                sg[t] = s;
+                idx = vbase + vals[j];
+                xy = p.xy[idx];
+                co = p.conic_o[idx];
+                hit = alpha_box_hits(co, xy.x, xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
             }
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int slot = n + __popc(bal & lt);
+                const float4 q = stage_q(co);
+                s_xyc[slot] = make_float4(xy.x, xy.y, exponent_cut(q.w, bp.alpha_min), 0.f);
+                s_q[slot] = q;
+                s_rgb[slot] = p.rgb_d[idx];
+                s_pos[slot] = j - rg.x;
+            }
+            n += __popc(bal);
         }
-        __syncthreads();
-        const int cnt = (int)min((uint32_t)BATCH, rg.y - b0);
+        __syncwarp();
         if (!done) {
-            int k = 0;
-            for (; k < cnt; ++k) {
-                const SmemG &s = sg[k];
-                const float dx = __fsub_rn(fx, s.xy.x), dy = __fsub_rn(fy, s.xy.y);
-                const float pw = power2(s.q, dx, dy);
-                if (pw > 0.f) continue;
-                const float alpha = fminf(bp.alpha_max, s.q.w * exp2f(pw));
+            for (int i = 0; i < n; ++i) {
+                const float4 xyc = s_xyc[i];
+                const float4 q = s_q[i];
+                const float pw = power2(q, __fsub_rn(ps.fx, xyc.x), __fsub_rn(ps.fy, xyc.y));
+                if (!(pw >= xyc.z && pw <= 0.f)) continue;      // below the alpha cut, or power > 0
+                const float alpha = fminf(bp.alpha_max, q.w * ex2(pw));
                 if (alpha < bp.alpha_min) continue;
                 const float Tn = T * (1.f - alpha);
                 if (Tn < bp.T_min) {
                     done = true;
+                    ne = s_pos[i] + 1;
                     break;
                 }
+                const float4 rgb = s_rgb[i];
                 const float w = alpha * T;
-                C0 += s.rgb.x * w;
-                C1 += s.rgb.y * w;
-                C2 += s.rgb.z * w;
+                C0 += rgb.x * w;
+                C1 += rgb.y * w;
+                C2 += rgb.z * w;
                 T = Tn;
-                nc = b0 - rg.x + k + 1;
+                nc = s_pos[i] + 1;
             }
-            ne = b0 - rg.x + min(k + 1, cnt);
+            if (!done) ne = min(base + CH, rg.y) - rg.x;
         }
+        __syncwarp();
     }
-    if (inside) {
-        const int64_t pix = (int64_t)py * c.W + px;
+    if (ps.inside) {
         const int64_t hw = (int64_t)c.W * c.H;
+        const int64_t pix = (int64_t)ps.py * c.W + ps.px;
         c.img[pix] = C0 + T * bp.bg[0];
         c.img[hw + pix] = C1 + T * bp.bg[1];
         c.img[2 * hw + pix] = C2 + T * bp.bg[2];
         c.T_final[pix] = T;
         c.n_contrib[pix] = nc;
     }
-    // (pixel, fragment) evaluations for the roofline counters
-    uint32_t s = inside ? ne : 0u;
+    // (pixel, list position) evaluations until termination, for the roofline counters
+    uint32_t evals = ps.inside ? ne : 0u;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
+    if (lane == 0) s_red[warp] = evals;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long tot = 0;
-        for (int w = 0; w < NT / 32; ++w) tot += s_red[w];
+        for (int w = 0; w < NW; ++w) tot += s_red[w];
         if (tot) atomicAdd(&status->counters[1], tot);
     }
 }
 
-struct SmemGB {       // one staged Gaussian (backward)
-    float2 xy;
-    float4 q;         // as forward
-    float4 conic;     // (a, b, c, -)
-    float4 rgb;
-    uint32_t g;
-};
-
-template <int TILE, int BATCH>
+template <int TILE, int CH>
 __global__ void __launch_bounds__(TILE *TILE) k_blend_bwd(ViewBatch vb, ProjView p, const uint32_t *vals,
                                                           const uint2 *ranges, BlendParams bp, GradView gv,
                                                           DevStatus *status)
 {
-    constexpr int NT = TILE * TILE;
-    __shared__ SmemGB sg[BATCH];
-    __shared__ uint32_t s_red[NT / 32];
+    constexpr int NW = TILE * TILE / 32;
+    extern __shared__ float4 smem[];
+    __shared__ unsigned long long s_red64[2][NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *s_xyc = smem + warp * CH;
+    float4 *s_q = smem + (NW + warp) * CH;
+    float4 *s_cn = smem + (2 * NW + warp) * CH;     // a, b, c, -
+    float4 *s_rgb = smem + (3 * NW + warp) * CH;    // r, g, b, Gaussian index (bits)
+    uint32_t *s_pos = reinterpret_cast<uint32_t *>(smem + 4 * NW * CH) + warp * CH;
+
     const uint32_t tile_id = blockIdx.x;
     const int v = find_view(vb, tile_id);
     const ViewCam &c = vb.v[v];
-    const uint32_t local = tile_id - c.tile_base;
-    const int ty = (int)(local / (uint32_t)c.TX), tx = (int)(local % (uint32_t)c.TX);
-    const int px = tx * TILE + (int)(threadIdx.x % TILE);
-    const int py = ty * TILE + (int)(threadIdx.x / TILE);
-    const bool inside = px < c.W && py < c.H;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const PixelSite ps = pixel_site<TILE>(c, tile_id - c.tile_base, warp, lane);
     const uint2 rg = ranges[tile_id];
     const int64_t vbase = (int64_t)v * p.N;
-    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t hw = (int64_t)c.W * c.H;
 
     float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
     uint32_t nc = 0;
-    if (inside) {
-        const int64_t pix = (int64_t)py * c.W + px;
-        const int64_t hw = (int64_t)c.W * c.H;
+    if (ps.inside) {
+        const int64_t pix = (int64_t)ps.py * c.W + ps.px;
         T = c.T_final[pix];
         nc = c.n_contrib[pix];
         dC0 = c.d_img[pix];
         dC1 = c.d_img[hw + pix];
         dC2 = c.d_img[2 * hw + pix];
     }
-    // largest n_contrib in the tile bounds the backward walk
-    uint32_t m = nc;
+    // this warp walks back to front from its own largest n_contrib, never past the list
+    uint32_t wnc = nc;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) s_red[threadIdx.x >> 5] = m;
-    __syncthreads();
-    uint32_t maxnc = 0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) maxnc = max(maxnc, s_red[w]);
-    maxnc = min(maxnc, rg.y - rg.x);   // never walk past the tile's list, whatever n_contrib holds
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) wnc = max(wnc, __shfl_xor_sync(0xffffffffu, wnc, o));
+    wnc = min(wnc, rg.y - rg.x);
 
     float B0 = bp.bg[0], B1 = bp.bg[1], B2 = bp.bg[2];   // colour behind (normalised)
-    uint32_t evals = 0;
-    for (int64_t end = (int64_t)rg.x + maxnc; end > (int64_t)rg.x; end -= BATCH) {
-        const int64_t start = max((int64_t)rg.x, end - BATCH);
-        const int cnt = (int)(end - start);
-        __syncthreads();
-        for (int t = threadIdx.x; t < cnt; t += NT) {
-            const uint32_t j = (uint32_t)(end - 1 - t);
-            const uint32_t g = vals[j];
-            const int64_t idx = vbase + g;
-            const float4 co = p.conic_o[idx];
-            SmemGB s;
-            s.xy = p.xy[idx];
-            s.q = stage_q(co);
-            s.conic = co;
-            s.rgb = p.rgb_d[idx];
-            s.g = g;
-            sg[t] = s;
+    uint32_t evals = 0, walked = 0;
+    for (int64_t end = (int64_t)rg.x + wnc; end > (int64_t)rg.x; end -= CH) {
+        const int64_t start = max((int64_t)rg.x, end - CH);
+        int n = 0;
+#pragma unroll
+        for (int r = 0; r < CH; r += 32) {
+            const int64_t j = end - 1 - r - lane;             // descending list positions
+            bool hit = false;
+            uint32_t g = 0;
+            float2 xy = make_float2(0.f, 0.f);
+            float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j >= start) {
+                g = vals[j];
+                const int64_t idx = vbase + g;
+                xy = p.xy[idx];
+                co = p.conic_o[idx];
+                hit = alpha_box_hits(co, xy.x, xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int slot = n + __popc(bal & lt);
+                const float4 q = stage_q(co);
+                const float4 rgbd = p.rgb_d[vbase + g];
+                s_xyc[slot] = make_float4(xy.x, xy.y, exponent_cut(q.w, bp.alpha_min), 0.f);
+                s_q[slot] = q;
+                s_cn[slot] = co;
+                s_rgb[slot] = make_float4(rgbd.x, rgbd.y, rgbd.z, __uint_as_float(g));
+                s_pos[slot] = (uint32_t)(j - rg.x);
+            }
+            n += __popc(bal);
         }
-        __syncthreads();
-        for (int k = 0; k < cnt; ++k) {
-            const uint32_t rel = (uint32_t)(end - 1 - k - rg.x);
-            const SmemGB &s = sg[k];
+        __syncwarp();
+        for (int i = 0; i < n; ++i) {
+            const uint32_t rel = s_pos[i];
+            const float4 xyc = s_xyc[i];
+            const float4 q = s_q[i];
+            const float dx = __fsub_rn(ps.fx, xyc.x), dy = __fsub_rn(ps.fy, xyc.y);
             bool act = rel < nc;
-            float gu = 0.f, gvv = 0.f, go = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
+            walked += act;
+            const float pw = power2(q, dx, dy);
+            act = act && pw >= xyc.z && pw <= 0.f;
+            float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float gbl = 0.f;
             if (act) {
-                const float dx = __fsub_rn(fx, s.xy.x), dy = __fsub_rn(fy, s.xy.y);
-                const float pw = power2(s.q, dx, dy);
-                const float G = exp2f(pw);
-                const float oG = s.q.w * G;
+                const float G = ex2(pw);
+                const float oG = q.w * G;
                 const float alpha = fminf(bp.alpha_max, oG);
-                act = !(pw > 0.f) && !(alpha < bp.alpha_min);
+                act = !(alpha < bp.alpha_min);
                 if (act) {
                     ++evals;
+                    const float4 rgb = s_rgb[i];
                     const float Tj = __fdividef(T, 1.f - alpha);
                     const float w = alpha * Tj;
-                    gr = w * dC0;
-                    gg = w * dC1;
+                    vv[6] = w * dC0;
+                    vv[7] = w * dC1;
                     gbl = w * dC2;
-                    const float dalpha = Tj * ((s.rgb.x - B0) * dC0 + (s.rgb.y - B1) * dC1 + (s.rgb.z - B2) * dC2);
-                    B0 = alpha * s.rgb.x + (1.f - alpha) * B0;
-                    B1 = alpha * s.rgb.y + (1.f - alpha) * B1;
-                    B2 = alpha * s.rgb.z + (1.f - alpha) * B2;
+                    const float dalpha = Tj * ((rgb.x - B0) * dC0 + (rgb.y - B1) * dC1 + (rgb.z - B2) * dC2);
+                    B0 = alpha * rgb.x + (1.f - alpha) * B0;
+                    B1 = alpha * rgb.y + (1.f - alpha) * B1;
+                    B2 = alpha * rgb.z + (1.f - alpha) * B2;
                     T = Tj;
                     if (oG < bp.alpha_max) {
+                        const float4 cn = s_cn[i];
                         const float dpow = alpha * dalpha;
-                        go = G * dalpha;
-                        gu = (s.conic.x * dx + s.conic.y * dy) * dpow;
-                        gvv = (s.conic.y * dx + s.conic.z * dy) * dpow;
-                        ga = -0.5f * dx * dx * dpow;
-                        gb = -dx * dy * dpow;
-                        gc = -0.5f * dy * dy * dpow;
+                        vv[2] = G * dalpha;
+                        vv[0] = (cn.x * dx + cn.y * dy) * dpow;
+                        vv[1] = (cn.y * dx + cn.z * dy) * dpow;
+                        vv[3] = -0.5f * dx * dx * dpow;
+                        vv[4] = -dx * dy * dpow;
+                        vv[5] = -0.5f * dy * dy * dpow;
                     }
                 }
             }
-            if (__any_sync(0xffffffffu, act)) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    gu += __shfl_xor_sync(0xffffffffu, gu, o);
-                    gvv += __shfl_xor_sync(0xffffffffu, gvv, o);
-                    go += __shfl_xor_sync(0xffffffffu, go, o);
-                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
-                    gb += __shfl_xor_sync(0xffffffffu, gb, o);
-                    gc += __shfl_xor_sync(0xffffffffu, gc, o);
-                    gr += __shfl_xor_sync(0xffffffffu, gr, o);
-                    gg += __shfl_xor_sync(0xffffffffu, gg, o);
-                    gbl += __shfl_xor_sync(0xffffffffu, gbl, o);
+            const uint32_t ballot = __ballot_sync(0xffffffffu, act);
+            if (ballot == 0u) continue;
+            const int64_t idx = vbase + __float_as_uint(s_rgb[i].w);
+            if (__popc(ballot) == 1) {
+                // one contributing pixel in this warp: no reduction needed
+                if (act) {
+                    atomicAdd(&gv.d_xy_o[idx], make_float4(vv[0], vv[1], vv[2], 0.f));
+                    atomicAdd(&gv.d_conic[idx], make_float4(vv[3], vv[4], vv[5], 0.f));
+                    atomicAdd(&gv.d_rgb[idx], make_float4(vv[6], vv[7], gbl, 0.f));
                 }
-                if (lane == 0) {
-                    const int64_t idx = vbase + s.g;
-                    atomicAdd(&gv.d_xy_o[idx], make_float4(gu, gvv, go, 0.f));
-                    atomicAdd(&gv.d_conic[idx], make_float4(ga, gb, gc, 0.f));
-                    atomicAdd(&gv.d_rgb[idx], make_float4(gr, gg, gbl, 0.f));
-                }
+                continue;
             }
-        }
-    }
-    uint32_t s = evals;
+            const float y = warp_reduce_scatter8(vv, lane);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __syncthreads();
-    if (lane == 0) s_red[threadIdx.x >> 5] = s;
+            for (int o = 16; o > 0; o >>= 1) gbl += __shfl_xor_sync(0xffffffffu, gbl, o);
+            // value k = (lane >> 2) & 7 lives in lanes with lane % 4 == 0; lane 1 adds the ninth
+            const int vk = (lane >> 2) & 7;
+            float *dst = vk < 3 ? reinterpret_cast<float *>(&gv.d_xy_o[idx]) + vk
+                         : vk < 6 ? reinterpret_cast<float *>(&gv.d_conic[idx]) + (vk - 3)
+                                  : reinterpret_cast<float *>(&gv.d_rgb[idx]) + (vk - 6);
+            if ((lane & 3) == 0) atomicAdd(dst, y);
+            else if (lane == 1) atomicAdd(reinterpret_cast<float *>(&gv.d_rgb[idx]) + 2, gbl);
+        }
+        __syncwarp();
+    }
+    // blended (pixel, Gaussian) pairs and walked (pixel, position) pairs
+    unsigned long long e = evals, wk = walked;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        wk += __shfl_xor_sync(0xffffffffu, wk, o);
+    }
+    if (lane == 0) { s_red64[0][warp] = e; s_red64[1][warp] = wk; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long tot = 0;
-        for (int w = 0; w < NT / 32; ++w) tot += s_red[w];
-        if (tot) atomicAdd(&status->counters[2], tot);
+        unsigned long long a = 0, b = 0;
+        for (int w = 0; w < NW; ++w) { a += s_red64[0][w]; b += s_red64[1][w]; }
+        if (a) atomicAdd(&status->counters[2], a);
+        if (b) atomicAdd(&status->counters[4], b);
     }
 }
 
-template <int TILE>
-void fwd_tile(int batch, const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-              const BlendParams &bp, DevStatus *status, cudaStream_t st)
+// Kernels needing more than 48 KB of dynamic shared memory opt in once.
+template <class K>
+bool smem_opt_in(K kernel, size_t bytes)
 {
-    const unsigned grid = vb.total_tiles;
-    if (batch <= 128)
-        k_blend_fwd<TILE, 128><<<grid, TILE * TILE, 0, st>>>(vb, p, vals, ranges, bp, status);
-    else if (batch <= 256)
-        k_blend_fwd<TILE, 256><<<grid, TILE * TILE, 0, st>>>(vb, p, vals, ranges, bp, status);
-    else
-        k_blend_fwd<TILE, 512><<<grid, TILE * TILE, 0, st>>>(vb, p, vals, ranges, bp, status);
+    if (bytes <= 48 * 1024) return true;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 
-template <int TILE>
-void bwd_tile(int batch, const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-              const BlendParams &bp, const GradView &g, DevStatus *status, cudaStream_t st)
+template <int TILE, int CH>
+void fwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
+                const BlendParams &bp, DevStatus *status, cudaStream_t st)
 {
-    const unsigned grid = vb.total_tiles;
-    if (batch <= 128)
-        k_blend_bwd<TILE, 128><<<grid, TILE * TILE, 0, st>>>(vb, p, vals, ranges, bp, g, status);
-    else if (batch <= 256)
-        k_blend_bwd<TILE, 256><<<grid, TILE * TILE, 0, st>>>(vb, p, vals, ranges, bp, g, status);
-    else
-        k_blend_bwd<TILE, 512><<<grid, TILE * TILE, 0, st>>>(vb, p, vals, ranges, bp, g, status);
+    constexpr size_t sm = smem_bytes<TILE, CH, false>();
+    static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH>, sm);
+    (void)ok;
+    k_blend_fwd<TILE, CH><<<vb.total_tiles, TILE * TILE, sm, st>>>(vb, p, vals, ranges, bp, status);
+}
+
+template <int TILE, int CH>
+void bwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
+                const BlendParams &bp, const GradView &g, DevStatus *status, cudaStream_t st)
+{
+    constexpr size_t sm = smem_bytes<TILE, CH, true>();
+    static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH>, sm);
+    (void)ok;
+    k_blend_bwd<TILE, CH><<<vb.total_tiles, TILE * TILE, sm, st>>>(vb, p, vals, ranges, bp, g, status);
 }
 
 }  // namespace
 
+// Supported (tile, entries per warp refill): 8 and 16 with 32, 64 or 128;
+// 32 with 32 or 64 (its 32 warps' slices must fit in shared memory).
+bool blend_config_ok(int tile, int chunk)
+{
+    if (chunk != 32 && chunk != 64 && chunk != 128) return false;
+    if (tile == 8 || tile == 16) return true;
+    return tile == 32 && chunk <= 64;
+}
+
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                      const BlendParams &bp, int batch, DevStatus *status, cudaStream_t st)
+                      const BlendParams &bp, int chunk, DevStatus *status, cudaStream_t st)
 {
     if (vb.total_tiles == 0) return;
-    switch (vb.tile) {
-    case 8: fwd_tile<8>(batch, vb, p, vals, ranges, bp, status, st); break;
-    case 32: fwd_tile<32>(batch, vb, p, vals, ranges, bp, status, st); break;
-    default: fwd_tile<16>(batch, vb, p, vals, ranges, bp, status, st); break;
+    switch (vb.tile * 1000 + chunk) {
+    case 8032: fwd_launch<8, 32>(vb, p, vals, ranges, bp, status, st); break;
+    case 8064: fwd_launch<8, 64>(vb, p, vals, ranges, bp, status, st); break;
+    case 8128: fwd_launch<8, 128>(vb, p, vals, ranges, bp, status, st); break;
+    case 16032: fwd_launch<16, 32>(vb, p, vals, ranges, bp, status, st); break;
+    case 16128: fwd_launch<16, 128>(vb, p, vals, ranges, bp, status, st); break;
+    case 32032: fwd_launch<32, 32>(vb, p, vals, ranges, bp, status, st); break;
+    case 32064: fwd_launch<32, 64>(vb, p, vals, ranges, bp, status, st); break;
+    default: fwd_launch<16, 64>(vb, p, vals, ranges, bp, status, st); break;
     }
     count_launches(1);
 }
 
 void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                      const BlendParams &bp, int batch, const GradView &g, DevStatus *status, cudaStream_t st)
+                      const BlendParams &bp, int chunk, const GradView &g, DevStatus *status, cudaStream_t st)
 {
     if (vb.total_tiles == 0) return;
-    switch (vb.tile) {
-    case 8: bwd_tile<8>(batch, vb, p, vals, ranges, bp, g, status, st); break;
-    case 32: bwd_tile<32>(batch, vb, p, vals, ranges, bp, g, status, st); break;
-    default: bwd_tile<16>(batch, vb, p, vals, ranges, bp, g, status, st); break;
+    switch (vb.tile * 1000 + chunk) {
+    case 8032: bwd_launch<8, 32>(vb, p, vals, ranges, bp, g, status, st); break;
+    case 8064: bwd_launch<8, 64>(vb, p, vals, ranges, bp, g, status, st); break;
+    case 8128: bwd_launch<8, 128>(vb, p, vals, ranges, bp, g, status, st); break;
+    case 16032: bwd_launch<16, 32>(vb, p, vals, ranges, bp, g, status, st); break;
+    case 16128: bwd_launch<16, 128>(vb, p, vals, ranges, bp, g, status, st); break;
+    case 32032: bwd_launch<32, 32>(vb, p, vals, ranges, bp, g, status, st); break;
+    case 32064: bwd_launch<32, 64>(vb, p, vals, ranges, bp, g, status, st); break;
+    default: bwd_launch<16, 64>(vb, p, vals, ranges, bp, g, status, st); break;
     }
     count_launches(1);
 }
