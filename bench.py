@@ -51,6 +51,9 @@ def make_workload(name):
     if name == "c2":
         sc, cams, tg = synth.workload_c2()
         return "c2_batch16_4m_1080p", sc, cams, tg, 71.4
+    if name == "c3":
+        sc, cams, tg = synth.workload_c3()
+        return "c3_batch4_40m_4k", sc, cams, tg, 709.0
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -236,20 +239,42 @@ def run_ours(args, rank, world, local_rank):
     targets = torch.from_numpy(tg).cuda()
     loss = torch.empty(Bv, dtype=torch.float32, device="cuda")
     cam_arr = binding.camera_array(cams)
-    step = 0
 
     def train_once():
-        nonlocal step
-        step += 1
-        ctx.train_step(P, G, M, V, step, cams, targets, loss_out=loss, cam_arr=cam_arr)
+        # step 0: Adam's step comes from the context's device counter, so the
+        # same call can be captured once and replayed
+        ctx.train_step(P, G, M, V, 0, cams, targets, loss_out=loss, cam_arr=cam_arr)
 
     for _ in range(args.warmup):
-        train_once()
+        ctx.train_step(P, G, M, V, 0, cams, targets, loss_out=loss, cam_arr=cam_arr, check=True)
     torch.cuda.synchronize()
     code, needed = ctx.status()
     if code != 0:
         raise SystemExit(f"device status {code} (needed {needed}) after warm-up")
-    binding.call("gs_trace_enable", ctx.h, args.steps, ctx=ctx.h)
+    graph = None
+    graph_launches = 0
+    if args.graph:
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            train_once()
+        torch.cuda.current_stream().wait_stream(side)
+        l0 = binding.lib().gs_kernel_launches()
+        with torch.cuda.graph(graph):
+            train_once()
+        graph_launches = int(binding.lib().gs_kernel_launches() - l0)
+        graph.replay()
+        torch.cuda.synchronize()
+
+    def timed_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            train_once()
+
+    if graph is None:
+        binding.call("gs_trace_enable", ctx.h, args.steps, ctx=ctx.h)
     dist = world > 1
     if dist:
         import torch.distributed as tdist
@@ -263,11 +288,11 @@ def run_ours(args, rank, world, local_rank):
     l0 = binding.lib().gs_kernel_launches()
     e0.record(st)
     for _ in range(args.steps):
-        train_once()
+        timed_step()
     e1.record(st)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    launches = int(binding.lib().gs_kernel_launches() - l0)
+    launches = int(binding.lib().gs_kernel_launches() - l0) + graph_launches * (args.steps if graph is not None else 0)
     ms_total = e0.elapsed_time(e1)
     if dist:
         t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
@@ -277,15 +302,62 @@ def run_ours(args, rank, world, local_rank):
     code, needed = ctx.status()
     if code != 0:
         raise SystemExit(f"device status {code} (needed {needed}) in the timed region")
-    # per-stage times of the timed steps (events on the launching stream)
+    # per-stage times from the library's trace events (on the launching stream);
+    # with graph replay they come from a separate traced pass of direct calls
     import ctypes
-    buf = (ctypes.c_float * (args.steps * binding.GS_TRACE_STAGES))()
+    nstep_tr = args.steps if graph is None else min(args.steps, 20)
+    if graph is not None:
+        binding.call("gs_trace_enable", ctx.h, nstep_tr, ctx=ctx.h)
+        for _ in range(nstep_tr):
+            train_once()
+    buf = (ctypes.c_float * (nstep_tr * binding.GS_TRACE_STAGES))()
     nst = ctypes.c_int32(0)
     binding.call("gs_trace_read", ctx.h, buf, ctypes.byref(nst), ctx=ctx.h)
     binding.call("gs_trace_enable", ctx.h, 0, ctx=ctx.h)
-    arr = np.frombuffer(buf, dtype=np.float32).reshape(args.steps, binding.GS_TRACE_STAGES)[:nst.value]
+    arr = np.frombuffer(buf, dtype=np.float32).reshape(nstep_tr, binding.GS_TRACE_STAGES)[:nst.value]
     stage_ms = {s: float(arr[:, i].mean()) for i, s in enumerate(binding.TRACE_STAGES)}
     counters = ctx.counters()
+
+    # per-view: the same scene stepped one view at a time over the same views
+    per_view = None
+    if Bv > 1 and not args.no_per_view:
+        ctx1 = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch)
+        P1 = P.clone()
+        G1, M1, V1 = P1.zeros_like(), P1.zeros_like(), P1.zeros_like()
+        loss1 = torch.empty(1, dtype=torch.float32, device="cuda")
+        arrs = [binding.camera_array([c]) for c in cams]
+        tgts = [targets[b:b + 1].contiguous() for b in range(Bv)]
+
+        def per_view_round(check=False):
+            for b in range(Bv):
+                ctx1.train_step(P1, G1, M1, V1, 0, [cams[b]], tgts[b], loss_out=loss1, cam_arr=arrs[b], check=check)
+
+        for _ in range(2):
+            per_view_round(check=True)     # sizes the fragment buffer for every view
+        g1 = None
+        if args.graph:
+            g1 = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                per_view_round()
+            torch.cuda.current_stream().wait_stream(side)
+            with torch.cuda.graph(g1):
+                per_view_round()
+        rounds = max(1, args.steps // 4)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(rounds):
+            g1.replay() if g1 is not None else per_view_round()
+        e1.record(st)
+        torch.cuda.synchronize()
+        pv_ms = e0.elapsed_time(e1)
+        code1, needed1 = ctx1.status()
+        if code1 != 0:
+            raise SystemExit(f"per-view leg: device status {code1} (needed {needed1})")
+        per_view = {"views_per_s": rounds * Bv * world / (pv_ms * 1e-3), "ms_per_view": pv_ms / (rounds * Bv),
+                    "rounds": rounds, "note": f"{Bv} single-view training steps (B=1, own Adam step each) per round"}
+        del ctx1, P1, G1, M1, V1
 
     # end to end through the public API with host buffers
     pinned = torch.from_numpy(tg).pin_memory()
@@ -301,6 +373,9 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.current_stream().synchronize()
         _ = float(loss_host[0])
     e2e_s = time.perf_counter() - t0
+    code, needed = ctx.status()
+    if code != 0:
+        raise SystemExit(f"device status {code} (needed {needed}) in the end-to-end leg")
     if dist:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
@@ -350,7 +425,8 @@ def run_ours(args, rank, world, local_rank):
                    "tile": args.tile, "smem_batch": args.batch, "sh_degree": 3,
                    "l2": "no flush: params + grad + Adam moments resident in HBM exceed the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "mpix_per_s": value * H * W / 1e6},
+                   "mpix_per_s": value * H * W / 1e6, "cuda_graph": bool(args.graph),
+                   "per_view": per_view},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tg.nbytes), "d2h_bytes_per_step": 4 * Bv,
                 "api": "gs_train_step with a pinned-host target upload and a loss readback every step"},
         "gpu_launches": launches,
@@ -396,24 +472,65 @@ def ncu_summary(path, steps=None):
     print(f"| total | {len(rows)} | {tot / 1e6:.3f} | 100% |")
 
 
+def run_serving(args, rank, world, local_rank):
+    """10M-Gaussian scene (built as the 40M aerial one), Poisson arrivals at
+    200 requests/s, resolutions 360p/720p/1080p/4K at 0.4/0.3/0.2/0.1, poses
+    on a 150 m hemisphere; continuous batching over concurrent slots."""
+    import torch
+    from paper_2406_18533_gb300 import engine, serve
+    torch.cuda.set_device(local_rank)
+    sc, rng = synth.large_scene(10_000_000, seed=0)
+    scene = engine.DeviceScene.from_host(sc)
+    reqs = [serve.Request(i, t, cam) for i, (t, cam) in enumerate(synth.serve_requests(rng, args.requests))]
+    server = serve.RenderServer(scene, n_slots=3, max_batch=8, tile=args.tile, smem_batch=args.batch)
+    # one untimed pass over a few requests sizes the fragment buffers
+    server.run([serve.Request(-1 - i, 0.0, r.cam) for i, r in enumerate(reqs[:16])])
+    server.retries = 0
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = None
+    from paper_2406_18533_gb300 import binding
+    l0 = binding.lib().gs_kernel_launches()
+    done = server.run(reqs)
+    clocks = sampler.stop()
+    rep = serve.latency_report(done, skip=min(200, len(done) // 4))
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": rep["p50_ms"], "unit": "ms", "n_gpus": world, "steps": rep["requests"],
+            "warmup": min(200, len(done) // 4), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c4_serve_10m", "gaussians": sc.N, "arrival_rate_per_s": 200,
+                       "slots": len(server.slots), "max_batch": server.max_batch, "tile": args.tile,
+                       "smem_batch": args.batch},
+            "serving": rep, "batches": server.batches, "capacity_retries": server.retries,
+            "gpu_launches": int(binding.lib().gs_kernel_launches() - l0), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     if len(sys.argv) >= 3 and sys.argv[1] == "--ncu-summary":
         return ncu_summary(sys.argv[2])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2"])
+    ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--requests", type=int, default=2200, help="c4: requests replayed (the first 200 warm up)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-view", action="store_true")
+    ap.add_argument("--graph", action="store_true", help="replay one captured training step (CUDA graph)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload == "c4":
+        return run_serving(args, rank, world, local_rank)
     if world > 1:
         import torch
         import torch.distributed as tdist

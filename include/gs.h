@@ -42,6 +42,7 @@ extern "C" {
 
 #define GS_ABI_VERSION 1
 #define GS_MAX_VIEWS 32   /* views per call (training batch or render batch) */
+#define GS_MAX_FRAGMENTS 1073741823ull  /* 2^30 - 1: largest fragment capacity of one call */
 
 typedef enum gs_status {
     GS_OK = 0,
@@ -215,7 +216,7 @@ gs_status gs_bin(gs_ctx *ctx, const gs_proj *proj, const gs_camera *cams, int32_
  * afford cudaMalloc/cudaFree (both synchronise the device), and callers
  * without a gs_ctx (creating one allocates).
  *
- * All scratch lives in one static device array of 14.5 MiB that every GPU on
+ * All scratch lives in one static device array of 14.63 MiB that every GPU on
  * which the library's kernels are loaded holds until the process exits.
  * Limits: B * proj->N <= 262144 (view, Gaussian) pairs and out->capacity <=
  * 1048576 fragments; larger sizes, an unsupported tile (8, 16, 32) or a bad
@@ -274,7 +275,10 @@ gs_status gs_loss(gs_ctx *ctx, const float *img, const float *target, int32_t B,
  * Adam over all 60 N floats (Sec. 4): m = b1' m + (1-b1') g, v = b2' v +
  * (1-b2') g^2, p -= lr' m_hat / (sqrt(v_hat) + eps), bias correction with
  * b' at `step` (>= 1), lr' = lr sqrt(B) (Eq. 1) and b' = b^B (Eq. 2) when the
- * hyperparameter flags ask for them.  In place on p, m, v.
+ * hyperparameter flags ask for them.  In place on p, m, v.  step == 0 takes
+ * the step from the context's device-side counter, incremented by the call
+ * itself (first call: step 1), so a call captured in a CUDA graph advances the
+ * step on every replay.  A pending GS_ERR_CAPACITY skips the update.
  */
 gs_status gs_adam_step(gs_ctx *ctx, gs_scene *p, const gs_scene *g, gs_scene *m, gs_scene *v,
                        int64_t step, int32_t B, void *stream);
@@ -284,6 +288,10 @@ gs_status gs_adam_step(gs_ctx *ctx, gs_scene *p, const gs_scene *g, gs_scene *m,
  * batched as in Sec. 4): transformation, binning, compositing, loss,
  * backward, Adam.  targets: [B][3][H][W] float device; loss_out: [B] float
  * device.  Scratch comes from the context.  g receives the batch gradient.
+ * step as in gs_adam_step (0: device counter).  Once the context has sized its
+ * scratch (a first call, or gs_reserve), the call allocates nothing and never
+ * synchronises, so it can be captured in a CUDA graph; the graph replays the
+ * captured cameras.
  */
 gs_status gs_train_step(gs_ctx *ctx, gs_scene *p, gs_scene *g, gs_scene *m, gs_scene *v, int64_t step,
                         const gs_camera *cams, int32_t B, const float *targets, float *loss_out,

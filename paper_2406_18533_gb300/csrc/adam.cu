@@ -26,10 +26,28 @@ __device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, flo
     p -= lr * mh / (sqrtf(vh) + a.eps);
 }
 
+// Advances the device-side step counter (graph-replayable training loops) and
+// stores the bias corrections 1 - b1^t, 1 - b2^t next to it for the update.
+__global__ void k_step_tick(long long *dstep, float b1, float b2, const DevStatus *status)
+{
+    if (status->code == GS_ERR_CAPACITY) return;
+    const long long t = dstep[0] + 1;
+    dstep[0] = t;
+    float *bc = reinterpret_cast<float *>(dstep + 1);
+    bc[0] = (float)(1.0 - pow((double)b1, (double)t));
+    bc[1] = (float)(1.0 - pow((double)b2, (double)t));
+}
+
+// Grid-stride over one plane per gridDim.y (about 8 resident CTAs per SM in total).
 __global__ void __launch_bounds__(256) k_adam(SceneMut P, SceneView G, SceneMut M, SceneMut V, AdamArgs a,
                                               const DevStatus *status)
 {
     if (status->code == GS_ERR_CAPACITY) return;   // the step's gradient is incomplete: skip the update
+    if (a.dstep) {
+        const float *bc = reinterpret_cast<const float *>(a.dstep + 1);
+        a.bc1 = bc[0];
+        a.bc2 = bc[1];
+    }
     const int pl = blockIdx.y;
     float4 *pp = plane_ptr(P, pl);
     const float4 *gp = plane_ptr(G, pl);
@@ -54,11 +72,14 @@ __global__ void __launch_bounds__(256) k_adam(SceneMut P, SceneView G, SceneMut 
 void launch_adam(const SceneMut &p, const SceneView &g, const SceneMut &m, const SceneMut &v, const AdamArgs &a,
                  const DevStatus *status, cudaStream_t st)
 {
+    if (a.dstep) {
+        k_step_tick<<<1, 1, 0, st>>>(a.dstep, a.b1, a.b2, status);
+        count_launches(1);
+    }
     if (p.N == 0) return;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // ~8 resident blocks of 256 per SM spread over the 15 planes
     int64_t bx = ((int64_t)sms * 8 + 14) / 15;
     const int64_t need = (p.N + 255) / 256;
     if (bx > need) bx = need;

@@ -195,83 +195,146 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, ProjView p, con
         }
 }
 
-// ---------------------------------------------------------------- K4 radix sort
+// ---------------------------------------------------------------- K4 radix sort (one-sweep)
+//
+// LSD radix sort on 8-bit digits of the 64-bit keys (only the digits that can
+// be nonzero: 4 depth bytes + the tile-id bytes), stable, so equal keys keep
+// the emission order (ascending Gaussian index).  An upfront kernel
+// histograms every digit position in one read of the keys; each pass is then
+// a single kernel: a CTA takes the next tile of RS_TILE keys (tile order =
+// launch order, from an atomic counter), ranks its keys stably in shared
+// memory, publishes its per-digit counts, and finds the keys of all earlier
+// tiles with the same digit by a decoupled look-back over their published
+// counts, so each pass reads and writes the keys once.
 
 constexpr int RS_THREADS = 256;
-constexpr int RS_ROUNDS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;     // 4096 keys per block
+constexpr int RS_ITEMS = 16;
 constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_WARP_KEYS = 32 * RS_ITEMS;         // 512 consecutive keys per warp
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;      // 4096 keys per tile
+constexpr int RS_MAX_PASSES = 8;
+constexpr uint32_t LB_AGG = 1u << 30;               // look-back flag: tile count available
+constexpr uint32_t LB_PRE = 2u << 30;               // look-back flag: inclusive prefix available
+constexpr uint32_t LB_VAL = (1u << 30) - 1u;
+constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;
 
-// Per-block digit histogram, written digit-major: hist[d * nblocks + b].
-__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint64_t *keys, const uint32_t *count, int shift,
-                                                           uint32_t *hist, uint32_t nblocks)
+__global__ void __launch_bounds__(RS_THREADS) k_digit_hist(const uint64_t *keys, const uint32_t *count, int passes,
+                                                           uint32_t *ghist)
 {
-    __shared__ uint32_t h[RS_WARPS][256];
-    const int t = threadIdx.x, w = t >> 5;
-#pragma unroll
-    for (int j = 0; j < RS_WARPS; ++j) h[j][t] = 0u;
+    __shared__ uint32_t h[RS_MAX_PASSES][256];
+    for (int i = threadIdx.x; i < RS_MAX_PASSES * 256; i += RS_THREADS) h[i / 256][i % 256] = 0u;
     __syncthreads();
     const uint32_t n = *count;
-    const uint64_t t0 = (uint64_t)blockIdx.x * RS_TILE;
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        const uint64_t i = t0 + (uint64_t)r * RS_THREADS + t;
-        if (i < n) atomicAdd(&h[w][(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    for (uint64_t i = blockIdx.x * (uint64_t)RS_THREADS + threadIdx.x; i < n; i += (uint64_t)gridDim.x * RS_THREADS) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(uint32_t)(k >> (8 * p)) & 255u], 1u);
     }
     __syncthreads();
-    uint32_t s = 0;
-#pragma unroll
-    for (int j = 0; j < RS_WARPS; ++j) s += h[j][t];
-    hist[(uint64_t)t * nblocks + blockIdx.x] = s;
+    for (int i = threadIdx.x; i < passes * 256; i += RS_THREADS) {
+        const uint32_t c = h[i / 256][i % 256];
+        if (c) atomicAdd(&ghist[i], c);
+    }
 }
 
-// Stable scatter of one digit.  Keys are taken in rounds of 256 consecutive
-// keys; within a round a key's rank is (running count of its digit in this
-// block) + (count in earlier warps of the round) + (count in earlier lanes of
-// its warp), which preserves input order among equal digits.
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint64_t *kin, const uint32_t *vin,
-                                                              uint64_t *kout, uint32_t *vout, const uint32_t *count,
-                                                              int shift, const uint32_t *offs, uint32_t nblocks)
+// Exclusive scan of each pass's 256 digit counts (one CTA per pass).
+__global__ void __launch_bounds__(256) k_digit_offsets(uint32_t *ghist)
 {
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t wc[RS_WARPS][256];
-    const int t = threadIdx.x, w = t >> 5;
+    __shared__ uint32_t sw[33];
+    uint32_t *h = ghist + 256 * blockIdx.x;
+    const uint32_t x = h[threadIdx.x];
+    uint32_t excl;
+    block_excl_scan(x, excl, sw);
+    h[threadIdx.x] = excl;
+}
+
+// Ranking: warp w owns the 512 consecutive keys t0 + w*512 + [0, 512), item i
+// of lane l being key t0 + w*512 + 32 i + l.  Items are ranked in order with
+// __match_any_sync against per-warp running digit counts, so ranks are stable
+// within the warp; one block-wide prefix over the warps' counts then orders
+// the warps.  Two block barriers per 4096-key tile.
+__global__ void __launch_bounds__(RS_THREADS) k_onesweep(const uint64_t *kin, const uint32_t *vin, uint64_t *kout,
+                                                         uint32_t *vout, const uint32_t *count, int shift,
+                                                         const uint32_t *doff, uint32_t *look, uint32_t *tile_ctr,
+                                                         DevStatus *status)
+{
+    __shared__ uint32_t wcnt[RS_WARPS][256];
+    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t s_tile;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const uint32_t n = *count;
-    const uint64_t t0 = (uint64_t)blockIdx.x * RS_TILE;
+    if (t == 0) s_tile = atomicAdd(tile_ctr, 1u);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) wcnt[w][lane + 32 * j] = 0u;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t t0 = (uint64_t)tile * RS_TILE;
     if (t0 >= n) return;
-    run[t] = offs[(uint64_t)t * nblocks + blockIdx.x];
     const uint32_t lt = lanemask_lt();
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        const uint64_t rb = t0 + (uint64_t)r * RS_THREADS;
-        if (rb >= n) break;
-        const uint64_t i = rb + t;
-        const bool valid = i < n;
-        const uint64_t k = valid ? kin[i] : 0ull;
-        const uint32_t val = valid ? vin[i] : 0u;
-        const uint32_t d = valid ? ((uint32_t)(k >> shift) & 255u) : 256u;
+    const uint64_t wb = t0 + (uint64_t)w * RS_WARP_KEYS;
+    uint64_t key[RS_ITEMS];
+    uint32_t val[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
-        for (int j = 0; j < RS_WARPS; ++j) wc[j][t] = 0u;
-        __syncthreads();
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const uint64_t idx = wb + 32 * i + lane;
+        const bool valid = idx < n;
+        key[i] = valid ? kin[idx] : 0ull;
+        val[i] = valid ? vin[idx] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const bool valid = wb + 32 * i + lane < n;
+        const uint32_t d = valid ? ((uint32_t)(key[i] >> shift) & 255u) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0) wc[w][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t acc = run[t];
+        const uint32_t base = valid ? wcnt[w][d] : 0u;
+        rank[i] = base + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0u) wcnt[w][d] = base + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // digit t: exclusive prefix over the warps, tile count, look-back over earlier tiles
+    uint32_t mine = 0;
 #pragma unroll
-            for (int j = 0; j < RS_WARPS; ++j) {
-                const uint32_t cnt = wc[j][t];
-                wc[j][t] = acc;
-                acc += cnt;
+    for (int j = 0; j < RS_WARPS; ++j) {
+        const uint32_t c = wcnt[j][t];
+        wcnt[j][t] = mine;
+        mine += c;
+    }
+    uint32_t *lk = look + (size_t)tile * 256 + t;
+    if (tile == 0) {
+        atomicExch(lk, LB_PRE | mine);
+        gbase[t] = doff[t];
+    } else {
+        atomicExch(lk, LB_AGG | mine);
+        uint32_t excl = 0;
+        bool timed_out = false;
+        for (int64_t pt = (int64_t)tile - 1; pt >= 0; --pt) {
+            const volatile uint32_t *q = look + (size_t)pt * 256 + t;
+            uint32_t v = *q, spins = 0;
+            while ((v & (LB_AGG | LB_PRE)) == 0u) {
+                if (++spins > LB_SPIN_LIMIT) {       // give up: report instead of hanging
+                    atomicCAS(&status->code, 0, (int)GS_ERR_TIMEOUT);
+                    timed_out = true;
+                    break;
+                }
+                v = *q;
             }
-            run[t] = acc;
+            excl += v & LB_VAL;
+            if ((v & LB_PRE) || timed_out) break;
         }
-        __syncthreads();
-        if (valid) {
-            const uint32_t dst = wc[w][d] + rank;
-            kout[dst] = k;
-            vout[dst] = val;
+        atomicExch(lk, LB_PRE | (excl + mine));
+        gbase[t] = doff[t] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const uint64_t idx = wb + 32 * i + lane;
+        if (idx < n) {
+            const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
+            const uint32_t dst = gbase[d] + wcnt[w][d] + rank[i];
+            kout[dst] = key[i];
+            vout[dst] = val[i];
         }
-        __syncthreads();
     }
 }
 
@@ -333,28 +396,37 @@ void launch_emit_keys(const ViewBatch &vb, const ProjView &p, const uint32_t *nt
 
 size_t sort_temp_bytes(uint64_t capacity)
 {
-    const uint64_t nb = capacity > 0 ? (capacity + RS_TILE - 1) / RS_TILE : 1;
-    const uint64_t nh = 256 * nb;
-    return (size_t)nh * sizeof(uint32_t) + scan_temp_bytes((int64_t)nh) + 256;
+    const uint64_t tiles = capacity > 0 ? (capacity + RS_TILE - 1) / RS_TILE : 1;
+    // digit offsets (passes x 256), tile counters, look-back words (tiles x 256)
+    return (size_t)RS_MAX_PASSES * 256 * 4 + 256 + (size_t)tiles * 256 * 4 + 256;
 }
 
 void launch_radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
-                       const uint32_t *count, int high_bits, void *temp, cudaStream_t st)
+                       const uint32_t *count, int high_bits, void *temp, DevStatus *status, cudaStream_t st)
 {
     if (capacity == 0) return;
-    const uint32_t nb = (uint32_t)((capacity + RS_TILE - 1) / RS_TILE);
-    const int64_t nh = 256 * (int64_t)nb;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(temp);
-    void *scan_tmp = reinterpret_cast<char *>(temp) + (((size_t)nh * sizeof(uint32_t) + 255) & ~(size_t)255);
     const int passes = 4 + (high_bits + 7) / 8;
+    const uint64_t tiles = (capacity + RS_TILE - 1) / RS_TILE;
+    char *tp = reinterpret_cast<char *>(temp);
+    uint32_t *ghist = reinterpret_cast<uint32_t *>(tp);
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(tp + (size_t)RS_MAX_PASSES * 256 * 4);
+    uint32_t *look = reinterpret_cast<uint32_t *>(tp + (size_t)RS_MAX_PASSES * 256 * 4 + 256);
+    cudaMemsetAsync(tp, 0, (size_t)RS_MAX_PASSES * 256 * 4 + 256, st);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t hb = (capacity + RS_THREADS * 16 - 1) / (RS_THREADS * 16);
+    if (hb > (uint64_t)sms * 8) hb = (uint64_t)sms * 8;
+    k_digit_hist<<<(unsigned)(hb ? hb : 1), RS_THREADS, 0, st>>>(keys, count, passes, ghist);
+    k_digit_offsets<<<passes, 256, 0, st>>>(ghist);
+    count_launches(2);
     uint64_t *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     for (int ps = 0; ps < passes; ++ps) {
-        const int shift = 8 * ps;
-        k_radix_hist<<<nb, RS_THREADS, 0, st>>>(ki, count, shift, hist, nb);
-        launch_exclusive_scan(hist, hist, nh, nullptr, scan_tmp, st);
-        k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, count, shift, hist, nb);
-        count_launches(2);
+        cudaMemsetAsync(look, 0, (size_t)tiles * 256 * 4, st);
+        k_onesweep<<<(unsigned)tiles, RS_THREADS, 0, st>>>(ki, vi, ko, vo, count, 8 * ps, ghist + 256 * ps, look,
+                                                           ctr + ps, status);
+        count_launches(1);
         uint64_t *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
     }

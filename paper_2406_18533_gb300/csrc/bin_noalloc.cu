@@ -26,8 +26,8 @@ constexpr size_t OFF_TOTAL = OFF_SCAN + 4096;                          // uint64
 constexpr size_t OFF_STATUS = OFF_TOTAL + 256;                         // DevStatus
 constexpr size_t OFF_KEYS = OFF_STATUS + 256;                          // uint64[frags]
 constexpr size_t OFF_VALS = OFF_KEYS + 8 * (size_t)NA_MAX_FRAGS;       // uint32[frags]
-constexpr size_t OFF_SORT = OFF_VALS + 4 * (size_t)NA_MAX_FRAGS;       // sort temp, 512 KiB
-constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_SORT + 512 * 1024;        // 14.5 MiB + 4.5 KiB
+constexpr size_t OFF_SORT = OFF_VALS + 4 * (size_t)NA_MAX_FRAGS;       // sort temp, 640 KiB
+constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_SORT + 640 * 1024;        // 14.63 MiB
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -127,7 +127,7 @@ extern "C" gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, 
     launch_count_tiles(vb, pv, ntiles, st);
     launch_exclusive_scan(ntiles, offsets, n, total, s + OFF_SCAN, st);
     launch_emit_keys(vb, pv, ntiles, offsets, k_emit, v_emit, out->capacity, total, status, out->count, st);
-    launch_radix_sort(k_emit, v_emit, k_other, v_other, out->capacity, out->count, high, sort_tmp, st);
+    launch_radix_sort(k_emit, v_emit, k_other, v_other, out->capacity, out->count, high, sort_tmp, status, st);
     launch_tile_ranges(out->keys, out->count, out->capacity, reinterpret_cast<uint2 *>(out->ranges), vb.total_tiles,
                        st);
     if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;

@@ -30,6 +30,7 @@ struct DBuf {
 struct gs_ctx {
     gs_hparams hp;
     DevStatus *status = nullptr;       // device
+    long long *dstep = nullptr;        // device step counter (step == 0 calls)
     DevStatus *h_status = nullptr;     // pinned host mirror
     char err[512];
     // binning scratch
@@ -231,7 +232,7 @@ gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, const u
     launch_emit_keys(vb, p, ntiles, ptr<uint32_t>(c->offsets), k_emit, v_emit, capacity, total, c->status, count,
                      st);
     mark(c, st, 3);
-    launch_radix_sort(k_emit, v_emit, k_other, v_other, capacity, count, high, c->sort_tmp.p, st);
+    launch_radix_sort(k_emit, v_emit, k_other, v_other, capacity, count, high, c->sort_tmp.p, c->status, st);
     mark(c, st, 4);
     launch_tile_ranges(keys, count, capacity, ranges, vb.total_tiles, st);
     mark(c, st, 5);
@@ -281,9 +282,11 @@ gs_status read_total(gs_ctx *c, cudaStream_t st, uint64_t *F)
     return GS_OK;
 }
 
-AdamArgs adam_args(const gs_hparams &hp, int64_t step, int32_t B)
+AdamArgs adam_args(const gs_hparams &hp, int64_t step, int32_t B, long long *dstep)
 {
     AdamArgs a;
+    a.dstep = step == 0 ? dstep : nullptr;
+    if (step == 0) step = 1;   // placeholders; the kernel computes the corrections
     const double b1 = hp.scale_beta_pow_b ? pow((double)hp.beta1, B) : hp.beta1;
     const double b2 = hp.scale_beta_pow_b ? pow((double)hp.beta2, B) : hp.beta2;
     const double lf = hp.scale_lr_sqrt_b ? sqrt((double)B) : 1.0;
@@ -389,7 +392,7 @@ gs_status gs_create(gs_ctx **out, const gs_hparams *hp)
     if (hp) c->hp = *hp; else gs_default_hparams(&c->hp);
     gs_status r = check_hparams(c, &c->hp);
     if (r != GS_OK) { delete c; return r; }
-    if (cudaMalloc(&c->status, sizeof(DevStatus)) != cudaSuccess ||
+    if (cudaMalloc(&c->status, sizeof(DevStatus)) != cudaSuccess || cudaMalloc(&c->dstep, 2 * sizeof(long long)) != cudaSuccess ||
         cudaMallocHost(&c->h_status, sizeof(DevStatus)) != cudaSuccess) {
         cudaGetLastError();
         if (c->status) cudaFree(c->status);
@@ -397,6 +400,7 @@ gs_status gs_create(gs_ctx **out, const gs_hparams *hp)
         return GS_ERR_CUDA;
     }
     cudaMemset(c->status, 0, sizeof(DevStatus));
+    cudaMemset(c->dstep, 0, 2 * sizeof(long long));
     memset(c->h_status, 0, sizeof(DevStatus));
     if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); }
     *out = c;
@@ -414,6 +418,7 @@ gs_status gs_destroy(gs_ctx *c)
         if (b->p) cudaFree(b->p);
     trace_free(c);
     if (c->status) cudaFree(c->status);
+    if (c->dstep) cudaFree(c->dstep);
     if (c->h_status) cudaFreeHost(c->h_status);
     delete c;
     return GS_OK;
@@ -467,7 +472,7 @@ gs_status gs_reserve(gs_ctx *c, int64_t N, const gs_camera *cams, int32_t B, uin
     ViewBatch vb;
     gs_status r = make_views(c, cams, B, vb, false);
     if (r != GS_OK) return r;
-    if (frag_capacity > 0xffffffffull) return fail(c, GS_ERR_INVALID_ARG, "fragment capacity above 2^32-1");
+    if (frag_capacity > GS_MAX_FRAGMENTS) return fail(c, GS_ERR_INVALID_ARG, "fragment capacity above 2^30-1");
     if (frag_capacity > c->frag_cap) c->frag_cap = frag_capacity;
     const int64_t n = (int64_t)B * (N > 0 ? N : 1);
     if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
@@ -527,7 +532,7 @@ gs_status gs_bin(gs_ctx *c, const gs_proj *proj, const gs_camera *cams, int32_t 
     if (!proj || proj->B != B || proj->N < 0) return fail(c, GS_ERR_INVALID_ARG, "bad gs_proj");
     if (!out || !out->ranges || !out->count || (out->capacity > 0 && (!out->keys || !out->vals)))
         return fail(c, GS_ERR_INVALID_ARG, "bad gs_bins");
-    if (out->capacity > 0xffffffffull) return fail(c, GS_ERR_INVALID_ARG, "capacity above 2^32-1");
+    if (out->capacity > GS_MAX_FRAGMENTS) return fail(c, GS_ERR_INVALID_ARG, "capacity above 2^30-1");
     ViewBatch vb;
     gs_status r = make_views(c, cams, B, vb, false);
     if (r != GS_OK) return r;
@@ -624,8 +629,8 @@ gs_status gs_adam_step(gs_ctx *c, gs_scene *p, const gs_scene *g, gs_scene *m, g
     if (!scene_ok(p) || !scene_ok(g) || !scene_ok(m) || !scene_ok(v) || g->N != p->N || m->N != p->N ||
         v->N != p->N)
         return fail(c, GS_ERR_INVALID_ARG, "bad parameter / moment planes");
-    if (step < 1 || B < 1) return fail(c, GS_ERR_INVALID_ARG, "step and B must be >= 1");
-    launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), adam_args(c->hp, step, B), c->status, S(stream));
+    if (step < 0 || B < 1) return fail(c, GS_ERR_INVALID_ARG, "step must be >= 0 and B >= 1");
+    launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), adam_args(c->hp, step, B, c->dstep), c->status, S(stream));
     return cuda_check(c, "gs_adam_step");
 }
 
@@ -636,7 +641,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     if (!scene_ok(p) || !scene_ok(g) || !scene_ok(m) || !scene_ok(v) || g->N != p->N || m->N != p->N ||
         v->N != p->N)
         return fail(c, GS_ERR_INVALID_ARG, "bad parameter / moment planes");
-    if (!targets || !loss_out || step < 1) return fail(c, GS_ERR_INVALID_ARG, "bad targets / loss_out / step");
+    if (!targets || !loss_out || step < 0) return fail(c, GS_ERR_INVALID_ARG, "bad targets / loss_out / step");
     ViewBatch vb;
     gs_status r = make_views(c, cams, B, vb, true);
     if (r != GS_OK) return r;
@@ -660,7 +665,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
         uint64_t F = 0;
         if ((r = read_total(c, st, &F)) != GS_OK) return r;
         uint64_t cap = F + F / 4 + 4096;
-        if (cap > 0xffffffffull) cap = 0xffffffffull;
+        if (cap > GS_MAX_FRAGMENTS) cap = GS_MAX_FRAGMENTS;
         c->frag_cap = cap;
         if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
     }
@@ -688,7 +693,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     mark(c, st, 9);
     launch_preprocess_bwd(sv, vb, pv, gv, mut_of(g), st);
     mark(c, st, 10);
-    launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), adam_args(c->hp, step, B), c->status, st);
+    launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), adam_args(c->hp, step, B, c->dstep), c->status, st);
     mark(c, st, 11);
     if (c->trace_on) ++c->trace_step;
     c->trace_on = false;
@@ -719,7 +724,7 @@ gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int
         uint64_t F = 0;
         if ((r = read_total(c, st, &F)) != GS_OK) return r;
         uint64_t cap = F + F / 4 + 4096;
-        if (cap > 0xffffffffull) cap = 0xffffffffull;
+        if (cap > GS_MAX_FRAGMENTS) cap = GS_MAX_FRAGMENTS;
         c->frag_cap = cap;
         if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
     }

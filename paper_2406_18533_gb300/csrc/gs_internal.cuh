@@ -96,8 +96,9 @@ void launch_emit_keys(const ViewBatch &vb, const ProjView &p, const uint32_t *nt
 size_t sort_temp_bytes(uint64_t capacity);
 // Sorts keys/vals (count on device, <= capacity) on bits [0, 32 + high_bits).
 // Result lands in keys/vals; alt buffers are scratch of the same capacity.
+// A look-back wait that exceeds its spin limit sets GS_ERR_TIMEOUT in *status.
 void launch_radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
-                       const uint32_t *count, int high_bits, void *temp, cudaStream_t st);
+                       const uint32_t *count, int high_bits, void *temp, DevStatus *status, cudaStream_t st);
 
 void launch_tile_ranges(const uint64_t *keys, const uint32_t *count, uint64_t capacity, uint2 *ranges,
                         uint32_t total_tiles, cudaStream_t st);
@@ -116,7 +117,9 @@ void launch_loss(const float *img, const float *target, int B, int W, int H, flo
 struct AdamArgs {
     float lr[15][4];   // per plane, per lane (already times sqrt(B) when asked)
     float b1, b2, eps;
-    float bc1, bc2;    // 1 - b1^t, 1 - b2^t
+    float bc1, bc2;    // 1 - b1^t, 1 - b2^t (host step)
+    long long *dstep;  // non-null: [0] step counter on the device, ticked before the update;
+                       // [1] holds the float bias corrections the tick computes
 };
 void launch_adam(const SceneMut &p, const SceneView &g, const SceneMut &m, const SceneMut &v, const AdamArgs &a,
                  const DevStatus *status, cudaStream_t st);

@@ -232,23 +232,41 @@ class Context:
         self._c("gs_adam_step", self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm), ctypes.byref(sv),
                 int(step), int(batch), _stream())
 
-    def train_step(self, p, g, m, v, step, cams, targets, loss_out=None, cam_arr=None):
+    def train_step(self, p, g, m, v, step, cams, targets, loss_out=None, cam_arr=None, check=False):
+        """One gs_train_step.  check=True synchronises, and when the fragment
+        buffer overflowed (the library then skipped the update) grows it and
+        runs the same step again."""
         Bv = len(cams)
         loss_out = loss_out if loss_out is not None else torch.empty(Bv, dtype=torch.float32, device=targets.device)
         sp, sg, sm, sv = p.struct(), g.struct(), m.struct(), v.struct()
         self._c("gs_train_step", self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm), ctypes.byref(sv),
                 int(step), cam_arr if cam_arr is not None else B.camera_array(cams), Bv, _ptr(targets),
                 _ptr(loss_out), _stream())
+        if check and self._grew(p.N, cams):
+            return self.train_step(p, g, m, v, step, cams, targets, loss_out, cam_arr, check=True)
         return loss_out
 
-    def render(self, scene: DeviceScene, cams, imgs=None, cam_arr=None):
+    def render(self, scene: DeviceScene, cams, imgs=None, cam_arr=None, check=False):
+        """gs_render of a batch of views (sizes may differ).  check=True as in
+        train_step: synchronise, grow the fragment buffer on overflow, render again."""
         if imgs is None:
             imgs = [torch.empty(3, c.H, c.W, dtype=torch.float32, device=scene.mo.device) for c in cams]
         arr = (ctypes.c_void_p * len(cams))(*[t.data_ptr() for t in imgs])
         s = scene.struct()
         self._c("gs_render", self.h, ctypes.byref(s), cam_arr if cam_arr is not None else B.camera_array(cams),
                 len(cams), arr, _stream())
+        if check and self._grew(scene.N, cams):
+            return self.render(scene, cams, imgs, cam_arr, check=True)
         return imgs
+
+    def _grew(self, N, cams) -> bool:
+        code, needed = self.status()
+        if code == B.GS_ERR_CAPACITY:
+            self.reserve(N, cams, int(needed * 1.25) + 4096)
+            return True
+        if code != B.GS_OK:
+            raise B.GSError("device status", code, B.lib().gs_last_error(self.h).decode())
+        return False
 
     def reserve(self, N, cams, frag_capacity):
         self._c("gs_reserve", self.h, int(N), B.camera_array(cams), len(cams), int(frag_capacity))

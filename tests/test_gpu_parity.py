@@ -372,9 +372,9 @@ def test_batched_render_equals_single_view(eng):
     cams[3] = synth.ring_cameras(rng, 1, (80.0, 80.0), W=97, H=61)[0]
     ctx = eng.Context()
     ds = eng.DeviceScene.from_host(sc)
-    mixed = ctx.render(ds, cams)
+    mixed = ctx.render(ds, cams, check=True)
     for b, cam in enumerate(cams):
-        alone = ctx.render(ds, [cam])[0]
+        alone = ctx.render(ds, [cam], check=True)[0]
         assert torch.equal(mixed[b], alone), b
 
 
@@ -390,7 +390,7 @@ def test_batched_train_gradient_is_mean_of_views(eng):
     for b, cam in enumerate(cams):
         c1 = eng.Context()
         g1, m1, v1 = P.zeros_like(), P.zeros_like(), P.zeros_like()
-        l1 = c1.train_step(P.clone(), g1, m1, v1, 1, [cam], tg[b:b + 1].contiguous())
+        l1 = c1.train_step(P.clone(), g1, m1, v1, 1, [cam], tg[b:b + 1].contiguous(), check=True)
         assert abs(float(l1[0]) - float(loss[b])) <= 1e-6 * max(1.0, abs(float(l1[0])))
         per.append(g1.flat().cpu().numpy().astype(np.float64))
     mean = sum(per) / len(per)
@@ -432,3 +432,128 @@ def test_train_step_c1_full_size(eng, oracle):
         assert err < GRAD_TOL, name
     m = M.flat().cpu().numpy()
     assert rel_l2(m, 0.1 * grad) < 1e-6
+
+
+# ------------------------------------------------------------------ device step counter and CUDA-graph replay
+
+def _small_train_setup(eng, seed=6):
+    sc, rng = synth.aerial_scene(40_000, n_clusters=8, seed=seed)
+    cams = synth.ring_cameras(rng, 2, (30.0, 90.0), W=192, H=108)
+    tg = torch.from_numpy(np.stack([synth.blurred_noise_target(rng, 108, 192) for _ in cams])).cuda()
+    return sc, cams, tg
+
+
+def test_device_step_counter_matches_explicit_steps(eng):
+    """step = 0 takes Adam's step from the context's device counter (1, 2, 3, ...)."""
+    sc, cams, tg = _small_train_setup(eng)
+    out = []
+    for mode in ("explicit", "device"):
+        ctx = eng.Context()
+        P = eng.DeviceScene.from_host(sc)
+        G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
+        for k in range(3):
+            ctx.train_step(P, G, M, V, k + 1 if mode == "explicit" else 0, cams, tg)
+        torch.cuda.synchronize()
+        out.append(P.flat().cpu().numpy().astype(np.float64))
+    assert rel_l2(out[1], out[0]) < 1e-6
+
+
+def test_cuda_graph_replay_matches_direct_calls(eng):
+    """A captured training step replayed three times equals three direct calls
+    (up to the reordering of float atomics)."""
+    sc, cams, tg = _small_train_setup(eng, seed=7)
+    res = []
+    for use_graph in (False, True):
+        ctx = eng.Context()
+        P = eng.DeviceScene.from_host(sc)
+        G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
+        loss = torch.empty(len(cams), device="cuda")
+        ctx.train_step(P, G, M, V, 0, cams, tg, loss_out=loss)     # sizes the scratch (step 1)
+        if use_graph:
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=side):
+                ctx.train_step(P, G, M, V, 0, cams, tg, loss_out=loss)
+            for _ in range(3):
+                g.replay()
+        else:
+            for _ in range(3):
+                ctx.train_step(P, G, M, V, 0, cams, tg, loss_out=loss)
+        torch.cuda.synchronize()
+        assert ctx.status()[0] == 0
+        res.append((P.flat().cpu().numpy().astype(np.float64), float(loss[0])))
+    assert rel_l2(res[1][0], res[0][0]) < 1e-6
+    assert abs(res[1][1] - res[0][1]) < 1e-5 * abs(res[0][1])
+
+
+# ------------------------------------------------------------------ serving: each result equals its render alone
+
+def test_serving_results_equal_rendering_alone(eng):
+    """Requests of mixed sizes arrive while others render; every served image
+    equals the same view rendered alone, bit for bit."""
+    from paper_2406_18533_gb300 import serve
+    sc, rng = synth.aerial_scene(80_000, n_clusters=12, seed=9)
+    sizes = [(160, 90), (320, 180), (97, 61), (480, 270)]
+    reqs = []
+    for i in range(24):
+        W, H = sizes[i % 4]
+        cam = synth.ring_cameras(rng, 1, (25.0, 110.0), W=W, H=H)[0]
+        reqs.append(serve.Request(i, 0.004 * i, cam))
+    ds = eng.DeviceScene.from_host(sc)
+    server = serve.RenderServer(ds, n_slots=2, max_batch=4, max_pixels=4 * 480 * 270, frag_capacity=50_000)
+    done = server.run(reqs)
+    assert len(done) == 24 and server.batches >= 6
+    alone = eng.Context()
+    for r in done:
+        ref = alone.render(ds, [r.cam], check=True)[0]
+        assert torch.equal(r.image, ref), r.rid
+    rep = serve.latency_report(done)
+    assert rep["p50_ms"] > 0 and rep["p99_ms"] >= rep["p50_ms"]
+
+
+def test_train_step_recovers_from_fragment_overflow(eng):
+    """A context reserved far too small overflows on its first step: the
+    update is skipped (parameters unchanged), the checked step grows the buffer
+    and runs the same step, matching a context that was sized correctly."""
+    sc, cams, tg = _small_train_setup(eng, seed=8)
+    ref_ctx = eng.Context()
+    P0 = eng.DeviceScene.from_host(sc)
+    Pa = P0.clone()
+    Ga, Ma, Va = Pa.zeros_like(), Pa.zeros_like(), Pa.zeros_like()
+    ref_ctx.train_step(Pa, Ga, Ma, Va, 1, cams, tg, check=True)
+    small = eng.Context()
+    small.reserve(sc.N, cams, 64)
+    Pb = P0.clone()
+    Gb, Mb, Vb = Pb.zeros_like(), Pb.zeros_like(), Pb.zeros_like()
+    small.train_step(Pb, Gb, Mb, Vb, 1, cams, tg)                 # overflows: no update
+    torch.cuda.synchronize()
+    code, needed = small.status()
+    from paper_2406_18533_gb300 import binding as b
+    assert code == b.GS_ERR_CAPACITY and needed > 64
+    assert torch.equal(Pb.flat(), P0.flat())
+    small.train_step(Pb, Gb, Mb, Vb, 1, cams, tg, check=True)
+    torch.cuda.synchronize()
+    assert rel_l2(Pb.flat().cpu().numpy(), Pa.flat().cpu().numpy()) < 1e-6
+
+
+def test_c2_full_size_sampled_views(eng, oracle):
+    """The 4M-Gaussian, 16-view 1080p batch rendered in one call (the launch
+    configuration of the batched training step's forward): two sampled views
+    against the FP64 oracle, and their L1 + SSIM losses."""
+    sc, cams, tg = synth.workload_c2()
+    ctx = eng.Context()
+    P = eng.DeviceScene.from_host(sc)
+    imgs = ctx.render(P, cams, check=True)
+    for b in (0, 11):
+        fw = oracle.render(sc, cams[b])
+        flag, nborder = _flags_from_oracle(oracle, fw, cams[b])
+        gi = imgs[b].cpu().numpy()
+        err = float(np.abs(gi - fw["img"])[:, ~flag].max())
+        print(f"C2 view {b}: flagged {flag.mean():.4f}, image max abs err {err:.2e}")
+        assert flag.mean() < 0.08
+        assert err <= IMG_TOL
+        loss, _ = ctx.loss(imgs[b][None].contiguous(), torch.from_numpy(tg[b:b + 1]).cuda())
+        L, _, _, _ = oracle.ssim_loss(fw["img"], tg[b])
+        assert abs(float(loss[0]) - L) < 1e-4 * abs(L)
