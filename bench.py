@@ -217,7 +217,10 @@ def stage_roofline(stage, ms, counters, N, Bv, pixels, passes, peaks, clock_mhz)
     elif stage == "loss":
         byt = pixels * 3 * 44.0
     elif stage == "emit":
-        byt = F * 12.0 + Bv * N * 16.0
+        byt = F * 12.0 + Bv * N * 24.0
+    elif stage == "order":
+        # depth keys (16 B/pair), histogram + 4 pair-sort passes (68), count gather (12), scan (12)
+        byt = Bv * N * 108.0
     else:
         byt = Bv * N * 8.0
     return dict(bound="hbm", achieved=byt / sec / 1e9, peak=hbm, unit="GB/s", work_desc=f"{byt:.3e} bytes")
@@ -230,6 +233,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     peaks, peak_kind = load_peaks()
     name, sc, cams, tg, extent = make_workload(args.workload)
+    if args.views:
+        cams, tg = cams[:args.views], tg[:args.views]
+        name += f"_first{args.views}views"
     lr6 = lr_groups(extent)
     Bv = len(cams)
     H, W = cams[0].H, cams[0].W
@@ -390,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
     high = 0
     while (1 << high) < engine.total_tiles(cams, args.tile):
         high += 1
-    passes = 4 + (high + 7) // 8
+    passes = (high + 7) // 8             # fragment sort: the tile-id digits only
     clk = clocks.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     rf = stage_roofline(dom, stage_ms[dom], counters, sc.N, Bv, Bv * H * W, passes, peaks, clk)
     roofline = {"kernel": dom, "bound": rf["bound"], "achieved": rf["achieved"], "peak": rf["peak"],
@@ -522,7 +528,9 @@ def main():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-view", action="store_true")
-    ap.add_argument("--graph", action="store_true", help="replay one captured training step (CUDA graph)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="call gs_train_step directly instead of replaying one captured step (CUDA graph)")
+    ap.add_argument("--views", type=int, default=0, help="use only the first K views of the workload (profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

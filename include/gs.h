@@ -175,8 +175,9 @@ gs_status gs_get_counters(gs_ctx *ctx, void *stream, uint64_t out[5]);
  * recorded step s and stage k, the elapsed milliseconds to
  * ms[s * GS_TRACE_STAGES + k] (ms holds max_steps * GS_TRACE_STAGES floats),
  * sets *steps to the number of recorded steps and restarts recording.
- * Stage order: preprocess, scan, emit, sort, ranges, blend_fwd, loss,
- * zero_grad, blend_bwd, preprocess_bwd, adam.
+ * Stage order: preprocess, order (pairs sorted by depth + offsets scan),
+ * emit, sort (fragments by tile), ranges, blend_fwd, loss, zero_grad,
+ * blend_bwd, preprocess_bwd, adam.
  */
 #define GS_TRACE_STAGES 11
 gs_status gs_trace_enable(gs_ctx *ctx, int32_t max_steps);
@@ -198,9 +199,10 @@ gs_status gs_preprocess(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam
 /*
  * Sec. 2.1 step 2, first half (Fig. 2 16x16 blocks; "iterates over
  * intersecting Gaussians in increasing depth"): counts the tiles each
- * (view, Gaussian) footprint rectangle covers, scans, emits one key per
- * covered tile and radix-sorts them (8-bit digits, LSD, stable), then writes
- * per-tile ranges.  If F > out->capacity nothing beyond capacity is written,
+ * (view, Gaussian) footprint rectangle covers; sorts the visible pairs by
+ * depth (stable LSD radix sort, 8-bit digits); emits one key per covered tile,
+ * pair by pair in that order; sorts the keys stably on their tile bits; and
+ * writes per-tile ranges.  If F > out->capacity nothing beyond capacity is written,
  * the status word gets GS_ERR_CAPACITY and *needed_host (if given: this call
  * then synchronises the stream) gets F and the call returns GS_ERR_CAPACITY.
  */
@@ -216,7 +218,7 @@ gs_status gs_bin(gs_ctx *ctx, const gs_proj *proj, const gs_camera *cams, int32_
  * afford cudaMalloc/cudaFree (both synchronise the device), and callers
  * without a gs_ctx (creating one allocates).
  *
- * All scratch lives in one static device array of 14.63 MiB that every GPU on
+ * All scratch lives in one static device array of 19.63 MiB that every GPU on
  * which the library's kernels are loaded holds until the process exits.
  * Limits: B * proj->N <= 262144 (view, Gaussian) pairs and out->capacity <=
  * 1048576 fragments; larger sizes, an unsupported tile (8, 16, 32) or a bad

@@ -90,7 +90,7 @@ SIGNATURES = {
 NOALLOC_MAX_PAIRS = 1 << 18
 NOALLOC_MAX_FRAGS = 1 << 20
 GS_TRACE_STAGES = 11
-TRACE_STAGES = ("preprocess", "scan", "emit", "sort", "ranges", "blend_fwd", "loss", "zero_grad", "blend_bwd",
+TRACE_STAGES = ("preprocess", "order", "emit", "sort", "ranges", "blend_fwd", "loss", "zero_grad", "blend_bwd",
                 "preprocess_bwd", "adam")
 
 _lib = None

@@ -1,5 +1,6 @@
-// K2 (exclusive scan), K3 (key emission), K4 (LSD radix sort, 8-bit digits)
-// and K5 (per-tile ranges): the "intersection test" and "increasing depth"
+// K2 (depth order of the (view, Gaussian) pairs and the offsets scan), K3
+// (fragment emission), K4 (LSD radix sort, 8- or 9-bit digits) and K5
+// (per-tile ranges): the "intersection test" and "increasing depth"
 // ordering of Sec. 2.1 step 2, built on 16x16 pixel blocks (Fig. 2).
 //
 // Sizes that depend on the data (the fragment count F) stay on the device:
@@ -125,40 +126,88 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t *in, 
     }
 }
 
-// Tiles covered by each (view, Gaussian) footprint rectangle, recomputed from
-// gs_proj with the same IEEE single operations as the transformation kernel.
-__global__ void __launch_bounds__(256) k_count_tiles(ViewBatch vb, ProjView p, uint32_t *ntiles)
+// Tile rectangle covered by a (view, Gaussian) footprint (centre uv, radius
+// r in pixels), with the same IEEE single operations as the transformation
+// kernel, packed as {x0 | x1 << 16, y0 | y1 << 16}; empty (x0 > x1) when the
+// Gaussian is culled or its footprint misses the image.  Tile coordinates fit
+// 16 bits (at most 65536 / 8 tiles per axis).
+__device__ __forceinline__ uint2 tile_rect(const ViewCam &c, float2 uv, int r, int tile)
+{
+    const uint2 empty = make_uint2(1u, 0u);
+    if (r <= 0) return empty;
+    const float rf = (float)r;
+    const float inv_tile = 1.f / (float)tile;
+    const float x0 = fmaxf(floorf(__fmul_rn(__fsub_rn(uv.x, rf), inv_tile)), 0.f);
+    const float x1 = fminf(floorf(__fmul_rn(__fadd_rn(uv.x, rf), inv_tile)), (float)(c.TX - 1));
+    const float y0 = fmaxf(floorf(__fmul_rn(__fsub_rn(uv.y, rf), inv_tile)), 0.f);
+    const float y1 = fminf(floorf(__fmul_rn(__fadd_rn(uv.y, rf), inv_tile)), (float)(c.TY - 1));
+    if (!(x0 <= x1 && y0 <= y1)) return empty;
+    return make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
+}
+
+__device__ __forceinline__ uint32_t rect_area(uint2 r)
+{
+    const uint32_t x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu, y1 = r.y >> 16;
+    return (x0 <= x1 && y0 <= y1) ? (x1 - x0 + 1u) * (y1 - y0 + 1u) : 0u;
+}
+
+// Per (view, Gaussian) pair i: its tile rectangle, and the depth key of the
+// pair sort: the float bits of the depth (positive, so they order as unsigned
+// integers); pairs that touch no tile get the largest key and sort last.
+// vals = pair index.  Also writes the pair count for the sort.
+__global__ void __launch_bounds__(256) k_pair_keys(ViewBatch vb, ProjView p, uint32_t *keys, uint32_t *vals,
+                                                   uint2 *rect, uint32_t *count)
 {
     const int64_t n = (int64_t)vb.B * p.N;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int r = p.radius[i];
-    uint32_t area = 0;
-    if (r > 0) {
-        const ViewCam &c = vb.v[(int)(i / p.N)];
-        const float2 uv = p.xy[i];
-        const float rf = (float)r;
-        const float inv_tile = 1.f / (float)vb.tile;
-        const float x0 = fmaxf(floorf(__fmul_rn(__fsub_rn(uv.x, rf), inv_tile)), 0.f);
-        const float x1 = fminf(floorf(__fmul_rn(__fadd_rn(uv.x, rf), inv_tile)), (float)(c.TX - 1));
-        const float y0 = fmaxf(floorf(__fmul_rn(__fsub_rn(uv.y, rf), inv_tile)), 0.f);
-        const float y1 = fminf(floorf(__fmul_rn(__fadd_rn(uv.y, rf), inv_tile)), (float)(c.TY - 1));
-        if (x0 <= x1 && y0 <= y1) area = (uint32_t)((int)(x1 - x0) + 1) * (uint32_t)((int)(y1 - y0) + 1);
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i0 == 0) *count = (uint32_t)n;
+    for (int64_t i = i0; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 rc = tile_rect(vb.v[(int)(i / p.N)], p.xy[i], p.radius[i], vb.tile);
+        rect[i] = rc;
+        const float depth = reinterpret_cast<const float *>(p.rgb_d)[4 * i + 3];
+        keys[i] = rect_area(rc) > 0u ? __float_as_uint(depth) : 0xffffffffu;
+        vals[i] = (uint32_t)i;
     }
-    ntiles[i] = area;
+}
+
+// The pairs' tile rectangles and tile counts in depth order (the counts are
+// the input of the offsets scan): one random read per pair, after which the
+// emission reads everything in order.
+__global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n,
+                                                       uint32_t *counts, uint32_t *rx, uint32_t *ry)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t o = order[j];
+        const uint2 rc = o < n ? rect[o] : make_uint2(1u, 0u);   // o >= n only after a failed (timed-out) pair sort
+        counts[j] = rect_area(rc);
+        rx[j] = rc.x;
+        ry[j] = rc.y;
+    }
 }
 
 // ---------------------------------------------------------------- K3 emit
 
-__global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, ProjView p, const uint32_t *ntiles,
-                                                   const uint32_t *offsets, uint64_t *keys, uint32_t *vals,
-                                                   uint64_t capacity, const unsigned long long *total,
-                                                   DevStatus *status, uint32_t *count_out)
+// Emits the fragments of pair order[j] at offsets[j]: key = global tile id,
+// value = Gaussian index.  Visiting the pairs in depth order puts every
+// tile's fragments in (depth, index) order, so a stable sort on the tile id
+// alone finishes the job.  A warp expands its 32 pairs together: output slot
+// f of the warp's range goes to lane f mod 32, which finds its pair by binary
+// search over the lanes' offsets, so consecutive lanes store consecutive
+// addresses.  Thread 0 publishes F (status, count_out); nothing is written
+// past capacity.
+__global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, const uint32_t *order,
+                                                   const uint32_t *rx, const uint32_t *ry,
+                                                   const uint32_t *offsets, uint32_t *keys,
+                                                   uint32_t *vals, uint64_t capacity,
+                                                   const unsigned long long *total, DevStatus *status,
+                                                   uint32_t *count_out)
 {
-    const int64_t n = (int64_t)vb.B * p.N;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)vb.B * N;
+    const int lane = threadIdx.x & 31;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t j0 = j - lane;                 // the warp's first pair
     const unsigned long long F = *total;
-    if (i == 0) {
+    if (j == 0) {
         status->needed = F;
         status->counters[0] = F;
         status->counters[1] = 0ull;
@@ -171,188 +220,363 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, ProjView p, con
             *count_out = (uint32_t)F;
         }
     }
-    if (F > capacity || i >= n) return;
-    const uint32_t cnt = ntiles[i];
-    if (cnt == 0) return;
-    const int v = (int)(i / p.N);
-    const uint32_t g = (uint32_t)(i - (int64_t)v * p.N);
-    const ViewCam &c = vb.v[v];
-    const float2 uv = p.xy[i];
-    const float rf = (float)p.radius[i];
-    const float inv_tile = 1.f / (float)vb.tile;
-    int x0 = (int)fmaxf(floorf(__fmul_rn(__fsub_rn(uv.x, rf), inv_tile)), 0.f);
-    int x1 = (int)fminf(floorf(__fmul_rn(__fadd_rn(uv.x, rf), inv_tile)), (float)(c.TX - 1));
-    int y0 = (int)fmaxf(floorf(__fmul_rn(__fsub_rn(uv.y, rf), inv_tile)), 0.f);
-    int y1 = (int)fminf(floorf(__fmul_rn(__fadd_rn(uv.y, rf), inv_tile)), (float)(c.TY - 1));
-    const uint32_t dbits = __float_as_uint(p.rgb_d[i].w);
-    uint64_t o = offsets[i];
-    for (int ty = y0; ty <= y1; ++ty)
-        for (int tx = x0; tx <= x1; ++tx) {
-            const uint64_t tid = (uint64_t)c.tile_base + (uint64_t)ty * c.TX + tx;
-            keys[o] = (tid << 32) | dbits;
-            vals[o] = g;
-            ++o;
+    if (F > capacity || j0 >= n) return;         // uniform over the warp
+    uint32_t start = 0u, cnt = 0u, g = 0u, corner = 0u, wdt = 1u, tx_row = 0u;
+    if (j < n) {
+        start = offsets[j];
+        const int64_t i = (int64_t)order[j];
+        const uint2 rc = make_uint2(rx[j], ry[j]);
+        cnt = rect_area(rc);                     // 0 where the pair sort failed (i >= n)
+        if (cnt && i < n) {
+            const int v = (int)(i / N);
+            g = (uint32_t)(i - (int64_t)v * N);
+            const uint32_t x0 = rc.x & 0xffffu;
+            wdt = (rc.x >> 16) - x0 + 1u;
+            tx_row = (uint32_t)vb.v[v].TX;
+            corner = vb.v[v].tile_base + (rc.y & 0xffffu) * tx_row + x0;   // tile (x0, y0)
         }
+    }
+    const int last = (int)(n - 1 - j0 < 31 ? n - 1 - j0 : 31);
+    const uint32_t base = __shfl_sync(0xffffffffu, start, 0);
+    const uint32_t span = __shfl_sync(0xffffffffu, start + cnt, last) - base;
+    const uint32_t rel = j < n ? start - base : span;   // lanes past n never match
+    for (uint32_t r0 = 0; r0 < span; r0 += 32) {
+        const uint32_t f = r0 + lane;
+        int L = 0;                               // last lane with rel <= f
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t s = __shfl_sync(0xffffffffu, rel, L + step);
+            if (s <= f) L += step;
+        }
+        const uint32_t lrel = __shfl_sync(0xffffffffu, rel, L);
+        const uint32_t lw = __shfl_sync(0xffffffffu, wdt, L);
+        const uint32_t ltx = __shfl_sync(0xffffffffu, tx_row, L);
+        const uint32_t lc = __shfl_sync(0xffffffffu, corner, L);
+        const uint32_t lg = __shfl_sync(0xffffffffu, g, L);
+        if (f < span) {
+            const uint32_t local = f - lrel;
+            const uint32_t dy = local / lw;
+            const uint64_t o = (uint64_t)base + f;
+            keys[o] = lc + dy * ltx + (local - dy * lw);
+            vals[o] = lg;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- K4 radix sort (one-sweep)
 //
-// LSD radix sort on 8-bit digits of the 64-bit keys (only the digits that can
-// be nonzero: 4 depth bytes + the tile-id bytes), stable, so equal keys keep
-// the emission order (ascending Gaussian index).  An upfront kernel
-// histograms every digit position in one read of the keys; each pass is then
-// a single kernel: a CTA takes the next tile of RS_TILE keys (tile order =
-// launch order, from an atomic counter), ranks its keys stably in shared
-// memory, publishes its per-digit counts, and finds the keys of all earlier
-// tiles with the same digit by a decoupled look-back over their published
-// counts, so each pass reads and writes the keys once.
-
+// LSD radix sort of 32-bit keys with 32-bit values on RB-bit digits (RB = 8
+// or 9), stable.  An upfront kernel histograms every digit position in one
+// read of the keys; each pass is then a single kernel: a CTA takes the next
+// tile of RS_TILE keys (tile order = launch order, from an atomic counter),
+// ranks its keys stably, publishes its per-digit counts, finds the keys of
+// all earlier tiles per digit by decoupled look-back, stages its keys in
+// shared memory in output order and writes them out so that consecutive
+// threads store consecutive addresses of a digit's run.  The look-back spin
+// is bounded: a wait that runs out sets GS_ERR_TIMEOUT and the pass finishes
+// with in-bounds (but wrong) positions instead of hanging.
 constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
 constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;
 constexpr int RS_WARP_KEYS = 32 * RS_ITEMS;         // 512 consecutive keys per warp
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;      // 4096 keys per tile
-constexpr int RS_MAX_PASSES = 8;
+constexpr int RS_MAX_PASSES = 4;
+constexpr int RS_MAX_NB = 512;
 constexpr uint32_t LB_AGG = 1u << 30;               // look-back flag: tile count available
 constexpr uint32_t LB_PRE = 2u << 30;               // look-back flag: inclusive prefix available
 constexpr uint32_t LB_VAL = (1u << 30) - 1u;
 constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;
+constexpr int LB_BATCH = 8;                         // look-back words read per round
 
-__global__ void __launch_bounds__(RS_THREADS) k_digit_hist(const uint64_t *keys, const uint32_t *count, int passes,
+// Digit histograms of every pass.  A thread takes 16 consecutive keys (four
+// 16-byte loads: the key buffers are 16-byte aligned) and adds runs of equal
+// digits at once, which keeps the shared-memory atomics of skewed digit
+// positions (float exponents, the high bits of tile ids) few.
+template <int RB>
+__global__ void __launch_bounds__(RS_THREADS) k_digit_hist(const uint32_t *keys, const uint32_t *count, int passes,
                                                            uint32_t *ghist)
 {
-    __shared__ uint32_t h[RS_MAX_PASSES][256];
-    for (int i = threadIdx.x; i < RS_MAX_PASSES * 256; i += RS_THREADS) h[i / 256][i % 256] = 0u;
+    constexpr int NB = 1 << RB;
+    __shared__ uint32_t h[RS_MAX_PASSES * NB];
+    for (int i = threadIdx.x; i < RS_MAX_PASSES * NB; i += RS_THREADS) h[i] = 0u;
     __syncthreads();
     const uint32_t n = *count;
-    for (uint64_t i = blockIdx.x * (uint64_t)RS_THREADS + threadIdx.x; i < n; i += (uint64_t)gridDim.x * RS_THREADS) {
-        const uint64_t k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(uint32_t)(k >> (8 * p)) & 255u], 1u);
+    const uint64_t chunks = ((uint64_t)n + 15) / 16;
+    for (uint64_t c = blockIdx.x * (uint64_t)RS_THREADS + threadIdx.x; c < chunks;
+         c += (uint64_t)gridDim.x * RS_THREADS) {
+        const uint64_t b = c * 16;
+        const int m = (int)((uint64_t)n - b < 16 ? (uint64_t)n - b : 16);
+        uint32_t k[16];
+        if (m == 16) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(keys + b);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint4 x = q[u];
+                k[4 * u] = x.x;
+                k[4 * u + 1] = x.y;
+                k[4 * u + 2] = x.z;
+                k[4 * u + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) k[u] = u < m ? keys[b + u] : 0u;
+        }
+        for (int p = 0; p < passes; ++p) {
+            const int sh = RB * p;
+            uint32_t cur = (k[0] >> sh) & (uint32_t)(NB - 1), run = 1;
+#pragma unroll
+            for (int u = 1; u < 16; ++u) {
+                if (u < m) {
+                    const uint32_t d = (k[u] >> sh) & (uint32_t)(NB - 1);
+                    if (d == cur) {
+                        ++run;
+                    } else {
+                        atomicAdd(&h[p * NB + cur], run);
+                        cur = d;
+                        run = 1;
+                    }
+                }
+            }
+            atomicAdd(&h[p * NB + cur], run);
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += RS_THREADS) {
-        const uint32_t c = h[i / 256][i % 256];
+    for (int i = threadIdx.x; i < passes * NB; i += RS_THREADS) {
+        const uint32_t c = h[i];
         if (c) atomicAdd(&ghist[i], c);
     }
 }
 
-// Exclusive scan of each pass's 256 digit counts (one CTA per pass).
-__global__ void __launch_bounds__(256) k_digit_offsets(uint32_t *ghist)
+// Exclusive scan of each pass's digit counts (one CTA per pass).
+template <int RB>
+__global__ void __launch_bounds__(RS_THREADS) k_digit_offsets(uint32_t *ghist)
 {
+    constexpr int NB = 1 << RB, DPT = NB / RS_THREADS;
     __shared__ uint32_t sw[33];
-    uint32_t *h = ghist + 256 * blockIdx.x;
-    const uint32_t x = h[threadIdx.x];
+    uint32_t *h = ghist + NB * blockIdx.x;
+    uint32_t x[DPT], s = 0;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+        x[k] = h[threadIdx.x * DPT + k];
+        s += x[k];
+    }
     uint32_t excl;
-    block_excl_scan(x, excl, sw);
-    h[threadIdx.x] = excl;
+    block_excl_scan(s, excl, sw);
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+        h[threadIdx.x * DPT + k] = excl;
+        excl += x[k];
+    }
 }
 
-// Ranking: warp w owns the 512 consecutive keys t0 + w*512 + [0, 512), item i
-// of lane l being key t0 + w*512 + 32 i + l.  Items are ranked in order with
-// __match_any_sync against per-warp running digit counts, so ranks are stable
-// within the warp; one block-wide prefix over the warps' counts then orders
-// the warps.  Two block barriers per 4096-key tile.
-__global__ void __launch_bounds__(RS_THREADS) k_onesweep(const uint64_t *kin, const uint32_t *vin, uint64_t *kout,
-                                                         uint32_t *vout, const uint32_t *count, int shift,
-                                                         const uint32_t *doff, uint32_t *look, uint32_t *tile_ctr,
-                                                         DevStatus *status)
+// Ranking: warp w owns the RS_WARP_KEYS consecutive keys t0 + w*RS_WARP_KEYS
+// + [0, RS_WARP_KEYS), item i of lane l being key t0 + w*RS_WARP_KEYS + 32 i
+// + l.  Items are ranked in order with __match_any_sync against per-warp
+// running digit counts, so ranks are stable within the warp; per-digit
+// prefixes over the warps and over the digits then give every key its
+// position in the tile's output order.
+template <int RB>
+__global__ void __launch_bounds__(RS_THREADS, 4) k_onesweep(const uint32_t *kin, const uint32_t *vin,
+                                                            uint32_t *kout, uint32_t *vout, const uint32_t *count,
+                                                            int shift, const uint32_t *doff, uint32_t *look,
+                                                            uint32_t *tile_ctr, DevStatus *status)
 {
-    __shared__ uint32_t wcnt[RS_WARPS][256];
-    __shared__ uint32_t gbase[256];
+    constexpr int NB = 1 << RB, DPT = NB / RS_THREADS;
+    constexpr int UNION_WORDS = RS_WARPS * NB > 2 * RS_TILE ? RS_WARPS * NB : 2 * RS_TILE;
+    __shared__ __align__(16) uint32_t sm[UNION_WORDS];
+    __shared__ uint32_t gofs[NB];
+    __shared__ uint32_t sw[33];
     __shared__ uint32_t s_tile;
+    uint32_t *wcnt = sm;                              // ranking: [RS_WARPS][NB] running counts
+    uint32_t *skey = sm, *sval = sm + RS_TILE;        // afterwards: the tile in output order
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const uint32_t n = *count;
     if (t == 0) s_tile = atomicAdd(tile_ctr, 1u);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) wcnt[w][lane + 32 * j] = 0u;
+    for (int j = t; j < RS_WARPS * NB; j += RS_THREADS) wcnt[j] = 0u;
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t t0 = (uint64_t)tile * RS_TILE;
     if (t0 >= n) return;
     const uint32_t lt = lanemask_lt();
     const uint64_t wb = t0 + (uint64_t)w * RS_WARP_KEYS;
-    uint64_t key[RS_ITEMS];
-    uint32_t val[RS_ITEMS], rank[RS_ITEMS];
+    uint32_t key[RS_ITEMS], pos[RS_ITEMS];
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const uint64_t idx = wb + 32 * i + lane;
-        const bool valid = idx < n;
-        key[i] = valid ? kin[idx] : 0ull;
-        val[i] = valid ? vin[idx] : 0u;
+        key[i] = idx < n ? kin[idx] : 0u;
     }
+    uint32_t *mycnt = wcnt + w * NB;
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const bool valid = wb + 32 * i + lane < n;
-        const uint32_t d = valid ? ((uint32_t)(key[i] >> shift) & 255u) : 256u;
+        const uint32_t d = valid ? ((key[i] >> shift) & (uint32_t)(NB - 1)) : (uint32_t)NB;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t base = valid ? wcnt[w][d] : 0u;
-        rank[i] = base + __popc(peers & lt);
+        const uint32_t base = valid ? mycnt[d] : 0u;
+        pos[i] = base + __popc(peers & lt);
         __syncwarp();
-        if (valid && (peers & lt) == 0u) wcnt[w][d] = base + __popc(peers);
+        if (valid && (peers & lt) == 0u) mycnt[d] = base + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // digit t: exclusive prefix over the warps, tile count, look-back over earlier tiles
-    uint32_t mine = 0;
+    // thread t owns digits t*DPT .. t*DPT + DPT - 1: warp prefixes in place, tile counts
+    uint32_t cnt[DPT];
 #pragma unroll
-    for (int j = 0; j < RS_WARPS; ++j) {
-        const uint32_t c = wcnt[j][t];
-        wcnt[j][t] = mine;
-        mine += c;
-    }
-    uint32_t *lk = look + (size_t)tile * 256 + t;
-    if (tile == 0) {
-        atomicExch(lk, LB_PRE | mine);
-        gbase[t] = doff[t];
-    } else {
-        atomicExch(lk, LB_AGG | mine);
-        uint32_t excl = 0;
-        bool timed_out = false;
-        for (int64_t pt = (int64_t)tile - 1; pt >= 0; --pt) {
-            const volatile uint32_t *q = look + (size_t)pt * 256 + t;
-            uint32_t v = *q, spins = 0;
-            while ((v & (LB_AGG | LB_PRE)) == 0u) {
-                if (++spins > LB_SPIN_LIMIT) {       // give up: report instead of hanging
-                    atomicCAS(&status->code, 0, (int)GS_ERR_TIMEOUT);
-                    timed_out = true;
-                    break;
-                }
-                v = *q;
-            }
-            excl += v & LB_VAL;
-            if ((v & LB_PRE) || timed_out) break;
+    for (int k = 0; k < DPT; ++k) {
+        const int d = t * DPT + k;
+        uint32_t run = 0;
+#pragma unroll
+        for (int j = 0; j < RS_WARPS; ++j) {
+            const uint32_t c = wcnt[j * NB + d];
+            wcnt[j * NB + d] = run;
+            run += c;
         }
-        atomicExch(lk, LB_PRE | (excl + mine));
-        gbase[t] = doff[t] + excl;
+        cnt[k] = run;
+        atomicExch(look + (size_t)tile * NB + d, (tile == 0 ? LB_PRE : LB_AGG) | run);
+    }
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) tsum += cnt[k];
+    uint32_t start;
+    block_excl_scan(tsum, start, sw);                // tile-local start of digit t*DPT
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+        const int d = t * DPT + k;
+        uint32_t excl = 0;
+        if (tile > 0) {
+            // walk back over earlier tiles, LB_BATCH words in flight at a time
+            int64_t pt = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            while (true) {
+                uint32_t v[LB_BATCH];
+#pragma unroll
+                for (int b = 0; b < LB_BATCH; ++b)
+                    v[b] = pt - b >= 0 ? *(const volatile uint32_t *)(look + (size_t)(pt - b) * NB + d) : LB_PRE;
+                bool stop = false, blocked = false;
+#pragma unroll
+                for (int b = 0; b < LB_BATCH; ++b) {
+                    if (!stop && !blocked) {
+                        if ((v[b] & (LB_AGG | LB_PRE)) == 0u) {
+                            blocked = true;              // not published yet: read again from here
+                        } else {
+                            excl += v[b] & LB_VAL;
+                            --pt;
+                            stop = (v[b] & LB_PRE) != 0u;
+                        }
+                    }
+                }
+                if (stop) break;
+                if (blocked) {                       // wait on that word alone, then read a batch again
+                    const volatile uint32_t *q = look + (size_t)pt * NB + d;
+                    bool timed_out = false;
+                    while ((*q & (LB_AGG | LB_PRE)) == 0u) {
+                        if (++spins > LB_SPIN_LIMIT) {   // give up: report instead of hanging
+                            atomicCAS(&status->code, 0, (int)GS_ERR_TIMEOUT);
+                            timed_out = true;
+                            break;
+                        }
+                    }
+                    if (timed_out) break;
+                }
+            }
+            atomicExch(look + (size_t)tile * NB + d, LB_PRE | (excl + cnt[k]));
+        }
+#pragma unroll
+        for (int j = 0; j < RS_WARPS; ++j) wcnt[j * NB + d] += start;
+        gofs[d] = doff[d] + excl - start;             // output index = gofs[d] + tile position
+        start += cnt[k];
     }
     __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i)
+        if (wb + 32 * i + lane < n) pos[i] += mycnt[(key[i] >> shift) & (uint32_t)(NB - 1)];
+    __syncthreads();                                  // the counts are dead: stage the tile over them
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const uint64_t idx = wb + 32 * i + lane;
         if (idx < n) {
-            const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
-            const uint32_t dst = gbase[d] + wcnt[w][d] + rank[i];
-            kout[dst] = key[i];
-            vout[dst] = val[i];
+            skey[pos[i]] = key[i];
+            sval[pos[i]] = vin[idx];                  // values are read only now, to save registers
+        }
+    }
+    __syncthreads();
+    const uint32_t tile_n = (uint32_t)((uint64_t)n - t0 < (uint64_t)RS_TILE ? (uint64_t)n - t0 : (uint64_t)RS_TILE);
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const uint32_t idx = (uint32_t)(k * RS_THREADS + t);
+        if (idx < tile_n) {
+            const uint32_t kk = skey[idx];
+            const uint32_t dst = gofs[(kk >> shift) & (uint32_t)(NB - 1)] + idx;
+            kout[dst] = kk;
+            vout[dst] = sval[idx];
         }
     }
 }
 
 // ---------------------------------------------------------------- K5 ranges
 
-__global__ void __launch_bounds__(256) k_tile_ranges(const uint64_t *keys, const uint32_t *count, uint2 *ranges,
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t *keys, const uint32_t *count, uint2 *ranges,
                                                      uint32_t total_tiles)
 {
+    // four keys per thread (one 16-byte load: the key buffers are 16-byte aligned)
     const uint32_t n = *count;
-    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t tile = (uint32_t)(keys[i] >> 32);
-    if (tile >= total_tiles) return;
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != tile) ranges[tile].x = (uint32_t)i;
-    if (i + 1 == n || (uint32_t)(keys[i + 1] >> 32) != tile) ranges[tile].y = (uint32_t)(i + 1);
+    const uint64_t quads = ((uint64_t)n + 3) / 4;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < quads; q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i0 = 4 * q;
+        uint32_t k[6];                            // keys i0-1 .. i0+4
+        k[0] = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+        if (i0 + 4 <= n) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(keys + i0);
+            k[1] = x.x; k[2] = x.y; k[3] = x.z; k[4] = x.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k[1 + u] = i0 + u < n ? keys[i0 + u] : 0xffffffffu;
+        }
+        k[5] = i0 + 4 < n ? keys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t i = i0 + u;
+            const uint32_t tile = k[1 + u];
+            if (i >= n || tile >= total_tiles) continue;
+            if (i == 0 || k[u] != tile) ranges[tile].x = (uint32_t)i;
+            if (i + 1 == n || k[2 + u] != tile) ranges[tile].y = (uint32_t)(i + 1);
+        }
+    }
+}
+
+// The 64-bit fragment keys of the binning's public output: tile id << 32 |
+// float bits of the fragment's depth in its view.
+__global__ void __launch_bounds__(256) k_compose_keys(ViewBatch vb, int64_t N, const uint32_t *tiles,
+                                                      const uint32_t *vals, const uint32_t *count,
+                                                      const float4 *rgb_d, uint64_t *keys)
+{
+    const uint32_t n = *count;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t tile = tiles[i], g = vals[i];
+        int v = 0;
+        while (v + 1 < vb.B && vb.v[v + 1].tile_base <= tile) ++v;
+        // g >= N only after a failed (timed-out) sort, which the status reports
+        const float depth =
+            (int64_t)g < N ? reinterpret_cast<const float *>(rgb_d)[4 * ((int64_t)v * N + g) + 3] : 0.f;
+        keys[i] = ((uint64_t)tile << 32) | __float_as_uint(depth);
+    }
 }
 
 }  // namespace
+
+// Blocks of 256 threads for a grid-stride loop over `items`: enough to fill
+// every SM several times, no more (small blocks are bound by block launches).
+static unsigned stride_blocks(uint64_t items)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0, m = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+        sms = m;
+    }
+    const uint64_t need = (items + 255) / 256, cap = (uint64_t)sms * 16;
+    return (unsigned)(need < 1 ? 1 : need < cap ? need : cap);
+}
 
 size_t scan_temp_bytes(int64_t n)
 {
@@ -375,21 +599,29 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigne
     count_launches(3);
 }
 
-void launch_count_tiles(const ViewBatch &vb, const ProjView &p, uint32_t *ntiles, cudaStream_t st)
+void launch_pair_keys(const ViewBatch &vb, const ProjView &p, uint32_t *keys, uint32_t *vals, uint2 *rect,
+                      uint32_t *count, cudaStream_t st)
 {
     const int64_t n = (int64_t)vb.B * p.N;
-    if (n <= 0) return;
-    k_count_tiles<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vb, p, ntiles);
+    k_pair_keys<<<stride_blocks(n > 0 ? (uint64_t)n : 1), 256, 0, st>>>(vb, p, keys, vals, rect, count);
     count_launches(1);
 }
 
-void launch_emit_keys(const ViewBatch &vb, const ProjView &p, const uint32_t *ntiles, const uint32_t *offsets,
-                       uint64_t *keys, uint32_t *vals, uint64_t capacity, const unsigned long long *total,
-                       DevStatus *status, uint32_t *count_out, cudaStream_t st)
+void launch_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n, uint32_t *counts, uint32_t *rx,
+                          uint32_t *ry, cudaStream_t st)
 {
-    const int64_t n = (int64_t)vb.B * p.N;
+    if (n <= 0) return;
+    k_gather_counts<<<stride_blocks((uint64_t)n), 256, 0, st>>>(order, rect, n, counts, rx, ry);
+    count_launches(1);
+}
+
+void launch_emit_keys(const ViewBatch &vb, int64_t N, const uint32_t *order, const uint32_t *rx, const uint32_t *ry,
+                      const uint32_t *offsets, uint32_t *keys, uint32_t *vals, uint64_t capacity,
+                      const unsigned long long *total, DevStatus *status, uint32_t *count_out, cudaStream_t st)
+{
+    const int64_t n = (int64_t)vb.B * N;
     const int64_t blocks = n > 0 ? (n + 255) / 256 : 1;
-    k_emit_keys<<<(unsigned)blocks, 256, 0, st>>>(vb, p, ntiles, offsets, keys, vals, capacity, total, status,
+    k_emit_keys<<<(unsigned)blocks, 256, 0, st>>>(vb, N, order, rx, ry, offsets, keys, vals, capacity, total, status,
                                                  count_out);
     count_launches(1);
 }
@@ -397,48 +629,90 @@ void launch_emit_keys(const ViewBatch &vb, const ProjView &p, const uint32_t *nt
 size_t sort_temp_bytes(uint64_t capacity)
 {
     const uint64_t tiles = capacity > 0 ? (capacity + RS_TILE - 1) / RS_TILE : 1;
-    // digit offsets (passes x 256), tile counters, look-back words (tiles x 256)
-    return (size_t)RS_MAX_PASSES * 256 * 4 + 256 + (size_t)tiles * 256 * 4 + 256;
+    // digit offsets (passes x NB), tile counters, look-back words (tiles x NB)
+    return (size_t)RS_MAX_PASSES * RS_MAX_NB * 4 + 256 + (size_t)tiles * RS_MAX_NB * 4 + 256;
 }
 
-void launch_radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
-                       const uint32_t *count, int high_bits, void *temp, DevStatus *status, cudaStream_t st)
+template <int RB>
+static void radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
+                       const uint32_t *count, int passes, void *temp, DevStatus *status, cudaStream_t st)
 {
-    if (capacity == 0) return;
-    const int passes = 4 + (high_bits + 7) / 8;
+    constexpr int NB = 1 << RB;
+    if (capacity == 0 || passes <= 0) return;
     const uint64_t tiles = (capacity + RS_TILE - 1) / RS_TILE;
     char *tp = reinterpret_cast<char *>(temp);
     uint32_t *ghist = reinterpret_cast<uint32_t *>(tp);
-    uint32_t *ctr = reinterpret_cast<uint32_t *>(tp + (size_t)RS_MAX_PASSES * 256 * 4);
-    uint32_t *look = reinterpret_cast<uint32_t *>(tp + (size_t)RS_MAX_PASSES * 256 * 4 + 256);
-    cudaMemsetAsync(tp, 0, (size_t)RS_MAX_PASSES * 256 * 4 + 256, st);
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(tp + (size_t)RS_MAX_PASSES * RS_MAX_NB * 4);
+    uint32_t *look = reinterpret_cast<uint32_t *>(tp + (size_t)RS_MAX_PASSES * RS_MAX_NB * 4 + 256);
+    cudaMemsetAsync(tp, 0, (size_t)RS_MAX_PASSES * RS_MAX_NB * 4 + 256, st);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     uint64_t hb = (capacity + RS_THREADS * 16 - 1) / (RS_THREADS * 16);
     if (hb > (uint64_t)sms * 8) hb = (uint64_t)sms * 8;
-    k_digit_hist<<<(unsigned)(hb ? hb : 1), RS_THREADS, 0, st>>>(keys, count, passes, ghist);
-    k_digit_offsets<<<passes, 256, 0, st>>>(ghist);
+    k_digit_hist<RB><<<(unsigned)(hb ? hb : 1), RS_THREADS, 0, st>>>(keys, count, passes, ghist);
+    k_digit_offsets<RB><<<passes, RS_THREADS, 0, st>>>(ghist);
     count_launches(2);
-    uint64_t *ki = keys, *ko = keys_alt;
-    uint32_t *vi = vals, *vo = vals_alt;
+    uint32_t *ki = keys, *ko = keys_alt, *vi = vals, *vo = vals_alt;
     for (int ps = 0; ps < passes; ++ps) {
-        cudaMemsetAsync(look, 0, (size_t)tiles * 256 * 4, st);
-        k_onesweep<<<(unsigned)tiles, RS_THREADS, 0, st>>>(ki, vi, ko, vo, count, 8 * ps, ghist + 256 * ps, look,
-                                                           ctr + ps, status);
+        cudaMemsetAsync(look, 0, (size_t)tiles * NB * 4, st);
+        k_onesweep<RB><<<(unsigned)tiles, RS_THREADS, 0, st>>>(ki, vi, ko, vo, count, RB * ps, ghist + NB * ps, look,
+                                                              ctr + ps, status);
         count_launches(1);
-        uint64_t *tk = ki; ki = ko; ko = tk;
+        uint32_t *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
     }
 }
 
-void launch_tile_ranges(const uint64_t *keys, const uint32_t *count, uint64_t capacity, uint2 *ranges,
+void launch_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
+                       const uint32_t *count, void *temp, DevStatus *status, cudaStream_t st)
+{
+    radix_sort<8>(keys, vals, keys_alt, vals_alt, capacity, count, 4, temp, status, st);
+}
+
+// Digit width and pass count for tile ids of `tile_bits` bits: 9-bit digits
+// where they save a pass (e.g. 17 bits: two passes instead of three).
+static void fragment_plan(int tile_bits, int &rb, int &passes)
+{
+    const int p8 = (tile_bits + 7) / 8, p9 = (tile_bits + 8) / 9;
+    rb = p9 < p8 ? 9 : 8;
+    passes = p9 < p8 ? p9 : p8;
+}
+
+int fragment_sort_passes(int tile_bits)
+{
+    int rb, passes;
+    fragment_plan(tile_bits, rb, passes);
+    return passes;
+}
+
+void launch_sort_fragments(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                           uint64_t capacity, const uint32_t *count, int tile_bits, void *temp, DevStatus *status,
+                           cudaStream_t st)
+{
+    int rb, passes;
+    fragment_plan(tile_bits, rb, passes);
+    if (rb == 9)
+        radix_sort<9>(keys, vals, keys_alt, vals_alt, capacity, count, passes, temp, status, st);
+    else
+        radix_sort<8>(keys, vals, keys_alt, vals_alt, capacity, count, passes, temp, status, st);
+}
+
+void launch_tile_ranges(const uint32_t *keys, const uint32_t *count, uint64_t capacity, uint2 *ranges,
                         uint32_t total_tiles, cudaStream_t st)
 {
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, st);
     if (capacity == 0) return;
-    const uint64_t blocks = (capacity + 255) / 256;
-    k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(keys, count, ranges, total_tiles);
+    k_tile_ranges<<<stride_blocks((capacity + 3) / 4), 256, 0, st>>>(keys, count, ranges, total_tiles);
+    count_launches(1);
+}
+
+void launch_compose_keys(const ViewBatch &vb, int64_t N, const uint32_t *tiles, const uint32_t *vals,
+                         const uint32_t *count, uint64_t capacity, const float4 *rgb_d, uint64_t *keys,
+                         cudaStream_t st)
+{
+    if (capacity == 0) return;
+    k_compose_keys<<<stride_blocks(capacity), 256, 0, st>>>(vb, N, tiles, vals, count, rgb_d, keys);
     count_launches(1);
 }
 

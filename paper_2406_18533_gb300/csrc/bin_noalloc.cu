@@ -19,15 +19,20 @@ constexpr int64_t NA_MAX_PAIRS = (int64_t)1 << 18;    // B * N (view, Gaussian) 
 constexpr uint64_t NA_MAX_FRAGS = (uint64_t)1 << 20;  // fragment capacity of the output
 
 // Byte layout of the scratch array (each region 256-byte aligned).
-constexpr size_t OFF_OFFSETS = 0;                                      // uint32[pairs]
-constexpr size_t OFF_NTILES = OFF_OFFSETS + 4 * (size_t)NA_MAX_PAIRS;  // uint32[pairs]
-constexpr size_t OFF_SCAN = OFF_NTILES + 4 * (size_t)NA_MAX_PAIRS;     // scan temp, 4 KiB
-constexpr size_t OFF_TOTAL = OFF_SCAN + 4096;                          // uint64 total
+constexpr size_t OFF_OFFSETS = 0;                                      // uint32[pairs] fragment offsets
+constexpr size_t OFF_RECT = OFF_OFFSETS + 4 * (size_t)NA_MAX_PAIRS;    // uint2[pairs] tile rectangles
+constexpr size_t OFF_SCAN = OFF_RECT + 8 * (size_t)NA_MAX_PAIRS;       // scan temp, 4 KiB
+constexpr size_t OFF_TOTAL = OFF_SCAN + 4096;                          // uint64 total, uint32 pair count
 constexpr size_t OFF_STATUS = OFF_TOTAL + 256;                         // DevStatus
-constexpr size_t OFF_KEYS = OFF_STATUS + 256;                          // uint64[frags]
-constexpr size_t OFF_VALS = OFF_KEYS + 8 * (size_t)NA_MAX_FRAGS;       // uint32[frags]
-constexpr size_t OFF_SORT = OFF_VALS + 4 * (size_t)NA_MAX_FRAGS;       // sort temp, 640 KiB
-constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_SORT + 640 * 1024;        // 14.63 MiB
+constexpr size_t OFF_TK = OFF_STATUS + 256;                            // uint32[frags] tile ids
+constexpr size_t OFF_TK_ALT = OFF_TK + 4 * (size_t)NA_MAX_FRAGS;       // uint32[frags]
+constexpr size_t OFF_VALS = OFF_TK_ALT + 4 * (size_t)NA_MAX_FRAGS;     // uint32[frags]
+constexpr size_t OFF_PK = OFF_VALS + 4 * (size_t)NA_MAX_FRAGS;         // uint32[pairs] depth keys
+constexpr size_t OFF_PV = OFF_PK + 4 * (size_t)NA_MAX_PAIRS;           // uint32[pairs] pair indices
+constexpr size_t OFF_PK_ALT = OFF_PV + 4 * (size_t)NA_MAX_PAIRS;       // uint32[pairs]
+constexpr size_t OFF_PV_ALT = OFF_PK_ALT + 4 * (size_t)NA_MAX_PAIRS;   // uint32[pairs]
+constexpr size_t OFF_SORT = OFF_PV_ALT + 4 * (size_t)NA_MAX_PAIRS;     // sort temp, 640 KiB
+constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_SORT + 640 * 1024;        // 19.63 MiB
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -80,7 +85,8 @@ extern "C" gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, 
     const int64_t n = (int64_t)B * proj->N;
     if (n > NA_MAX_PAIRS || out->capacity > NA_MAX_FRAGS) return GS_ERR_INVALID_ARG;   // beyond the fixed scratch
     if (n > 0 && (!proj->xy || !proj->radius || !proj->rgb_d)) return GS_ERR_INVALID_ARG;
-    if (scan_temp_bytes(n) > OFF_TOTAL - OFF_SCAN || sort_temp_bytes(out->capacity) > NOALLOC_SCRATCH_BYTES - OFF_SORT)
+    if (scan_temp_bytes(n) > OFF_TOTAL - OFF_SCAN ||
+        sort_temp_bytes((uint64_t)n > out->capacity ? (uint64_t)n : out->capacity) > NOALLOC_SCRATCH_BYTES - OFF_SORT)
         return GS_ERR_INVALID_ARG;
     // view batch (host-side validation of the cameras as in gs_bin)
     ViewBatch vb;
@@ -107,11 +113,17 @@ extern "C" gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, 
     if (r != GS_OK) return r;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     auto *offsets = reinterpret_cast<uint32_t *>(s + OFF_OFFSETS);
-    auto *ntiles = reinterpret_cast<uint32_t *>(s + OFF_NTILES);
+    auto *rect = reinterpret_cast<uint2 *>(s + OFF_RECT);
     auto *total = reinterpret_cast<unsigned long long *>(s + OFF_TOTAL);
+    auto *pair_count = reinterpret_cast<uint32_t *>(s + OFF_TOTAL + 8);
     auto *status = reinterpret_cast<DevStatus *>(s + OFF_STATUS);
-    auto *keys_alt = reinterpret_cast<uint64_t *>(s + OFF_KEYS);
+    auto *tk = reinterpret_cast<uint32_t *>(s + OFF_TK);
+    auto *tk_alt = reinterpret_cast<uint32_t *>(s + OFF_TK_ALT);
     auto *vals_alt = reinterpret_cast<uint32_t *>(s + OFF_VALS);
+    auto *pk = reinterpret_cast<uint32_t *>(s + OFF_PK);
+    auto *pv_order = reinterpret_cast<uint32_t *>(s + OFF_PV);
+    auto *pk_alt = reinterpret_cast<uint32_t *>(s + OFF_PK_ALT);
+    auto *pv_alt = reinterpret_cast<uint32_t *>(s + OFF_PV_ALT);
     void *sort_tmp = s + OFF_SORT;
     // The array keeps the previous call's contents: the status word must start at zero.
     cudaMemsetAsync(status, 0, sizeof(DevStatus), st);
@@ -119,17 +131,17 @@ extern "C" gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, 
     const ProjView pv{reinterpret_cast<float2 *>(proj->xy), reinterpret_cast<float4 *>(proj->conic_o),
                       reinterpret_cast<float4 *>(proj->rgb_d), proj->radius, proj->N};
     const int high = bits_for(vb.total_tiles);
-    const int passes = 4 + (high + 7) / 8;
-    uint64_t *k_emit = (passes % 2 == 0) ? out->keys : keys_alt;
-    uint32_t *v_emit = (passes % 2 == 0) ? out->vals : vals_alt;
-    uint64_t *k_other = (passes % 2 == 0) ? keys_alt : out->keys;
-    uint32_t *v_other = (passes % 2 == 0) ? vals_alt : out->vals;
-    launch_count_tiles(vb, pv, ntiles, st);
-    launch_exclusive_scan(ntiles, offsets, n, total, s + OFF_SCAN, st);
-    launch_emit_keys(vb, pv, ntiles, offsets, k_emit, v_emit, out->capacity, total, status, out->count, st);
-    launch_radix_sort(k_emit, v_emit, k_other, v_other, out->capacity, out->count, high, sort_tmp, status, st);
-    launch_tile_ranges(out->keys, out->count, out->capacity, reinterpret_cast<uint2 *>(out->ranges), vb.total_tiles,
-                       st);
+    const bool even = fragment_sort_passes(high) % 2 == 0;
+    launch_pair_keys(vb, pv, pk, pv_order, rect, pair_count, st);
+    launch_sort_pairs(pk, pv_order, pk_alt, pv_alt, (uint64_t)n, pair_count, sort_tmp, status, st);
+    launch_gather_counts(pv_order, rect, n, pv_alt, pk, pk_alt, st);   // depth keys dead: rectangles there
+    launch_exclusive_scan(pv_alt, offsets, n, total, s + OFF_SCAN, st);
+    launch_emit_keys(vb, pv.N, pv_order, pk, pk_alt, offsets, even ? tk : tk_alt, even ? out->vals : vals_alt,
+                     out->capacity, total, status, out->count, st);
+    launch_sort_fragments(even ? tk : tk_alt, even ? out->vals : vals_alt, even ? tk_alt : tk,
+                          even ? vals_alt : out->vals, out->capacity, out->count, high, sort_tmp, status, st);
+    launch_tile_ranges(tk, out->count, out->capacity, reinterpret_cast<uint2 *>(out->ranges), vb.total_tiles, st);
+    launch_compose_keys(vb, pv.N, tk, out->vals, out->count, out->capacity, pv.rgb_d, out->keys, st);
     if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
     if (needed_host) {
         unsigned long long F = 0;

@@ -35,6 +35,8 @@ struct gs_ctx {
     char err[512];
     // binning scratch
     DBuf ntiles, offsets, scan_tmp, total, keys_alt, vals_alt, sort_tmp;
+    DBuf pk, pv, pk_alt, pv_alt;   // (view, Gaussian) pairs sorted by depth
+    DBuf rect;                     // their tile rectangles
     // iteration scratch (gs_train_step / gs_render)
     DBuf xy, conic_o, rgb_d, radius, g_xy, g_co, g_rgb, keys, vals, ranges, count;
     DBuf img, dimg, T_final, n_contrib, maps, acc;
@@ -200,41 +202,51 @@ void trace_free(gs_ctx *c)
     c->trace_on = false;
 }
 
-// Count, scan, emit, sort and range the fragments of `p` into (keys, vals,
-// ranges, count).  `ntiles` may already hold the per-(view, Gaussian) tile
-// counts (the transformation kernel writes them); otherwise pass nullptr.
-gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, const uint32_t *ntiles_in, uint64_t *keys,
-                      uint32_t *vals, uint2 *ranges, uint32_t *count, uint64_t capacity, cudaStream_t st)
+// Bins the fragments of `p` into (vals, ranges, count) in depth order; the
+// fragments' tile ids stay in c->keys.  With keys64 non-null it also writes
+// the public 64-bit keys (tile id << 32 | depth bits).
+gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, uint64_t *keys64, uint32_t *vals,
+                      uint2 *ranges, uint32_t *count, uint64_t capacity, cudaStream_t st)
 {
     const int64_t n = (int64_t)vb.B * p.N;
+    if ((uint64_t)n > GS_MAX_FRAGMENTS) return fail(c, GS_ERR_INVALID_ARG, "B*N above 2^30-1 (view, Gaussian) pairs");
+    const size_t n1 = (size_t)(n > 0 ? n : 1);
+    const uint64_t cap1 = capacity ? capacity : 1;
+    const uint64_t sort_cap = (uint64_t)n > capacity ? (uint64_t)n : capacity;
     gs_status r;
-    if ((r = ensure(c, c->offsets, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1))) != GS_OK) return r;
-    if ((r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) != GS_OK) return r;
-    if ((r = ensure(c, c->total, 64)) != GS_OK) return r;
-    const uint32_t *ntiles = ntiles_in;
-    if (!ntiles) {
-        if ((r = ensure(c, c->ntiles, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1))) != GS_OK) return r;
-        launch_count_tiles(vb, p, ptr<uint32_t>(c->ntiles), st);
-        ntiles = ptr<uint32_t>(c->ntiles);
-    }
+    if ((r = ensure(c, c->offsets, 4 * n1)) || (r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) ||
+        (r = ensure(c, c->total, 64)) || (r = ensure(c, c->pk, 4 * n1)) || (r = ensure(c, c->pv, 4 * n1)) ||
+        (r = ensure(c, c->pk_alt, 4 * n1)) || (r = ensure(c, c->pv_alt, 4 * n1)) || (r = ensure(c, c->rect, 8 * n1)) ||
+        (r = ensure(c, c->keys, 4 * (size_t)cap1)) || (r = ensure(c, c->keys_alt, 4 * (size_t)cap1)) ||
+        (r = ensure(c, c->vals_alt, 4 * (size_t)cap1)) || (r = ensure(c, c->sort_tmp, sort_temp_bytes(sort_cap))))
+        return r;
     const int high = bits_for(vb.total_tiles);
-    const int passes = 4 + (high + 7) / 8;
-    if ((r = ensure(c, c->keys_alt, sizeof(uint64_t) * (size_t)(capacity ? capacity : 1))) != GS_OK) return r;
-    if ((r = ensure(c, c->vals_alt, sizeof(uint32_t) * (size_t)(capacity ? capacity : 1))) != GS_OK) return r;
-    if ((r = ensure(c, c->sort_tmp, sort_temp_bytes(capacity))) != GS_OK) return r;
-    uint64_t *k_emit = (passes % 2 == 0) ? keys : ptr<uint64_t>(c->keys_alt);
-    uint32_t *v_emit = (passes % 2 == 0) ? vals : ptr<uint32_t>(c->vals_alt);
-    uint64_t *k_other = (passes % 2 == 0) ? ptr<uint64_t>(c->keys_alt) : keys;
-    uint32_t *v_other = (passes % 2 == 0) ? ptr<uint32_t>(c->vals_alt) : vals;
+    const bool even = fragment_sort_passes(high) % 2 == 0;
     auto *total = ptr<unsigned long long>(c->total);
-    launch_exclusive_scan(ntiles, ptr<uint32_t>(c->offsets), n, total, c->scan_tmp.p, st);
+    uint32_t *pair_count = reinterpret_cast<uint32_t *>(ptr<char>(c->total) + 8);
+    uint32_t *pk = ptr<uint32_t>(c->pk), *pv = ptr<uint32_t>(c->pv);
+    uint2 *rect = ptr<uint2>(c->rect);
+    uint32_t *tk = ptr<uint32_t>(c->keys), *tk_alt = ptr<uint32_t>(c->keys_alt), *v_alt = ptr<uint32_t>(c->vals_alt);
+    // (1) the (view, Gaussian) pairs in depth order (4 passes: the result returns to pk / pv)
+    launch_pair_keys(vb, p, pk, pv, rect, pair_count, st);
+    launch_sort_pairs(pk, pv, ptr<uint32_t>(c->pk_alt), ptr<uint32_t>(c->pv_alt), (uint64_t)n, pair_count,
+                      c->sort_tmp.p, c->status, st);
+    // (2) their rectangles and tile counts in that order (the depth keys are
+    // dead: their buffers take the rectangles), counts scanned into offsets
+    uint32_t *rx = pk, *ry = ptr<uint32_t>(c->pk_alt), *counts = ptr<uint32_t>(c->pv_alt);
+    launch_gather_counts(pv, rect, n, counts, rx, ry, st);
+    launch_exclusive_scan(counts, ptr<uint32_t>(c->offsets), n, total, c->scan_tmp.p, st);
     mark(c, st, 2);
-    launch_emit_keys(vb, p, ntiles, ptr<uint32_t>(c->offsets), k_emit, v_emit, capacity, total, c->status, count,
-                     st);
+    // (3) fragments pair by pair in depth order, into the buffers the tile sort ends in
+    launch_emit_keys(vb, p.N, pv, rx, ry, ptr<uint32_t>(c->offsets), even ? tk : tk_alt, even ? vals : v_alt,
+                     capacity, total, c->status, count, st);
     mark(c, st, 3);
-    launch_radix_sort(k_emit, v_emit, k_other, v_other, capacity, count, high, c->sort_tmp.p, c->status, st);
+    // (4) stable sort on the tile id
+    launch_sort_fragments(even ? tk : tk_alt, even ? vals : v_alt, even ? tk_alt : tk, even ? v_alt : vals, capacity,
+                          count, high, c->sort_tmp.p, c->status, st);
     mark(c, st, 4);
-    launch_tile_ranges(keys, count, capacity, ranges, vb.total_tiles, st);
+    launch_tile_ranges(tk, count, capacity, ranges, vb.total_tiles, st);
+    if (keys64) launch_compose_keys(vb, p.N, tk, vals, count, capacity, p.rgb_d, keys64, st);
     mark(c, st, 5);
     return cuda_check(c, "binning");
 }
@@ -247,9 +259,14 @@ gs_status ensure_iter(gs_ctx *c, int64_t N, const ViewBatch &vb, uint64_t cap)
     for (int v = 0; v < vb.B; ++v) pix += (size_t)vb.v[v].W * vb.v[v].H;
     gs_status r;
     if ((r = ensure(c, c->xy, 8 * n)) || (r = ensure(c, c->conic_o, 16 * n)) || (r = ensure(c, c->rgb_d, 16 * n)) ||
-        (r = ensure(c, c->radius, 4 * n)) || (r = ensure(c, c->ntiles, 4 * n)) || (r = ensure(c, c->offsets, 4 * n)))
+        (r = ensure(c, c->radius, 4 * n)) || (r = ensure(c, c->ntiles, 4 * n)) || (r = ensure(c, c->offsets, 4 * n)) ||
+        (r = ensure(c, c->pk, 4 * n)) || (r = ensure(c, c->pv, 4 * n)) || (r = ensure(c, c->pk_alt, 4 * n)) ||
+        (r = ensure(c, c->pv_alt, 4 * n)) || (r = ensure(c, c->rect, 8 * n)) ||
+        (r = ensure(c, c->scan_tmp, scan_temp_bytes((int64_t)n))) || (r = ensure(c, c->total, 64)) ||
+        (r = ensure(c, c->keys_alt, 4 * (size_t)(cap ? cap : 1))) || (r = ensure(c, c->vals_alt, 4 * (size_t)(cap ? cap : 1))) ||
+        (r = ensure(c, c->sort_tmp, sort_temp_bytes((uint64_t)n > cap ? (uint64_t)n : cap))))
         return r;
-    if ((r = ensure(c, c->keys, 8 * (size_t)(cap ? cap : 1))) || (r = ensure(c, c->vals, 4 * (size_t)(cap ? cap : 1))) ||
+    if ((r = ensure(c, c->keys, 4 * (size_t)(cap ? cap : 1))) || (r = ensure(c, c->vals, 4 * (size_t)(cap ? cap : 1))) ||
         (r = ensure(c, c->ranges, 8 * (size_t)vb.total_tiles)) || (r = ensure(c, c->count, 64)))
         return r;
     if ((r = ensure(c, c->T_final, 4 * pix)) || (r = ensure(c, c->n_contrib, 4 * pix))) return r;
@@ -411,6 +428,7 @@ gs_status gs_destroy(gs_ctx *c)
 {
     if (!c) return GS_ERR_INVALID_ARG;
     DBuf *bufs[] = {&c->ntiles, &c->offsets, &c->scan_tmp, &c->total, &c->keys_alt, &c->vals_alt, &c->sort_tmp,
+                    &c->pk, &c->pv, &c->pk_alt, &c->pv_alt, &c->rect,
                     &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_xy, &c->g_co, &c->g_rgb, &c->keys,
                     &c->vals, &c->ranges, &c->count, &c->img, &c->dimg, &c->T_final, &c->n_contrib, &c->maps,
                     &c->acc};
@@ -474,13 +492,7 @@ gs_status gs_reserve(gs_ctx *c, int64_t N, const gs_camera *cams, int32_t B, uin
     if (r != GS_OK) return r;
     if (frag_capacity > GS_MAX_FRAGMENTS) return fail(c, GS_ERR_INVALID_ARG, "fragment capacity above 2^30-1");
     if (frag_capacity > c->frag_cap) c->frag_cap = frag_capacity;
-    const int64_t n = (int64_t)B * (N > 0 ? N : 1);
     if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
-    if ((r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) || (r = ensure(c, c->total, 64)) ||
-        (r = ensure(c, c->keys_alt, 8 * (size_t)(c->frag_cap ? c->frag_cap : 1))) ||
-        (r = ensure(c, c->vals_alt, 4 * (size_t)(c->frag_cap ? c->frag_cap : 1))) ||
-        (r = ensure(c, c->sort_tmp, sort_temp_bytes(c->frag_cap))))
-        return r;
     bool uniform = true;
     for (int v = 1; v < B; ++v) uniform = uniform && cams[v].W == cams[0].W && cams[v].H == cams[0].H;
     if (uniform && (r = ensure_train(c, N, vb)) != GS_OK) return r;
@@ -501,7 +513,8 @@ gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *ca
         pix += (size_t)cams[v].W * cams[v].H;
     }
     const size_t n = (size_t)B * (size_t)N;
-    size_t s = n * (8 + 16 + 16 + 4 + 4 + 4 + 48) + frag_capacity * (12 * 2) + sort_temp_bytes(frag_capacity) +
+    size_t s = n * (8 + 16 + 16 + 4 + 4 + 4 + 16 + 8 + 48) + frag_capacity * (8 * 2) +
+               sort_temp_bytes((uint64_t)n > frag_capacity ? (uint64_t)n : frag_capacity) +
                scan_temp_bytes((int64_t)n) + tiles * 8 + pix * (4 + 4 + 12 + 12 + 36) + 4096;
     *bytes = s;
     return GS_OK;
@@ -537,7 +550,7 @@ gs_status gs_bin(gs_ctx *c, const gs_proj *proj, const gs_camera *cams, int32_t 
     gs_status r = make_views(c, cams, B, vb, false);
     if (r != GS_OK) return r;
     cudaStream_t st = S(stream);
-    r = run_binning(c, vb, proj_of(proj), nullptr, out->keys, out->vals, reinterpret_cast<uint2 *>(out->ranges),
+    r = run_binning(c, vb, proj_of(proj), out->keys, out->vals, reinterpret_cast<uint2 *>(out->ranges),
                     out->count, out->capacity, st);
     if (r != GS_OK) return r;
     if (needed_host) {
@@ -669,7 +682,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
         c->frag_cap = cap;
         if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
     }
-    r = run_binning(c, vb, pv, ptr<uint32_t>(c->ntiles), ptr<uint64_t>(c->keys), ptr<uint32_t>(c->vals),
+    r = run_binning(c, vb, pv, nullptr, ptr<uint32_t>(c->vals),
                     ptr<uint2>(c->ranges), ptr<uint32_t>(c->count), c->frag_cap, st);
     if (r != GS_OK) return r;
     set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
@@ -728,7 +741,7 @@ gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int
         c->frag_cap = cap;
         if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
     }
-    r = run_binning(c, vb, pv, ptr<uint32_t>(c->ntiles), ptr<uint64_t>(c->keys), ptr<uint32_t>(c->vals),
+    r = run_binning(c, vb, pv, nullptr, ptr<uint32_t>(c->vals),
                     ptr<uint2>(c->ranges), ptr<uint32_t>(c->count), c->frag_cap, st);
     if (r != GS_OK) return r;
     size_t off = 0;

@@ -88,20 +88,38 @@ size_t scan_temp_bytes(int64_t n);
 void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *total, void *temp,
                            cudaStream_t st);
 
-void launch_count_tiles(const ViewBatch &vb, const ProjView &p, uint32_t *ntiles, cudaStream_t st);
-void launch_emit_keys(const ViewBatch &vb, const ProjView &p, const uint32_t *ntiles, const uint32_t *offsets,
-                      uint64_t *keys, uint32_t *vals, uint64_t capacity, const unsigned long long *total,
-                      DevStatus *status, uint32_t *count_out, cudaStream_t st);
+// Binning in depth order: (1) per (view, Gaussian) pair its tile rectangle
+// and a depth key (float bits of the depth; pairs on no tile last), sorted
+// stably (4 passes of 8-bit digits); (2) tile counts gathered in that order
+// and scanned; (3) fragments emitted pair by pair in that order, key = global
+// tile id, value = Gaussian index; (4) a stable sort on the tile id.  Within a
+// tile the fragments then follow (depth, Gaussian index).
+void launch_pair_keys(const ViewBatch &vb, const ProjView &p, uint32_t *keys, uint32_t *vals, uint2 *rect,
+                      uint32_t *count, cudaStream_t st);
+// counts / rx / ry: tile count and the two rectangle words of pair order[j]
+void launch_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n, uint32_t *counts, uint32_t *rx,
+                          uint32_t *ry, cudaStream_t st);
+void launch_emit_keys(const ViewBatch &vb, int64_t N, const uint32_t *order, const uint32_t *rx, const uint32_t *ry,
+                      const uint32_t *offsets, uint32_t *keys, uint32_t *vals, uint64_t capacity,
+                      const unsigned long long *total, DevStatus *status, uint32_t *count_out, cudaStream_t st);
 
 size_t sort_temp_bytes(uint64_t capacity);
-// Sorts keys/vals (count on device, <= capacity) on bits [0, 32 + high_bits).
-// Result lands in keys/vals; alt buffers are scratch of the same capacity.
-// A look-back wait that exceeds its spin limit sets GS_ERR_TIMEOUT in *status.
-void launch_radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
-                       const uint32_t *count, int high_bits, void *temp, DevStatus *status, cudaStream_t st);
+// Stable LSD radix sorts of 32-bit keys (one-sweep passes).  The result lands
+// in keys/vals when the number of passes is even, else in the alt buffers.  A
+// look-back wait that exceeds its spin limit sets GS_ERR_TIMEOUT in *status.
+void launch_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
+                       const uint32_t *count, void *temp, DevStatus *status, cudaStream_t st);
+int fragment_sort_passes(int tile_bits);
+void launch_sort_fragments(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                           uint64_t capacity, const uint32_t *count, int tile_bits, void *temp, DevStatus *status,
+                           cudaStream_t st);
 
-void launch_tile_ranges(const uint64_t *keys, const uint32_t *count, uint64_t capacity, uint2 *ranges,
+void launch_tile_ranges(const uint32_t *keys, const uint32_t *count, uint64_t capacity, uint2 *ranges,
                         uint32_t total_tiles, cudaStream_t st);
+// keys[i] = tiles[i] << 32 | depth bits of fragment i (the public key format).
+void launch_compose_keys(const ViewBatch &vb, int64_t N, const uint32_t *tiles, const uint32_t *vals,
+                         const uint32_t *count, uint64_t capacity, const float4 *rgb_d, uint64_t *keys,
+                         cudaStream_t st);
 
 // chunk: list entries a warp gathers and filters per shared-memory refill
 // (blend_config_ok says which (tile, chunk) pairs are built).

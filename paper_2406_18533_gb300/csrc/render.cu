@@ -2,13 +2,15 @@
 //
 // One CTA per screen tile of TILE x TILE pixels, one pixel per thread; warp w
 // owns an 8 x 4 block of the tile.  Warps work independently (no block-wide
-// barrier inside the walk): a warp refills its own chunk of CH entries of the
-// tile's depth-sorted list (lane i gathers entry i with coalesced 8/16-byte
-// loads; the warps of a tile hit the same L1 lines), keeps only the Gaussians
-// whose alpha >= alpha_min ellipse meets the warp's block (ballot + prefix
-// compaction into the warp's slice of shared memory, order preserved), and
-// walks those.  So a warp spends nothing on list entries that cannot reach its
-// pixels, and finishes as soon as its own pixels do.  The staged record holds
+// barrier inside the walk): a warp reads the tile's depth-sorted list in
+// rounds of 32 entries (lane i gathers entry i with coalesced 8/16-byte loads;
+// the warps of a tile hit the same L1 lines; the next round's gathers are
+// issued before the current round is used), keeps only the Gaussians whose
+// alpha >= alpha_min ellipse meets the warp's block (ballot + prefix
+// compaction into the warp's buffer of CH entries in shared memory, order
+// preserved), and walks the buffer when another round could overflow it.  So
+// a warp spends nothing on list entries that cannot reach its pixels, and
+// finishes as soon as its own pixels do.  The staged record holds
 // the exponent below which alpha < alpha_min, so most (pixel, Gaussian) pairs
 // are rejected before the exponential.
 // Forward: a lane stops once its pixel saturates; the warp stops refilling
@@ -136,6 +138,30 @@ __device__ __forceinline__ PixelSite pixel_site(const ViewCam &c, uint32_t local
     return s;
 }
 
+// One list entry as gathered by a lane during a refill.
+struct Entry {
+    bool ok;
+    uint32_t g;
+    float2 xy;
+    float4 co;
+};
+
+__device__ __forceinline__ Entry fetch_entry(const ProjView &p, const uint32_t *vals, int64_t vbase, int64_t j,
+                                             bool valid)
+{
+    Entry e;
+    e.g = valid ? vals[j] : 0u;
+    e.ok = valid && (int64_t)e.g < p.N;           // an index >= N only after a failed (timed-out) sort
+    e.xy = make_float2(0.f, 0.f);
+    e.co = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e.ok) {
+        const int64_t idx = vbase + e.g;
+        e.xy = p.xy[idx];
+        e.co = p.conic_o[idx];
+    }
+    return e;
+}
+
 // Bytes of dynamic shared memory per CTA.
 template <int TILE, int CH, bool BWD>
 constexpr size_t smem_bytes()
@@ -167,60 +193,58 @@ __global__ void __launch_bounds__(TILE *TILE) k_blend_fwd(ViewBatch vb, ProjView
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t nc = 0, ne = 0;
     bool done = !ps.inside;
-    for (uint32_t base = rg.x; base < rg.y; base += CH) {
-        if (__all_sync(0xffffffffu, done)) break;
-        // refill: gather CH entries, keep those that can reach this warp's block
-        int n = 0;
-#pragma unroll
-        for (int r = 0; r < CH; r += 32) {
-            const uint32_t j = base + r + lane;
-            bool hit = false;
-            int64_t idx = 0;
-            float2 xy = make_float2(0.f, 0.f);
-            float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (j < rg.y) {
-                idx = vbase + vals[j];
-                xy = p.xy[idx];
-                co = p.conic_o[idx];
-                hit = alpha_box_hits(co, xy.x, xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
-            }
-            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const int slot = n + __popc(bal & lt);
-                const float4 q = stage_q(co);
-                s_xyc[slot] = make_float4(xy.x, xy.y, exponent_cut(q.w, bp.alpha_min), 0.f);
-                s_q[slot] = q;
-                s_rgb[slot] = p.rgb_d[idx];
-                s_pos[slot] = j - rg.x;
-            }
-            n += __popc(bal);
+    // Rounds of 32 entries, software-pipelined: the gathers of the next round
+    // are in flight while the current one is tested and staged.  Hits pile up
+    // in the warp's buffer, which is walked when another round could overflow
+    // it, or at the end of the list.
+    int n = 0;
+    Entry nxt = fetch_entry(p, vals, vbase, (int64_t)rg.x + lane, rg.x + lane < rg.y);
+    for (uint32_t base = rg.x; base < rg.y; base += 32) {
+        const Entry e = nxt;
+        const uint32_t j = base + lane;
+        if (base + 32 < rg.y) nxt = fetch_entry(p, vals, vbase, (int64_t)j + 32, j + 32 < rg.y);
+        const bool hit = e.ok && alpha_box_hits(e.co, e.xy.x, e.xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
+        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int slot = n + __popc(bal & lt);
+            const float4 q = stage_q(e.co);
+            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_cut(q.w, bp.alpha_min), 0.f);
+            s_q[slot] = q;
+            s_rgb[slot] = p.rgb_d[vbase + e.g];
+            s_pos[slot] = j - rg.x;
         }
-        __syncwarp();
-        if (!done) {
-            for (int i = 0; i < n; ++i) {
-                const float4 xyc = s_xyc[i];
-                const float4 q = s_q[i];
-                const float pw = power2(q, __fsub_rn(ps.fx, xyc.x), __fsub_rn(ps.fy, xyc.y));
-                if (!(pw >= xyc.z && pw <= 0.f)) continue;      // below the alpha cut, or power > 0
-                const float alpha = fminf(bp.alpha_max, q.w * ex2(pw));
-                if (alpha < bp.alpha_min) continue;
-                const float Tn = T * (1.f - alpha);
-                if (Tn < bp.T_min) {
-                    done = true;
-                    ne = s_pos[i] + 1;
-                    break;
+        n += __popc(bal);
+        const bool last = base + 32 >= rg.y;
+        if (n > CH - 32 || last) {
+            __syncwarp();
+            if (!done) {
+                for (int i = 0; i < n; ++i) {
+                    const float4 xyc = s_xyc[i];
+                    const float4 q = s_q[i];
+                    const float pw = power2(q, __fsub_rn(ps.fx, xyc.x), __fsub_rn(ps.fy, xyc.y));
+                    if (!(pw >= xyc.z && pw <= 0.f)) continue;      // below the alpha cut, or power > 0
+                    const float alpha = fminf(bp.alpha_max, q.w * ex2(pw));
+                    if (alpha < bp.alpha_min) continue;
+                    const float Tn = T * (1.f - alpha);
+                    if (Tn < bp.T_min) {
+                        done = true;
+                        ne = s_pos[i] + 1;
+                        break;
+                    }
+                    const float4 rgb = s_rgb[i];
+                    const float w = alpha * T;
+                    C0 += rgb.x * w;
+                    C1 += rgb.y * w;
+                    C2 += rgb.z * w;
+                    T = Tn;
+                    nc = s_pos[i] + 1;
                 }
-                const float4 rgb = s_rgb[i];
-                const float w = alpha * T;
-                C0 += rgb.x * w;
-                C1 += rgb.y * w;
-                C2 += rgb.z * w;
-                T = Tn;
-                nc = s_pos[i] + 1;
+                if (!done) ne = min(base + 32, rg.y) - rg.x;
             }
-            if (!done) ne = min(base + CH, rg.y) - rg.x;
+            n = 0;
+            __syncwarp();
+            if (__all_sync(0xffffffffu, done)) break;
         }
-        __syncwarp();
     }
     if (ps.inside) {
         const int64_t hw = (int64_t)c.W * c.H;
@@ -286,36 +310,30 @@ __global__ void __launch_bounds__(TILE *TILE) k_blend_bwd(ViewBatch vb, ProjView
 
     float B0 = bp.bg[0], B1 = bp.bg[1], B2 = bp.bg[2];   // colour behind (normalised)
     uint32_t evals = 0, walked = 0;
-    for (int64_t end = (int64_t)rg.x + wnc; end > (int64_t)rg.x; end -= CH) {
-        const int64_t start = max((int64_t)rg.x, end - CH);
-        int n = 0;
-#pragma unroll
-        for (int r = 0; r < CH; r += 32) {
-            const int64_t j = end - 1 - r - lane;             // descending list positions
-            bool hit = false;
-            uint32_t g = 0;
-            float2 xy = make_float2(0.f, 0.f);
-            float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (j >= start) {
-                g = vals[j];
-                const int64_t idx = vbase + g;
-                xy = p.xy[idx];
-                co = p.conic_o[idx];
-                hit = alpha_box_hits(co, xy.x, xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
-            }
-            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const int slot = n + __popc(bal & lt);
-                const float4 q = stage_q(co);
-                const float4 rgbd = p.rgb_d[vbase + g];
-                s_xyc[slot] = make_float4(xy.x, xy.y, exponent_cut(q.w, bp.alpha_min), 0.f);
-                s_q[slot] = q;
-                s_cn[slot] = co;
-                s_rgb[slot] = make_float4(rgbd.x, rgbd.y, rgbd.z, __uint_as_float(g));
-                s_pos[slot] = (uint32_t)(j - rg.x);
-            }
-            n += __popc(bal);
+    // Rounds of 32 entries from the walk's top down, software-pipelined like
+    // the forward; hits are staged in descending list order and walked when
+    // another round could overflow the warp's buffer, or at the bottom.
+    const int64_t top = (int64_t)rg.x + wnc;
+    int n = 0;
+    Entry nxt = fetch_entry(p, vals, vbase, top - 1 - lane, top - 1 - lane >= (int64_t)rg.x);
+    for (int64_t hi = top; hi > (int64_t)rg.x; hi -= 32) {
+        const Entry e = nxt;
+        const int64_t j = hi - 1 - lane;
+        if (hi - 32 > (int64_t)rg.x) nxt = fetch_entry(p, vals, vbase, j - 32, j - 32 >= (int64_t)rg.x);
+        const bool hit = e.ok && alpha_box_hits(e.co, e.xy.x, e.xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
+        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int slot = n + __popc(bal & lt);
+            const float4 q = stage_q(e.co);
+            const float4 rgbd = p.rgb_d[vbase + e.g];
+            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_cut(q.w, bp.alpha_min), 0.f);
+            s_q[slot] = q;
+            s_cn[slot] = e.co;
+            s_rgb[slot] = make_float4(rgbd.x, rgbd.y, rgbd.z, __uint_as_float(e.g));
+            s_pos[slot] = (uint32_t)(j - rg.x);
         }
+        n += __popc(bal);
+        if (n <= CH - 32 && hi - 32 > (int64_t)rg.x) continue;
         __syncwarp();
         for (int i = 0; i < n; ++i) {
             const uint32_t rel = s_pos[i];
@@ -381,6 +399,7 @@ __global__ void __launch_bounds__(TILE *TILE) k_blend_bwd(ViewBatch vb, ProjView
             if ((lane & 3) == 0) atomicAdd(dst, y);
             else if (lane == 1) atomicAdd(reinterpret_cast<float *>(&gv.d_rgb[idx]) + 2, gbl);
         }
+        n = 0;
         __syncwarp();
     }
     // blended (pixel, Gaussian) pairs and walked (pixel, position) pairs
