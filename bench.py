@@ -239,10 +239,17 @@ def run_ours(args, rank, world, local_rank):
     lr6 = lr_groups(extent)
     Bv = len(cams)
     H, W = cams[0].H, cams[0].W
-    ctx = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch)
     P = engine.DeviceScene.from_host(sc)
-    G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
     targets = torch.from_numpy(tg).cuda()
+    tuned = None
+    if args.autotune:
+        from paper_2406_18533_gb300 import autotune
+        best, trials = autotune.tune(P, cams, targets, lr=lr6, log=lambda m: print(m, file=sys.stderr, flush=True))
+        args.tile, args.batch, args.ppt = best["tile"], best["smem_batch"], best["px_per_thread"]
+        tuned = {"chosen": best, "trials_ms": {f"t{t.tile}_b{t.smem_batch}_p{t.px_per_thread}": round(t.ms, 3)
+                                               for t in trials}}
+    ctx = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt)
+    G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
     loss = torch.empty(Bv, dtype=torch.float32, device="cuda")
     cam_arr = binding.camera_array(cams)
 
@@ -327,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
     # per-view: the same scene stepped one view at a time over the same views
     per_view = None
     if Bv > 1 and not args.no_per_view:
-        ctx1 = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch)
+        ctx1 = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt)
         P1 = P.clone()
         G1, M1, V1 = P1.zeros_like(), P1.zeros_like(), P1.zeros_like()
         loss1 = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -428,7 +435,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": name, "gaussians": sc.N, "views_per_step": Bv, "resolution": f"{W}x{H}",
-                   "tile": args.tile, "smem_batch": args.batch, "sh_degree": 3,
+                   "tile": args.tile, "smem_batch": args.batch, "px_per_thread": args.ppt, "autotune": tuned,
+                   "sh_degree": 3,
                    "l2": "no flush: params + grad + Adam moments resident in HBM exceed the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "mpix_per_s": value * H * W / 1e6, "cuda_graph": bool(args.graph),
@@ -488,7 +496,8 @@ def run_serving(args, rank, world, local_rank):
     sc, rng = synth.large_scene(10_000_000, seed=0)
     scene = engine.DeviceScene.from_host(sc)
     reqs = [serve.Request(i, t, cam) for i, (t, cam) in enumerate(synth.serve_requests(rng, args.requests))]
-    server = serve.RenderServer(scene, n_slots=3, max_batch=8, tile=args.tile, smem_batch=args.batch)
+    server = serve.RenderServer(scene, n_slots=3, max_batch=8, tile=args.tile, smem_batch=args.batch,
+                                px_per_thread=args.ppt)
     # one untimed pass over a few requests sizes the fragment buffers
     server.run([serve.Request(-1 - i, 0.0, r.cam) for i, r in enumerate(reqs[:16])])
     server.retries = 0
@@ -524,14 +533,24 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3", "c4"])
     ap.add_argument("--requests", type=int, default=2200, help="c4: requests replayed (the first 200 warm up)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--tile", type=int, default=None, help="fix the tile edge (8, 16, 32) instead of autotuning")
+    ap.add_argument("--batch", type=int, default=None, help="fix the entries per warp refill (32, 64, 128)")
+    ap.add_argument("--ppt", type=int, default=None, help="fix the pixels per blending thread (1, 2 or 4)")
+    ap.add_argument("--no-autotune", action="store_true", help="use tile 16, 64 entries, 1 pixel per thread "
+                    "unless set above")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="call gs_train_step directly instead of replaying one captured step (CUDA graph)")
     ap.add_argument("--views", type=int, default=0, help="use only the first K views of the workload (profiling)")
     args = ap.parse_args()
+    # the batched training workloads pick their blending shape with the autotuner
+    # unless a shape is given; the single-view and serving workloads use the defaults
+    fixed = args.tile is not None or args.batch is not None or args.ppt is not None
+    args.autotune = not (fixed or args.no_autotune) and args.workload in ("c2", "c3") and args.impl == "ours"
+    args.tile = 16 if args.tile is None else args.tile
+    args.batch = 64 if args.batch is None else args.batch
+    args.ppt = 1 if args.ppt is None else args.ppt
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -86,7 +86,7 @@ typedef struct gs_scene {
 typedef struct gs_hparams {
     int32_t tile;             /* screen tile edge: 8, 16 (paper's 16x16 blocks) or 32 */
     int32_t smem_batch;       /* list entries a warp stages per shared-memory refill: 32, 64
-                                 or 128 (tile 32: 32 or 64) */
+                                 or 128 (tile 32 with one pixel per thread: 32 or 64) */
     int32_t strict_nonfinite; /* 1: report GS_ERR_NONFINITE; 0: cull silently */
     float alpha_min;          /* skip a Gaussian at a pixel below this alpha (1/255) */
     float alpha_max;          /* alpha is clamped to this (0.99) */
@@ -97,7 +97,9 @@ typedef struct gs_hparams {
     int32_t scale_lr_sqrt_b;  /* Eq. 1: lr' = lr * sqrt(B) */
     int32_t scale_beta_pow_b; /* Eq. 2: beta' = beta^B */
     float lambda_dssim;       /* loss = (1-l) L1 + l (1 - SSIM), l = 0.2 */
-    int32_t reserved[2];
+    int32_t px_per_thread;    /* pixels a blending thread owns: 1 (a warp blends an 8x4 block),
+                                 2 (8x8) or 4 (8x16); 2 and 4 need tile 16 or 32 */
+    int32_t reserved;
 } gs_hparams;
 
 /*

@@ -32,7 +32,7 @@ class gs_hparams(ctypes.Structure):
                 ("bg", ctypes.c_float * 3), ("lr", ctypes.c_float * 6), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("scale_lr_sqrt_b", ctypes.c_int32),
                 ("scale_beta_pow_b", ctypes.c_int32), ("lambda_dssim", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("px_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gs_proj(ctypes.Structure):

@@ -38,7 +38,7 @@ struct gs_ctx {
     DBuf pk, pv, pk_alt, pv_alt;   // (view, Gaussian) pairs sorted by depth
     DBuf rect;                     // their tile rectangles
     // iteration scratch (gs_train_step / gs_render)
-    DBuf xy, conic_o, rgb_d, radius, g_xy, g_co, g_rgb, keys, vals, ranges, count;
+    DBuf xy, conic_o, rgb_d, radius, g_proj, keys, vals, ranges, count;
     DBuf img, dimg, T_final, n_contrib, maps, acc;
     uint64_t frag_cap = 0;
     // tracing: events around the stages of gs_train_step
@@ -278,8 +278,7 @@ gs_status ensure_train(gs_ctx *c, int64_t N, const ViewBatch &vb)
     const size_t n = (size_t)vb.B * (size_t)(N > 0 ? N : 1);
     const size_t pix = (size_t)vb.B * vb.v[0].W * vb.v[0].H;
     gs_status r;
-    if ((r = ensure(c, c->g_xy, 16 * n)) || (r = ensure(c, c->g_co, 16 * n)) || (r = ensure(c, c->g_rgb, 16 * n)))
-        return r;
+    if ((r = ensure(c, c->g_proj, 48 * n)) != GS_OK) return r;
     if ((r = ensure(c, c->img, 12 * pix)) || (r = ensure(c, c->dimg, 12 * pix)) || (r = ensure(c, c->maps, 36 * pix)) ||
         (r = ensure(c, c->acc, 16 * (size_t)vb.B + 64)))
         return r;
@@ -328,8 +327,12 @@ AdamArgs adam_args(const gs_hparams &hp, int64_t step, int32_t B, long long *dst
 gs_status check_hparams(gs_ctx *c, const gs_hparams *hp)
 {
     if (ilog2_exact(hp->tile) < 0) return fail(c, GS_ERR_INVALID_ARG, "tile must be 8, 16 or 32");
-    if (!blend_config_ok(hp->tile, hp->smem_batch))
-        return fail(c, GS_ERR_INVALID_ARG, "smem_batch must be 32, 64 or 128 (32 or 64 with tile 32)");
+    if (hp->px_per_thread != 1 && hp->px_per_thread != 2 && hp->px_per_thread != 4)
+        return fail(c, GS_ERR_INVALID_ARG, "px_per_thread must be 1, 2 or 4");
+    if (!blend_config_ok(hp->tile, hp->smem_batch, hp->px_per_thread))
+        return fail(c, GS_ERR_INVALID_ARG,
+                    "unsupported (tile, smem_batch, px_per_thread): smem_batch 32, 64 or 128 (32 or 64 with tile 32 "
+                    "and one pixel per thread); two or four pixels per thread need tile 16 or 32");
     if (!(hp->alpha_max > 0.f && hp->alpha_max < 1.f) || !(hp->alpha_min >= 0.f) || !(hp->T_min >= 0.f))
         return fail(c, GS_ERR_INVALID_ARG, "blend thresholds out of range");
     return GS_OK;
@@ -384,6 +387,7 @@ gs_status gs_default_hparams(gs_hparams *hp)
     memset(hp, 0, sizeof *hp);
     hp->tile = 16;
     hp->smem_batch = 64;
+    hp->px_per_thread = 1;
     hp->strict_nonfinite = 0;
     hp->alpha_min = 1.0f / 255.0f;
     hp->alpha_max = 0.99f;
@@ -429,7 +433,7 @@ gs_status gs_destroy(gs_ctx *c)
     if (!c) return GS_ERR_INVALID_ARG;
     DBuf *bufs[] = {&c->ntiles, &c->offsets, &c->scan_tmp, &c->total, &c->keys_alt, &c->vals_alt, &c->sort_tmp,
                     &c->pk, &c->pv, &c->pk_alt, &c->pv_alt, &c->rect,
-                    &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_xy, &c->g_co, &c->g_rgb, &c->keys,
+                    &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_proj, &c->keys,
                     &c->vals, &c->ranges, &c->count, &c->img, &c->dimg, &c->T_final, &c->n_contrib, &c->maps,
                     &c->acc};
     for (DBuf *b : bufs)
@@ -574,7 +578,7 @@ gs_status gs_render_fwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, con
     if (r != GS_OK) return r;
     set_images(vb, img, T_final, n_contrib, nullptr);
     launch_blend_fwd(vb, proj_of(proj), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges), blend_of(c->hp),
-                     c->hp.smem_batch, c->status, S(stream));
+                     c->hp.smem_batch, c->hp.px_per_thread, c->status, S(stream));
     return cuda_check(c, "gs_render_fwd");
 }
 
@@ -601,7 +605,7 @@ gs_status gs_render_bwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, con
     GradView gv{reinterpret_cast<float4 *>(out->d_xy_o), reinterpret_cast<float4 *>(out->d_conic),
                 reinterpret_cast<float4 *>(out->d_rgb)};
     launch_blend_bwd(vb, proj_of(proj), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges), blend_of(c->hp),
-                     c->hp.smem_batch, gv, c->status, st);
+                     c->hp.smem_batch, c->hp.px_per_thread, gv, c->status, st);
     return cuda_check(c, "gs_render_bwd");
 }
 
@@ -687,21 +691,18 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     if (r != GS_OK) return r;
     set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
     const BlendParams bp = blend_of(c->hp);
-    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch,
+    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
                      c->status, st);
     mark(c, st, 6);
     launch_loss(ptr<float>(c->img), targets, B, vb.v[0].W, vb.v[0].H, c->hp.lambda_dssim, loss_out,
                 ptr<float>(c->dimg), ptr<float>(c->maps), ptr<double>(c->acc), st);
     mark(c, st, 7);
-    const size_t gbytes = 16 * (size_t)n;
-    if (gbytes) {
-        cudaMemsetAsync(c->g_xy.p, 0, gbytes, st);
-        cudaMemsetAsync(c->g_co.p, 0, gbytes, st);
-        cudaMemsetAsync(c->g_rgb.p, 0, gbytes, st);
-    }
+    // three gradient planes of n float4 each, in one buffer: (u, v, opacity), conic, rgb
+    if (n) cudaMemsetAsync(c->g_proj.p, 0, 48 * (size_t)n, st);
     mark(c, st, 8);
-    const GradView gv{ptr<float4>(c->g_xy), ptr<float4>(c->g_co), ptr<float4>(c->g_rgb)};
-    launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch,
+    float4 *gp = ptr<float4>(c->g_proj);
+    const GradView gv{gp, gp + n, gp + 2 * n};
+    launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
                      gv, c->status, st);
     mark(c, st, 9);
     launch_preprocess_bwd(sv, vb, pv, gv, mut_of(g), st);
@@ -752,7 +753,7 @@ gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int
         vb.v[v].n_contrib = ptr<uint32_t>(c->n_contrib) + off;
         off += hw;
     }
-    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), blend_of(c->hp), c->hp.smem_batch,
+    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), blend_of(c->hp), c->hp.smem_batch, c->hp.px_per_thread,
                      c->status, st);
     return cuda_check(c, "gs_render");
 }

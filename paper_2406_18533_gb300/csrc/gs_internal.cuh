@@ -60,6 +60,8 @@ struct ProjView {
     int64_t N;
 };
 
+// Gradients per (view, Gaussian) entry: three separate float4 arrays (the
+// three atomics of an entry then go to different L2 slices).
 struct GradView {
     float4 *d_xy_o, *d_conic, *d_rgb;
 };
@@ -121,13 +123,14 @@ void launch_compose_keys(const ViewBatch &vb, int64_t N, const uint32_t *tiles, 
                          const uint32_t *count, uint64_t capacity, const float4 *rgb_d, uint64_t *keys,
                          cudaStream_t st);
 
-// chunk: list entries a warp gathers and filters per shared-memory refill
-// (blend_config_ok says which (tile, chunk) pairs are built).
-bool blend_config_ok(int tile, int chunk);
+// chunk: list entries a warp gathers and filters per shared-memory refill;
+// ppt: pixels per thread (blend_config_ok says which combinations are built).
+bool blend_config_ok(int tile, int chunk, int ppt);
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                      const BlendParams &bp, int chunk, DevStatus *status, cudaStream_t st);
+                      const BlendParams &bp, int chunk, int ppt, DevStatus *status, cudaStream_t st);
 void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                      const BlendParams &bp, int chunk, const GradView &g, DevStatus *status, cudaStream_t st);
+                      const BlendParams &bp, int chunk, int ppt, const GradView &g, DevStatus *status,
+                      cudaStream_t st);
 
 void launch_loss(const float *img, const float *target, int B, int W, int H, float lambda, float *loss_out,
                  float *d_img, float *maps, double *acc, cudaStream_t st);

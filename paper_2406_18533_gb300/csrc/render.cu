@@ -1,7 +1,8 @@
 // K6 (front-to-back compositing, Sec. 2.1 step 2) and K7 (its backward).
 //
-// One CTA per screen tile of TILE x TILE pixels, one pixel per thread; warp w
-// owns an 8 x 4 block of the tile.  Warps work independently (no block-wide
+// One CTA per screen tile of TILE x TILE pixels; a thread blends PPT pixels
+// of one column (rows 4 apart), so warp w owns an 8 x 4 PPT block of the
+// tile.  Warps work independently (no block-wide
 // barrier inside the walk): a warp reads the tile's depth-sorted list in
 // rounds of 32 entries (lane i gathers entry i with coalesced 8/16-byte loads;
 // the warps of a tile hit the same L1 lines; the next round's gathers are
@@ -19,7 +20,7 @@
 // recovers the transmittance before each contributor by division from
 // T_final (no per-fragment state is stored), reduces a Gaussian's nine
 // gradient components over the warp with a reduce-scatter (14 shuffles) and
-// adds them with one 9-lane atomic instruction per (warp, Gaussian).
+// adds them as three float4 atomics from three lanes per (warp, Gaussian).
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -30,12 +31,20 @@ constexpr float LOG2E = 1.4426950408889634f;
 // Base-2 exponent of the Gaussian at offset (dx, dy), evaluated as
 // dy (C dy + B dx) + A dx^2 with explicitly rounded operations, so the
 // forward and the backward get the same bits whatever the compiler fuses
-// around it; q = (A, B, C, o) = (-a/2, -b, -c/2) log2(e), opacity.
-__device__ __forceinline__ float power2(const float4 &q, float dx, float dy)
+// around it; q = (A, B, C, o) = (-a/2, -b, -c/2) log2(e), opacity.  The dx
+// terms are shared by the pixels of one column.
+struct DxTerms {
+    float adx2, bdx;          // A dx^2 and B dx
+};
+
+__device__ __forceinline__ DxTerms dx_terms(const float4 &q, float dx)
 {
-    const float adx2 = __fmul_rn(q.x, __fmul_rn(dx, dx));
-    const float bdx = __fmul_rn(q.y, dx);
-    return __fmaf_rn(dy, __fmaf_rn(q.z, dy, bdx), adx2);
+    return DxTerms{__fmul_rn(q.x, __fmul_rn(dx, dx)), __fmul_rn(q.y, dx)};
+}
+
+__device__ __forceinline__ float power2(const float4 &q, const DxTerms &t, float dy)
+{
+    return __fmaf_rn(dy, __fmaf_rn(q.z, dy, t.bdx), t.adx2);
 }
 
 __device__ __forceinline__ float ex2(float x)
@@ -57,25 +66,45 @@ __device__ __forceinline__ float exponent_cut(float o, float alpha_min)
     return o > alpha_min ? __log2f(__fdividef(alpha_min, o)) : 1.f;
 }
 
-// Does the ellipse {d : d^T Q d <= 2 ln(o / alpha_min)} around (u, v) -- the
-// only offsets at which alpha can reach alpha_min -- meet the pixel-centre
-// box [x0, x1] x [y0, y1]?  Its bounding half-widths are sqrt(2 L Q^-1_xx)
-// and sqrt(2 L Q^-1_yy), padded (0.1 % + 0.05 px) so float rounding never
-// drops a pixel the per-pixel test would accept; the determinant uses
-// Kahan's form (no cancellation loss); a determinant that rounds to <= 0 keeps
-// the Gaussian.
+// Can alpha reach alpha_min anywhere in the pixel-centre box [x0, x1] x
+// [y0, y1]?  That is: does min over the box of f(d) = a dx^2 + 2 b dx dy +
+// c dy^2 (d = pixel - centre) stay within L = 2 ln(o / alpha_min)?  f is
+// convex with its minimum 0 at the centre, so for a centre outside the box
+// the minimum lies on an edge that faces the centre (x = clamp(u) or y =
+// clamp(v)).  Along such an edge f is a parabola, minimised at the clamp of
+// its vertex and evaluated as c (dy - dy*)^2 + (det / c) dx^2 (a sum of
+// non-negative terms: no cancellation); the determinant uses Kahan's form.
+// The acceptance bound is widened (0.1 % + 1e-6 x the conic's condition
+// number, + 1e-4) beyond the rounding error of the per-pixel exponent, so
+// the test never drops a Gaussian the per-pixel test would blend.  A
+// non-positive-definite conic keeps the Gaussian.
 __device__ __forceinline__ bool alpha_box_hits(const float4 &co, float u, float v, float alpha_min, float x0,
                                                float x1, float y0, float y1)
 {
     if (!(co.w > alpha_min)) return false;                 // never reaches alpha_min
-    const float w = co.y * co.y;
-    const float e = __fmaf_rn(-co.y, co.y, w);
-    const float det = __fmaf_rn(co.x, co.z, -w) + e;
-    if (!(det > 0.f)) return true;
-    const float L2 = 2.f * __logf(co.w / alpha_min);
-    const float rx = sqrtf(L2 * co.z / det) * 1.001f + 0.05f;
-    const float ry = sqrtf(L2 * co.x / det) * 1.001f + 0.05f;
-    return !(u + rx < x0 || u - rx > x1 || v + ry < y0 || v - ry > y1);
+    const float a = co.x, b = co.y, c = co.z;
+    const float bb = b * b;
+    const float det = __fmaf_rn(a, c, -bb) + __fmaf_rn(-b, b, bb);
+    if (!(det > 0.f && a > 0.f && c > 0.f)) return true;
+    const float ex = fminf(fmaxf(u, x0), x1), ey = fminf(fmaxf(v, y0), y1);
+    if (ex == u && ey == v) return true;                   // centre inside the box
+    float fmin = INFINITY;
+    if (ex != u) {                                         // edge x = ex
+        const float dx = ex - u;
+        const float dys = -b * dx / c;
+        const float t = fminf(fmaxf(dys, y0 - v), y1 - v) - dys;
+        fmin = c * t * t + det / c * (dx * dx);
+    }
+    if (ey != v) {                                         // edge y = ey
+        const float dy = ey - v;
+        const float dxs = -b * dy / a;
+        const float t = fminf(fmaxf(dxs, x0 - u), x1 - u) - dxs;
+        fmin = fminf(fmin, a * t * t + det / a * (dy * dy));
+    }
+    const float L = 2.f * __logf(co.w / alpha_min);
+    const float tr = 0.5f * (a + c), r = sqrtf(0.25f * (a - c) * (a - c) + bb);
+    const float kappa = (tr + r) / fmaxf(tr - r, 1e-30f);  // condition number of the conic
+    return fmin <= L * (1.001f + 1e-6f * kappa) + 1e-4f;
 }
 
 __device__ __forceinline__ int find_view(const ViewBatch &vb, uint32_t tile_id)
@@ -112,29 +141,34 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float v[8], int lane
     return y;
 }
 
-// Tile-local geometry of this thread's pixel and its warp's 8 x 4 block.
+// Tile-local geometry of this thread's PPT pixels (one column, rows 4 apart)
+// and its warp's 8 x 4 PPT block.
+template <int PPT>
 struct PixelSite {
-    int px, py;
-    bool inside;
-    float fx, fy;             // pixel centre
+    int px, py[PPT];
+    bool inside[PPT];
+    float fx, fy[PPT];        // pixel centres
     float bx0, bx1, by0, by1; // pixel-centre extent of the warp's block
 };
 
-template <int TILE>
-__device__ __forceinline__ PixelSite pixel_site(const ViewCam &c, uint32_t local, int warp, int lane)
+template <int TILE, int PPT>
+__device__ __forceinline__ PixelSite<PPT> pixel_site(const ViewCam &c, uint32_t local, int warp, int lane)
 {
-    PixelSite s;
+    PixelSite<PPT> s;
     const int ty = (int)(local / (uint32_t)c.TX), tx = (int)(local % (uint32_t)c.TX);
-    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * 4;
+    const int wx = (warp % (TILE / 8)) * 8, wy = (warp / (TILE / 8)) * (4 * PPT);
     s.px = tx * TILE + wx + (lane & 7);
-    s.py = ty * TILE + wy + (lane >> 3);
-    s.inside = s.px < c.W && s.py < c.H;
     s.fx = (float)s.px + 0.5f;
-    s.fy = (float)s.py + 0.5f;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        s.py[k] = ty * TILE + wy + (lane >> 3) + 4 * k;
+        s.inside[k] = s.px < c.W && s.py[k] < c.H;
+        s.fy[k] = (float)s.py[k] + 0.5f;
+    }
     s.bx0 = (float)(tx * TILE + wx) + 0.5f;
     s.bx1 = s.bx0 + 7.f;
     s.by0 = (float)(ty * TILE + wy) + 0.5f;
-    s.by1 = s.by0 + 3.f;
+    s.by1 = s.by0 + (float)(4 * PPT - 1);
     return s;
 }
 
@@ -163,17 +197,18 @@ __device__ __forceinline__ Entry fetch_entry(const ProjView &p, const uint32_t *
 }
 
 // Bytes of dynamic shared memory per CTA.
-template <int TILE, int CH, bool BWD>
+template <int TILE, int CH, int PPT, bool BWD>
 constexpr size_t smem_bytes()
 {
-    return (size_t)(TILE * TILE / 32) * CH * ((BWD ? 4 : 3) * sizeof(float4) + sizeof(uint32_t));
+    return (size_t)(TILE * TILE / (32 * PPT)) * CH * ((BWD ? 4 : 3) * sizeof(float4) + sizeof(uint32_t));
 }
 
-template <int TILE, int CH>
-__global__ void __launch_bounds__(TILE *TILE) k_blend_fwd(ViewBatch vb, ProjView p, const uint32_t *vals,
-                                                          const uint2 *ranges, BlendParams bp, DevStatus *status)
+template <int TILE, int CH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, ProjView p, const uint32_t *vals,
+                                                                const uint2 *ranges, BlendParams bp,
+                                                                DevStatus *status)
 {
-    constexpr int NW = TILE * TILE / 32;
+    constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
     __shared__ uint32_t s_red[NW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -185,14 +220,21 @@ __global__ void __launch_bounds__(TILE *TILE) k_blend_fwd(ViewBatch vb, ProjView
     const uint32_t tile_id = blockIdx.x;
     const int v = find_view(vb, tile_id);
     const ViewCam &c = vb.v[v];
-    const PixelSite ps = pixel_site<TILE>(c, tile_id - c.tile_base, warp, lane);
+    const PixelSite<PPT> ps = pixel_site<TILE, PPT>(c, tile_id - c.tile_base, warp, lane);
     const uint2 rg = ranges[tile_id];
     const int64_t vbase = (int64_t)v * p.N;
     const uint32_t lt = (1u << lane) - 1u;
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t nc = 0, ne = 0;
-    bool done = !ps.inside;
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    uint32_t nc[PPT], ne[PPT];
+    bool done[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        T[k] = 1.f;
+        C0[k] = C1[k] = C2[k] = 0.f;
+        nc[k] = ne[k] = 0u;
+        done[k] = !ps.inside[k];
+    }
     // Rounds of 32 entries, software-pipelined: the gathers of the next round
     // are in flight while the current one is tested and staged.  Hits pile up
     // in the warp's buffer, which is walked when another round could overflow
@@ -217,46 +259,65 @@ __global__ void __launch_bounds__(TILE *TILE) k_blend_fwd(ViewBatch vb, ProjView
         const bool last = base + 32 >= rg.y;
         if (n > CH - 32 || last) {
             __syncwarp();
-            if (!done) {
+            bool all_done = true;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) all_done = all_done && done[k];
+            if (!all_done) {
                 for (int i = 0; i < n; ++i) {
                     const float4 xyc = s_xyc[i];
                     const float4 q = s_q[i];
-                    const float pw = power2(q, __fsub_rn(ps.fx, xyc.x), __fsub_rn(ps.fy, xyc.y));
-                    if (!(pw >= xyc.z && pw <= 0.f)) continue;      // below the alpha cut, or power > 0
-                    const float alpha = fminf(bp.alpha_max, q.w * ex2(pw));
-                    if (alpha < bp.alpha_min) continue;
-                    const float Tn = T * (1.f - alpha);
-                    if (Tn < bp.T_min) {
-                        done = true;
-                        ne = s_pos[i] + 1;
-                        break;
+                    const DxTerms dt = dx_terms(q, __fsub_rn(ps.fx, xyc.x));
+                    bool still = false;
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        if (done[k]) continue;
+                        still = true;
+                        const float pw = power2(q, dt, __fsub_rn(ps.fy[k], xyc.y));
+                        if (!(pw >= xyc.z && pw <= 0.f)) continue;  // below the alpha cut, or power > 0
+                        const float alpha = fminf(bp.alpha_max, q.w * ex2(pw));
+                        if (alpha < bp.alpha_min) continue;
+                        const float Tn = T[k] * (1.f - alpha);
+                        if (Tn < bp.T_min) {
+                            done[k] = true;
+                            ne[k] = s_pos[i] + 1;
+                            continue;
+                        }
+                        const float4 rgb = s_rgb[i];
+                        const float w = alpha * T[k];
+                        C0[k] += rgb.x * w;
+                        C1[k] += rgb.y * w;
+                        C2[k] += rgb.z * w;
+                        T[k] = Tn;
+                        nc[k] = s_pos[i] + 1;
                     }
-                    const float4 rgb = s_rgb[i];
-                    const float w = alpha * T;
-                    C0 += rgb.x * w;
-                    C1 += rgb.y * w;
-                    C2 += rgb.z * w;
-                    T = Tn;
-                    nc = s_pos[i] + 1;
+                    if (!still) break;
                 }
-                if (!done) ne = min(base + 32, rg.y) - rg.x;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (!done[k]) ne[k] = min(base + 32, rg.y) - rg.x;
             }
             n = 0;
             __syncwarp();
-            if (__all_sync(0xffffffffu, done)) break;
+            bool fin = true;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) fin = fin && done[k];
+            if (__all_sync(0xffffffffu, fin)) break;
         }
     }
-    if (ps.inside) {
-        const int64_t hw = (int64_t)c.W * c.H;
-        const int64_t pix = (int64_t)ps.py * c.W + ps.px;
-        c.img[pix] = C0 + T * bp.bg[0];
-        c.img[hw + pix] = C1 + T * bp.bg[1];
-        c.img[2 * hw + pix] = C2 + T * bp.bg[2];
-        c.T_final[pix] = T;
-        c.n_contrib[pix] = nc;
+    const int64_t hw = (int64_t)c.W * c.H;
+    uint32_t evals = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (!ps.inside[k]) continue;
+        const int64_t pix = (int64_t)ps.py[k] * c.W + ps.px;
+        c.img[pix] = C0[k] + T[k] * bp.bg[0];
+        c.img[hw + pix] = C1[k] + T[k] * bp.bg[1];
+        c.img[2 * hw + pix] = C2[k] + T[k] * bp.bg[2];
+        c.T_final[pix] = T[k];
+        c.n_contrib[pix] = nc[k];
+        evals += ne[k];
     }
     // (pixel, list position) evaluations until termination, for the roofline counters
-    uint32_t evals = ps.inside ? ne : 0u;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
     if (lane == 0) s_red[warp] = evals;
@@ -268,12 +329,12 @@ __global__ void __launch_bounds__(TILE *TILE) k_blend_fwd(ViewBatch vb, ProjView
     }
 }
 
-template <int TILE, int CH>
-__global__ void __launch_bounds__(TILE *TILE) k_blend_bwd(ViewBatch vb, ProjView p, const uint32_t *vals,
-                                                          const uint2 *ranges, BlendParams bp, GradView gv,
-                                                          DevStatus *status)
+template <int TILE, int CH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, ProjView p, const uint32_t *vals,
+                                                                const uint2 *ranges, BlendParams bp, GradView gv,
+                                                                DevStatus *status)
 {
-    constexpr int NW = TILE * TILE / 32;
+    constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
     __shared__ unsigned long long s_red64[2][NW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -286,29 +347,37 @@ __global__ void __launch_bounds__(TILE *TILE) k_blend_bwd(ViewBatch vb, ProjView
     const uint32_t tile_id = blockIdx.x;
     const int v = find_view(vb, tile_id);
     const ViewCam &c = vb.v[v];
-    const PixelSite ps = pixel_site<TILE>(c, tile_id - c.tile_base, warp, lane);
+    const PixelSite<PPT> ps = pixel_site<TILE, PPT>(c, tile_id - c.tile_base, warp, lane);
     const uint2 rg = ranges[tile_id];
     const int64_t vbase = (int64_t)v * p.N;
     const uint32_t lt = (1u << lane) - 1u;
     const int64_t hw = (int64_t)c.W * c.H;
 
-    float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
-    uint32_t nc = 0;
-    if (ps.inside) {
-        const int64_t pix = (int64_t)ps.py * c.W + ps.px;
-        T = c.T_final[pix];
-        nc = c.n_contrib[pix];
-        dC0 = c.d_img[pix];
-        dC1 = c.d_img[hw + pix];
-        dC2 = c.d_img[2 * hw + pix];
+    float T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], B0[PPT], B1[PPT], B2[PPT];
+    uint32_t nc[PPT], wnc = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        T[k] = 1.f;
+        dC0[k] = dC1[k] = dC2[k] = 0.f;
+        nc[k] = 0u;
+        B0[k] = bp.bg[0];                            // colour behind (normalised)
+        B1[k] = bp.bg[1];
+        B2[k] = bp.bg[2];
+        if (ps.inside[k]) {
+            const int64_t pix = (int64_t)ps.py[k] * c.W + ps.px;
+            T[k] = c.T_final[pix];
+            nc[k] = c.n_contrib[pix];
+            dC0[k] = c.d_img[pix];
+            dC1[k] = c.d_img[hw + pix];
+            dC2[k] = c.d_img[2 * hw + pix];
+        }
+        wnc = max(wnc, nc[k]);
     }
     // this warp walks back to front from its own largest n_contrib, never past the list
-    uint32_t wnc = nc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wnc = max(wnc, __shfl_xor_sync(0xffffffffu, wnc, o));
     wnc = min(wnc, rg.y - rg.x);
 
-    float B0 = bp.bg[0], B1 = bp.bg[1], B2 = bp.bg[2];   // colour behind (normalised)
     uint32_t evals = 0, walked = 0;
     // Rounds of 32 entries from the walk's top down, software-pipelined like
     // the forward; hits are staged in descending list order and walked when
@@ -339,49 +408,55 @@ __global__ void __launch_bounds__(TILE *TILE) k_blend_bwd(ViewBatch vb, ProjView
             const uint32_t rel = s_pos[i];
             const float4 xyc = s_xyc[i];
             const float4 q = s_q[i];
-            const float dx = __fsub_rn(ps.fx, xyc.x), dy = __fsub_rn(ps.fy, xyc.y);
-            bool act = rel < nc;
-            walked += act;
-            const float pw = power2(q, dx, dy);
-            act = act && pw >= xyc.z && pw <= 0.f;
+            const float dx = __fsub_rn(ps.fx, xyc.x);
+            const DxTerms dt = dx_terms(q, dx);
+            // this lane's gradient contributions, summed over its pixels
             float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float gbl = 0.f;
-            if (act) {
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (!(rel < nc[k])) continue;
+                ++walked;
+                const float dy = __fsub_rn(ps.fy[k], xyc.y);
+                const float pw = power2(q, dt, dy);
+                if (!(pw >= xyc.z && pw <= 0.f)) continue;
                 const float G = ex2(pw);
                 const float oG = q.w * G;
                 const float alpha = fminf(bp.alpha_max, oG);
-                act = !(alpha < bp.alpha_min);
-                if (act) {
-                    ++evals;
-                    const float4 rgb = s_rgb[i];
-                    const float Tj = __fdividef(T, 1.f - alpha);
-                    const float w = alpha * Tj;
-                    vv[6] = w * dC0;
-                    vv[7] = w * dC1;
-                    gbl = w * dC2;
-                    const float dalpha = Tj * ((rgb.x - B0) * dC0 + (rgb.y - B1) * dC1 + (rgb.z - B2) * dC2);
-                    B0 = alpha * rgb.x + (1.f - alpha) * B0;
-                    B1 = alpha * rgb.y + (1.f - alpha) * B1;
-                    B2 = alpha * rgb.z + (1.f - alpha) * B2;
-                    T = Tj;
-                    if (oG < bp.alpha_max) {
-                        const float4 cn = s_cn[i];
-                        const float dpow = alpha * dalpha;
-                        vv[2] = G * dalpha;
-                        vv[0] = (cn.x * dx + cn.y * dy) * dpow;
-                        vv[1] = (cn.y * dx + cn.z * dy) * dpow;
-                        vv[3] = -0.5f * dx * dx * dpow;
-                        vv[4] = -dx * dy * dpow;
-                        vv[5] = -0.5f * dy * dy * dpow;
-                    }
+                if (alpha < bp.alpha_min) continue;
+                any = true;
+                ++evals;
+                const float4 rgb = s_rgb[i];
+                const float Tj = __fdividef(T[k], 1.f - alpha);
+                const float w = alpha * Tj;
+                vv[6] += w * dC0[k];
+                vv[7] += w * dC1[k];
+                gbl += w * dC2[k];
+                const float e0 = rgb.x - B0[k], e1 = rgb.y - B1[k], e2 = rgb.z - B2[k];
+                const float dalpha = Tj * (e0 * dC0[k] + e1 * dC1[k] + e2 * dC2[k]);
+                B0[k] += alpha * e0;
+                B1[k] += alpha * e1;
+                B2[k] += alpha * e2;
+                T[k] = Tj;
+                if (oG < bp.alpha_max) {
+                    const float4 cn = s_cn[i];
+                    const float dpow = alpha * dalpha;
+                    const float hx = -0.5f * dpow * dx;
+                    vv[2] += G * dalpha;
+                    vv[0] += (cn.x * dx + cn.y * dy) * dpow;
+                    vv[1] += (cn.y * dx + cn.z * dy) * dpow;
+                    vv[3] += hx * dx;
+                    vv[4] += (hx + hx) * dy;
+                    vv[5] += -0.5f * dpow * dy * dy;
                 }
             }
-            const uint32_t ballot = __ballot_sync(0xffffffffu, act);
+            const uint32_t ballot = __ballot_sync(0xffffffffu, any);
             if (ballot == 0u) continue;
             const int64_t idx = vbase + __float_as_uint(s_rgb[i].w);
             if (__popc(ballot) == 1) {
-                // one contributing pixel in this warp: no reduction needed
-                if (act) {
+                // one contributing lane in this warp: no reduction needed
+                if (any) {
                     atomicAdd(&gv.d_xy_o[idx], make_float4(vv[0], vv[1], vv[2], 0.f));
                     atomicAdd(&gv.d_conic[idx], make_float4(vv[3], vv[4], vv[5], 0.f));
                     atomicAdd(&gv.d_rgb[idx], make_float4(vv[6], vv[7], gbl, 0.f));
@@ -391,13 +466,16 @@ __global__ void __launch_bounds__(TILE *TILE) k_blend_bwd(ViewBatch vb, ProjView
             const float y = warp_reduce_scatter8(vv, lane);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) gbl += __shfl_xor_sync(0xffffffffu, gbl, o);
-            // value k = (lane >> 2) & 7 lives in lanes with lane % 4 == 0; lane 1 adds the ninth
-            const int vk = (lane >> 2) & 7;
-            float *dst = vk < 3 ? reinterpret_cast<float *>(&gv.d_xy_o[idx]) + vk
-                         : vk < 6 ? reinterpret_cast<float *>(&gv.d_conic[idx]) + (vk - 3)
-                                  : reinterpret_cast<float *>(&gv.d_rgb[idx]) + (vk - 6);
-            if ((lane & 3) == 0) atomicAdd(dst, y);
-            else if (lane == 1) atomicAdd(reinterpret_cast<float *>(&gv.d_rgb[idx]) + 2, gbl);
+            // value k lives in lanes 4k .. 4k+3: lane L < 3 gathers values 3L .. 3L+2
+            // and adds them as one float4 (lane 2 takes the ninth value, gbl)
+            const int src = 12 * (lane < 3 ? lane : 0);
+            const float a0 = __shfl_sync(0xffffffffu, y, src);
+            const float a1 = __shfl_sync(0xffffffffu, y, src + 4);
+            const float a2 = __shfl_sync(0xffffffffu, y, (src + 8) & 31);
+            if (lane < 3) {
+                float4 *dst = lane == 0 ? &gv.d_xy_o[idx] : lane == 1 ? &gv.d_conic[idx] : &gv.d_rgb[idx];
+                atomicAdd(dst, make_float4(a0, a1, lane == 2 ? gbl : a2, 0.f));
+            }
         }
         n = 0;
         __syncwarp();
@@ -427,67 +505,71 @@ bool smem_opt_in(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 
-template <int TILE, int CH>
+template <int TILE, int CH, int PPT>
 void fwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                 const BlendParams &bp, DevStatus *status, cudaStream_t st)
 {
-    constexpr size_t sm = smem_bytes<TILE, CH, false>();
-    static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH>, sm);
+    constexpr size_t sm = smem_bytes<TILE, CH, PPT, false>();
+    static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH, PPT>, sm);
     (void)ok;
-    k_blend_fwd<TILE, CH><<<vb.total_tiles, TILE * TILE, sm, st>>>(vb, p, vals, ranges, bp, status);
+    k_blend_fwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status);
 }
 
-template <int TILE, int CH>
+template <int TILE, int CH, int PPT>
 void bwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                 const BlendParams &bp, const GradView &g, DevStatus *status, cudaStream_t st)
 {
-    constexpr size_t sm = smem_bytes<TILE, CH, true>();
-    static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH>, sm);
+    constexpr size_t sm = smem_bytes<TILE, CH, PPT, true>();
+    static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH, PPT>, sm);
     (void)ok;
-    k_blend_bwd<TILE, CH><<<vb.total_tiles, TILE * TILE, sm, st>>>(vb, p, vals, ranges, bp, g, status);
+    k_blend_bwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status);
 }
 
 }  // namespace
 
-// Supported (tile, entries per warp refill): 8 and 16 with 32, 64 or 128;
-// 32 with 32 or 64 (its 32 warps' slices must fit in shared memory).
-bool blend_config_ok(int tile, int chunk)
+// Built (tile, entries per warp refill, pixels per thread) combinations.
+// One pixel per thread (warp = 8 x 4 pixels): tile 8 or 16 with 32, 64 or
+// 128 entries; tile 32 with 32 or 64 (its 32 warps' slices must fit in shared
+// memory).  Two (warp = 8 x 8) or four (8 x 16): tile 16 or 32 with 32, 64
+// or 128.
+bool blend_config_ok(int tile, int chunk, int ppt)
 {
     if (chunk != 32 && chunk != 64 && chunk != 128) return false;
-    if (tile == 8 || tile == 16) return true;
-    return tile == 32 && chunk <= 64;
+    if (ppt == 1) return tile == 8 || tile == 16 || (tile == 32 && chunk <= 64);
+    if (ppt == 2 || ppt == 4) return tile == 16 || tile == 32;
+    return false;
 }
 
+#define GS_BLEND_CASES(X)                                                                                      \
+    X(8, 32, 1) X(8, 64, 1) X(8, 128, 1) X(16, 32, 1) X(16, 64, 1) X(16, 128, 1) X(32, 32, 1) X(32, 64, 1)   \
+    X(16, 32, 2) X(16, 64, 2) X(16, 128, 2) X(32, 32, 2) X(32, 64, 2) X(32, 128, 2) X(16, 32, 4) X(16, 64, 4)   \
+    X(16, 128, 4) X(32, 32, 4) X(32, 64, 4) X(32, 128, 4)
+
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                      const BlendParams &bp, int chunk, DevStatus *status, cudaStream_t st)
+                      const BlendParams &bp, int chunk, int ppt, DevStatus *status, cudaStream_t st)
 {
     if (vb.total_tiles == 0) return;
-    switch (vb.tile * 1000 + chunk) {
-    case 8032: fwd_launch<8, 32>(vb, p, vals, ranges, bp, status, st); break;
-    case 8064: fwd_launch<8, 64>(vb, p, vals, ranges, bp, status, st); break;
-    case 8128: fwd_launch<8, 128>(vb, p, vals, ranges, bp, status, st); break;
-    case 16032: fwd_launch<16, 32>(vb, p, vals, ranges, bp, status, st); break;
-    case 16128: fwd_launch<16, 128>(vb, p, vals, ranges, bp, status, st); break;
-    case 32032: fwd_launch<32, 32>(vb, p, vals, ranges, bp, status, st); break;
-    case 32064: fwd_launch<32, 64>(vb, p, vals, ranges, bp, status, st); break;
-    default: fwd_launch<16, 64>(vb, p, vals, ranges, bp, status, st); break;
+    switch (vb.tile * 10000 + chunk * 10 + ppt) {
+#define GS_FWD_CASE(T, C, P) \
+    case T * 10000 + C * 10 + P: fwd_launch<T, C, P>(vb, p, vals, ranges, bp, status, st); break;
+        GS_BLEND_CASES(GS_FWD_CASE)
+#undef GS_FWD_CASE
+    default: fwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, status, st); break;
     }
     count_launches(1);
 }
 
 void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                      const BlendParams &bp, int chunk, const GradView &g, DevStatus *status, cudaStream_t st)
+                      const BlendParams &bp, int chunk, int ppt, const GradView &g, DevStatus *status,
+                      cudaStream_t st)
 {
     if (vb.total_tiles == 0) return;
-    switch (vb.tile * 1000 + chunk) {
-    case 8032: bwd_launch<8, 32>(vb, p, vals, ranges, bp, g, status, st); break;
-    case 8064: bwd_launch<8, 64>(vb, p, vals, ranges, bp, g, status, st); break;
-    case 8128: bwd_launch<8, 128>(vb, p, vals, ranges, bp, g, status, st); break;
-    case 16032: bwd_launch<16, 32>(vb, p, vals, ranges, bp, g, status, st); break;
-    case 16128: bwd_launch<16, 128>(vb, p, vals, ranges, bp, g, status, st); break;
-    case 32032: bwd_launch<32, 32>(vb, p, vals, ranges, bp, g, status, st); break;
-    case 32064: bwd_launch<32, 64>(vb, p, vals, ranges, bp, g, status, st); break;
-    default: bwd_launch<16, 64>(vb, p, vals, ranges, bp, g, status, st); break;
+    switch (vb.tile * 10000 + chunk * 10 + ppt) {
+#define GS_BWD_CASE(T, C, P) \
+    case T * 10000 + C * 10 + P: bwd_launch<T, C, P>(vb, p, vals, ranges, bp, g, status, st); break;
+        GS_BLEND_CASES(GS_BWD_CASE)
+#undef GS_BWD_CASE
+    default: bwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, g, status, st); break;
     }
     count_launches(1);
 }

@@ -39,7 +39,7 @@ def test_abi_version_and_defaults(libgs):
     from paper_2406_18533_gb300 import binding
     assert libgs.gs_abi_version() == 1
     hp = binding.default_hparams()
-    assert hp.tile == 16 and hp.smem_batch == 64
+    assert hp.tile == 16 and hp.smem_batch == 64 and hp.px_per_thread == 1
     assert abs(hp.alpha_min - 1 / 255) < 1e-9 and abs(hp.alpha_max - 0.99) < 1e-7 and abs(hp.T_min - 1e-4) < 1e-10
     assert hp.scale_lr_sqrt_b == 1 and hp.scale_beta_pow_b == 1 and abs(hp.lambda_dssim - 0.2) < 1e-7
 
@@ -80,6 +80,9 @@ def test_invalid_arguments_rejected_on_host(libgs):
     assert libgs.gs_create(ctypes.byref(h), ctypes.byref(hp)) == b.GS_ERR_INVALID_ARG
     hp = b.default_hparams(tile=32, smem_batch=128)
     assert libgs.gs_create(ctypes.byref(h), ctypes.byref(hp)) == b.GS_ERR_INVALID_ARG
+    for ppt, tile in ((0, 16), (3, 16), (2, 8), (4, 8)):   # 1, 2 or 4 pixels per thread; 2 and 4 need tile >= 16
+        hp = b.default_hparams(px_per_thread=ppt, tile=tile)
+        assert libgs.gs_create(ctypes.byref(h), ctypes.byref(hp)) == b.GS_ERR_INVALID_ARG
     assert libgs.gs_create(None, None) == b.GS_ERR_INVALID_ARG
     assert libgs.gs_destroy(None) == b.GS_ERR_INVALID_ARG
     size = ctypes.c_size_t(0)

@@ -102,10 +102,10 @@ def test_bin_capacity_overflow_reports_needed(eng, oracle):
 
 # ------------------------------------------------------------------ blending, forward and backward
 
-def _stage_case(eng, oracle, seed, W, H, n, tile, batch):
+def _stage_case(eng, oracle, seed, W, H, n, tile, batch, ppt=1):
     pj = synth.synthetic_proj(n, W, H, seed=seed, ties=50)
     cam = synth.test_camera(W, H)
-    ctx = eng.Context(tile=tile, smem_batch=batch)
+    ctx = eng.Context(tile=tile, smem_batch=batch, px_per_thread=ppt)
     proj = upload_proj(eng, [pj])
     bins = ctx.bin(proj, [cam])
     img, T, nc = ctx.render_fwd(proj, bins, [cam])
@@ -114,10 +114,12 @@ def _stage_case(eng, oracle, seed, W, H, n, tile, batch):
     return ctx, pj, cam, proj, bins, (img, T, nc), (toff, gidx), ref
 
 
-@pytest.mark.parametrize("tile,batch", [(16, 64), (8, 32), (32, 64), (16, 128), (8, 128), (32, 32)])
-def test_render_fwd_stage(eng, oracle, tile, batch):
+@pytest.mark.parametrize("tile,batch,ppt", [(16, 64, 1), (8, 32, 1), (32, 64, 1), (16, 128, 1), (8, 128, 1),
+                                            (32, 32, 1), (16, 64, 2), (16, 32, 2), (32, 128, 2), (32, 32, 2),
+                                            (16, 64, 4), (32, 32, 4)])
+def test_render_fwd_stage(eng, oracle, tile, batch, ppt):
     W, H = 150, 90
-    _, _, _, _, _, (img, T, nc), _, ref = _stage_case(eng, oracle, 5, W, H, 4000, tile, batch)
+    _, _, _, _, _, (img, T, nc), _, ref = _stage_case(eng, oracle, 5, W, H, 4000, tile, batch, ppt)
     ok = ref["margin"] > MARGIN
     assert ok.mean() > 0.97
     img = img[0].cpu().numpy()
@@ -127,10 +129,12 @@ def test_render_fwd_stage(eng, oracle, tile, batch):
     assert ref["n_contrib"].max() > 20
 
 
-@pytest.mark.parametrize("tile,batch", [(16, 64), (8, 128), (32, 32), (16, 32)])
-def test_render_bwd_stage(eng, oracle, tile, batch):
+@pytest.mark.parametrize("tile,batch,ppt", [(16, 64, 1), (8, 128, 1), (32, 32, 1), (16, 32, 1), (16, 64, 2),
+                                            (32, 64, 2), (16, 128, 2), (16, 64, 4), (32, 128, 4)])
+def test_render_bwd_stage(eng, oracle, tile, batch, ppt):
     W, H = 120, 100
-    ctx, pj, cam, proj, bins, (img, T, nc), (toff, gidx), ref = _stage_case(eng, oracle, 9, W, H, 3000, tile, batch)
+    ctx, pj, cam, proj, bins, (img, T, nc), (toff, gidx), ref = _stage_case(eng, oracle, 9, W, H, 3000, tile, batch,
+                                                                            ppt)
     rng = np.random.default_rng(1)
     dimg = rng.standard_normal((3, H, W)).astype(np.float32)
     dimg[:, ref["margin"] <= MARGIN] = 0.0          # flagged pixels contribute on neither side
@@ -557,3 +561,23 @@ def test_c2_full_size_sampled_views(eng, oracle):
         loss, _ = ctx.loss(imgs[b][None].contiguous(), torch.from_numpy(tg[b:b + 1]).cuda())
         L, _, _, _ = oracle.ssim_loss(fw["img"], tg[b])
         assert abs(float(loss[0]) - L) < 1e-4 * abs(L)
+
+
+# ------------------------------------------------------------------ autotuner
+
+def test_autotune_picks_a_supported_shape_and_leaves_the_scene(eng):
+    from paper_2406_18533_gb300 import autotune
+    sc, cams, _ = synth.workload_c0(seed=3, N=20000)
+    cams = [cams[0], cams[0]]
+    H, W = cams[0].H, cams[0].W
+    targets = torch.rand(2, 3, H, W, generator=torch.Generator().manual_seed(0)).cuda()
+    P = eng.DeviceScene.from_host(sc)
+    before = P.flat().clone()
+    shapes = [(16, 64, 1), (16, 64, 2), (8, 32, 1), (8, 64, 2)]     # the last one is not built
+    best, trials = autotune.tune(P, cams, targets, shapes=shapes, warmup=1, steps=2)
+    assert (best["tile"], best["smem_batch"], best["px_per_thread"]) in shapes[:3]
+    assert [(t.tile, t.smem_batch, t.px_per_thread) for t in trials] == shapes[:3]
+    assert all(t.ms > 0 and t.fragments > 0 for t in trials)
+    assert min(t.ms for t in trials) == [t.ms for t in trials if (t.tile, t.smem_batch, t.px_per_thread)
+                                         == (best["tile"], best["smem_batch"], best["px_per_thread"])][0]
+    assert torch.equal(P.flat(), before)
