@@ -98,7 +98,7 @@ typedef struct gs_hparams {
     int32_t scale_beta_pow_b; /* Eq. 2: beta' = beta^B */
     float lambda_dssim;       /* loss = (1-l) L1 + l (1 - SSIM), l = 0.2 */
     int32_t px_per_thread;    /* pixels a blending thread owns: 1 (a warp blends an 8x4 block),
-                                 2 (8x8) or 4 (8x16); 2 and 4 need tile 16 or 32 */
+                                 2 (8x8) or 4 (8x16, tile 16 or 32) */
     int32_t reserved;
 } gs_hparams;
 
@@ -220,7 +220,7 @@ gs_status gs_bin(gs_ctx *ctx, const gs_proj *proj, const gs_camera *cams, int32_
  * afford cudaMalloc/cudaFree (both synchronise the device), and callers
  * without a gs_ctx (creating one allocates).
  *
- * All scratch lives in one static device array of 19.63 MiB that every GPU on
+ * All scratch lives in one static device array of 20.63 MiB that every GPU on
  * which the library's kernels are loaded holds until the process exits.
  * Limits: B * proj->N <= 262144 (view, Gaussian) pairs and out->capacity <=
  * 1048576 fragments; larger sizes, an unsupported tile (8, 16, 32) or a bad

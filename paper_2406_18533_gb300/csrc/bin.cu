@@ -53,14 +53,31 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t &excl, 
     return total;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t *in, int64_t n, uint32_t *block_sums)
+// Scan input value: the value itself, or 1 for a nonzero value (NZ).
+template <bool NZ>
+__device__ __forceinline__ uint32_t scan_in(uint32_t x)
+{
+    return NZ ? (x != 0u) : x;
+}
+
+// n_dev, when set, caps the count on the device (items past it read as 0 and
+// get no output).
+__device__ __forceinline__ int64_t scan_count(int64_t n, const uint32_t *n_dev)
+{
+    return n_dev && (int64_t)*n_dev < n ? (int64_t)*n_dev : n;
+}
+
+template <bool NZ>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t *in, int64_t n, const uint32_t *n_dev,
+                                                              uint32_t *block_sums)
 {
     __shared__ uint32_t sw[33];
+    n = scan_count(n, n_dev);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k)
-        if (base + k < n) s += in[base + k];
+        if (base + k < n) s += scan_in<NZ>(in[base + k]);
     uint32_t excl;
     const uint32_t tot = block_excl_scan(s, excl, sw);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
@@ -104,16 +121,18 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *block_sums, int6
     if (threadIdx.x == 0 && total) *total = sw[32];
 }
 
+template <bool NZ>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t *in, uint32_t *out, int64_t n,
-                                                            const uint32_t *block_offs)
+                                                            const uint32_t *n_dev, const uint32_t *block_offs)
 {
     __shared__ uint32_t sw[33];
+    n = scan_count(n, n_dev);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t v[SCAN_ITEMS];
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        v[k] = base + k < n ? in[base + k] : 0u;
+        v[k] = base + k < n ? scan_in<NZ>(in[base + k]) : 0u;
         s += v[k];
     }
     uint32_t excl;
@@ -142,7 +161,7 @@ __device__ __forceinline__ uint2 tile_rect(const ViewCam &c, float2 uv, int r, i
     const float y0 = fmaxf(floorf(__fmul_rn(__fsub_rn(uv.y, rf), inv_tile)), 0.f);
     const float y1 = fminf(floorf(__fmul_rn(__fadd_rn(uv.y, rf), inv_tile)), (float)(c.TY - 1));
     if (!(x0 <= x1 && y0 <= y1)) return empty;
-    return make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
+    return pack_rect((uint32_t)x0, (uint32_t)x1, (uint32_t)y0, (uint32_t)y1);
 }
 
 __device__ __forceinline__ uint32_t rect_area(uint2 r)
@@ -151,34 +170,54 @@ __device__ __forceinline__ uint32_t rect_area(uint2 r)
     return (x0 <= x1 && y0 <= y1) ? (x1 - x0 + 1u) * (y1 - y0 + 1u) : 0u;
 }
 
-// Per (view, Gaussian) pair i: its tile rectangle, and the depth key of the
-// pair sort: the float bits of the depth (positive, so they order as unsigned
-// integers); pairs that touch no tile get the largest key and sort last.
-// vals = pair index.  Also writes the pair count for the sort.
-__global__ void __launch_bounds__(256) k_pair_keys(ViewBatch vb, ProjView p, uint32_t *keys, uint32_t *vals,
-                                                   uint2 *rect, uint32_t *count)
+// Float depth -> unsigned integer of the same order (-0 taken as +0).
+__device__ __forceinline__ uint32_t depth_order_bits(float d)
+{
+    const uint32_t b = __float_as_uint(d + 0.f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Per (view, Gaussian) pair i: its tile rectangle and tile count (nonzero =
+// visible: the input of the scan that compacts the visible pairs).  The
+// transformation kernel writes the same two arrays in a training step.
+__global__ void __launch_bounds__(256) k_pair_rect(ViewBatch vb, ProjView p, uint2 *rect, uint32_t *area)
 {
     const int64_t n = (int64_t)vb.B * p.N;
-    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i0 == 0) *count = (uint32_t)n;
-    for (int64_t i = i0; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint2 rc = tile_rect(vb.v[(int)(i / p.N)], p.xy[i], p.radius[i], vb.tile);
         rect[i] = rc;
-        const float depth = reinterpret_cast<const float *>(p.rgb_d)[4 * i + 3];
-        keys[i] = rect_area(rc) > 0u ? __float_as_uint(depth) : 0xffffffffu;
-        vals[i] = (uint32_t)i;
+        area[i] = rect_area(rc);
     }
 }
 
-// The pairs' tile rectangles and tile counts in depth order (the counts are
-// the input of the offsets scan): one random read per pair, after which the
-// emission reads everything in order.
-__global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n,
-                                                       uint32_t *counts, uint32_t *rx, uint32_t *ry)
+// The visible pairs, compacted in index order (so the stable sort keeps equal
+// depths in ascending index): key = depth_order_bits(depth), value = pair
+// index.  Thread 0 writes the visible count.
+__global__ void __launch_bounds__(256) k_pair_compact(int64_t n, const float4 *rgb_d, const uint32_t *area,
+                                                      const uint32_t *pos, const unsigned long long *total,
+                                                      uint32_t *keys, uint32_t *vals, uint32_t *n_vis)
 {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i0 == 0) *n_vis = (uint32_t)*total;
+    for (int64_t i = i0; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!area[i]) continue;
+        const uint32_t j = pos[i];
+        keys[j] = depth_order_bits(reinterpret_cast<const float *>(rgb_d)[4 * i + 3]);
+        vals[j] = (uint32_t)i;
+    }
+}
+
+// The visible pairs' tile rectangles and tile counts in depth order (the
+// counts are the input of the offsets scan): one random read per visible
+// pair, after which the emission reads everything in order.
+__global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n,
+                                                       const uint32_t *n_vis, uint32_t *counts, uint32_t *rx,
+                                                       uint32_t *ry)
+{
+    const int64_t nv = *n_vis;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nv; j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t o = order[j];
-        const uint2 rc = o < n ? rect[o] : make_uint2(1u, 0u);   // o >= n only after a failed (timed-out) pair sort
+        const uint2 rc = o < n ? rect[o] : make_uint2(1u, 0u);   // o >= n only after a failed (timed-out) sort
         counts[j] = rect_area(rc);
         rx[j] = rc.x;
         ry[j] = rc.y;
@@ -195,14 +234,15 @@ __global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, co
 // search over the lanes' offsets, so consecutive lanes store consecutive
 // addresses.  Thread 0 publishes F (status, count_out); nothing is written
 // past capacity.
-__global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, const uint32_t *order,
-                                                   const uint32_t *rx, const uint32_t *ry,
+__global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, const uint32_t *n_vis,
+                                                   const uint32_t *order, const uint32_t *rx, const uint32_t *ry,
                                                    const uint32_t *offsets, uint32_t *keys,
                                                    uint32_t *vals, uint64_t capacity,
                                                    const unsigned long long *total, DevStatus *status,
                                                    uint32_t *count_out)
 {
-    const int64_t n = (int64_t)vb.B * N;
+    const int64_t nb = (int64_t)vb.B * N;
+    const int64_t n = (int64_t)*n_vis < nb ? (int64_t)*n_vis : nb;   // pairs in depth order
     const int lane = threadIdx.x & 31;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t j0 = j - lane;                 // the warp's first pair
@@ -226,8 +266,8 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
         start = offsets[j];
         const int64_t i = (int64_t)order[j];
         const uint2 rc = make_uint2(rx[j], ry[j]);
-        cnt = rect_area(rc);                     // 0 where the pair sort failed (i >= n)
-        if (cnt && i < n) {
+        cnt = rect_area(rc);                     // 0 where the pair sort failed (i >= B * N)
+        if (cnt && i < nb) {
             const int v = (int)(i / N);
             g = (uint32_t)(i - (int64_t)v * N);
             const uint32_t x0 = rc.x & 0xffffu;
@@ -585,7 +625,7 @@ size_t scan_temp_bytes(int64_t n)
 }
 
 void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *total, void *temp,
-                           cudaStream_t st)
+                           cudaStream_t st, const uint32_t *n_dev, bool nonzero)
 {
     if (n <= 0) {
         if (total) cudaMemsetAsync(total, 0, sizeof(unsigned long long), st);
@@ -593,44 +633,67 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigne
     }
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     uint32_t *bs = reinterpret_cast<uint32_t *>(temp);
-    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, bs);
+    if (nonzero)
+        k_scan_reduce<true><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, n_dev, bs);
+    else
+        k_scan_reduce<false><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, n_dev, bs);
     k_scan_blocks<<<1, 1024, 0, st>>>(bs, nb, total);
-    k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, bs);
+    if (nonzero)
+        k_scan_down<true><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, n_dev, bs);
+    else
+        k_scan_down<false><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, n_dev, bs);
     count_launches(3);
 }
 
-void launch_pair_keys(const ViewBatch &vb, const ProjView &p, uint32_t *keys, uint32_t *vals, uint2 *rect,
-                      uint32_t *count, cudaStream_t st)
+template <int RB>
+static void radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
+                       const uint32_t *count, int passes, void *temp, DevStatus *status, cudaStream_t st);
+
+uint32_t *launch_depth_order(const ViewBatch &vb, const ProjView &p, bool rect_ready, uint2 *rect, uint32_t *area,
+                             uint32_t *keys, uint32_t *order, uint32_t *keys_alt, uint32_t *order_alt,
+                             uint32_t *pos, uint32_t *n_vis, unsigned long long *total, void *scan_tmp,
+                             void *sort_tmp, DevStatus *status, cudaStream_t st)
 {
     const int64_t n = (int64_t)vb.B * p.N;
-    k_pair_keys<<<stride_blocks(n > 0 ? (uint64_t)n : 1), 256, 0, st>>>(vb, p, keys, vals, rect, count);
+    if (!rect_ready && n > 0) {
+        k_pair_rect<<<stride_blocks((uint64_t)n), 256, 0, st>>>(vb, p, rect, area);
+        count_launches(1);
+    }
+    launch_exclusive_scan(area, pos, n, total, scan_tmp, st, nullptr, true);
+    k_pair_compact<<<stride_blocks(n > 0 ? (uint64_t)n : 1), 256, 0, st>>>(n, p.rgb_d, area, pos, total, keys, order,
+                                                                          n_vis);
     count_launches(1);
+    radix_sort<8>(keys, order, keys_alt, order_alt, (uint64_t)n, n_vis, 4, sort_tmp, status, st);
+    return order;                                 // four passes: back in the first buffers
 }
 
-void launch_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n, uint32_t *counts, uint32_t *rx,
-                          uint32_t *ry, cudaStream_t st)
+void launch_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n, const uint32_t *n_vis,
+                          uint32_t *counts, uint32_t *rx, uint32_t *ry, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_gather_counts<<<stride_blocks((uint64_t)n), 256, 0, st>>>(order, rect, n, counts, rx, ry);
+    k_gather_counts<<<stride_blocks((uint64_t)n), 256, 0, st>>>(order, rect, n, n_vis, counts, rx, ry);
     count_launches(1);
 }
 
-void launch_emit_keys(const ViewBatch &vb, int64_t N, const uint32_t *order, const uint32_t *rx, const uint32_t *ry,
-                      const uint32_t *offsets, uint32_t *keys, uint32_t *vals, uint64_t capacity,
-                      const unsigned long long *total, DevStatus *status, uint32_t *count_out, cudaStream_t st)
+void launch_emit_keys(const ViewBatch &vb, int64_t N, const uint32_t *n_vis, const uint32_t *order,
+                      const uint32_t *rx, const uint32_t *ry, const uint32_t *offsets, uint32_t *keys, uint32_t *vals,
+                      uint64_t capacity, const unsigned long long *total, DevStatus *status, uint32_t *count_out,
+                      cudaStream_t st)
 {
     const int64_t n = (int64_t)vb.B * N;
     const int64_t blocks = n > 0 ? (n + 255) / 256 : 1;
-    k_emit_keys<<<(unsigned)blocks, 256, 0, st>>>(vb, N, order, rx, ry, offsets, keys, vals, capacity, total, status,
-                                                 count_out);
+    k_emit_keys<<<(unsigned)blocks, 256, 0, st>>>(vb, N, n_vis, order, rx, ry, offsets, keys, vals, capacity, total,
+                                                 status, count_out);
     count_launches(1);
 }
 
-size_t sort_temp_bytes(uint64_t capacity)
+size_t sort_temp_bytes(uint64_t pairs, uint64_t fragments)
 {
-    const uint64_t tiles = capacity > 0 ? (capacity + RS_TILE - 1) / RS_TILE : 1;
-    // digit offsets (passes x NB), tile counters, look-back words (tiles x NB)
-    return (size_t)RS_MAX_PASSES * RS_MAX_NB * 4 + 256 + (size_t)tiles * RS_MAX_NB * 4 + 256;
+    // digit offsets (passes x NB), tile counters, look-back words (tiles x NB):
+    // 256 digits for the pair sort, at most 512 for the fragment sort
+    const uint64_t tp = (pairs + RS_TILE - 1) / RS_TILE, tf = (fragments + RS_TILE - 1) / RS_TILE;
+    const uint64_t look = tp * 256 > tf * 512 ? tp * 256 : tf * 512;
+    return (size_t)RS_MAX_PASSES * RS_MAX_NB * 4 + 256 + (size_t)(look ? look : 1) * 4 + 256;
 }
 
 template <int RB>
@@ -662,12 +725,6 @@ static void radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint3
         uint32_t *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
     }
-}
-
-void launch_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
-                       const uint32_t *count, void *temp, DevStatus *status, cudaStream_t st)
-{
-    radix_sort<8>(keys, vals, keys_alt, vals_alt, capacity, count, 4, temp, status, st);
 }
 
 // Digit width and pass count for tile ids of `tile_bits` bits: 9-bit digits

@@ -21,7 +21,8 @@ constexpr uint64_t NA_MAX_FRAGS = (uint64_t)1 << 20;  // fragment capacity of th
 // Byte layout of the scratch array (each region 256-byte aligned).
 constexpr size_t OFF_OFFSETS = 0;                                      // uint32[pairs] fragment offsets
 constexpr size_t OFF_RECT = OFF_OFFSETS + 4 * (size_t)NA_MAX_PAIRS;    // uint2[pairs] tile rectangles
-constexpr size_t OFF_SCAN = OFF_RECT + 8 * (size_t)NA_MAX_PAIRS;       // scan temp, 4 KiB
+constexpr size_t OFF_AREA = OFF_RECT + 8 * (size_t)NA_MAX_PAIRS;       // uint32[pairs] tile counts
+constexpr size_t OFF_SCAN = OFF_AREA + 4 * (size_t)NA_MAX_PAIRS;       // scan temp, 4 KiB
 constexpr size_t OFF_TOTAL = OFF_SCAN + 4096;                          // uint64 total, uint32 pair count
 constexpr size_t OFF_STATUS = OFF_TOTAL + 256;                         // DevStatus
 constexpr size_t OFF_TK = OFF_STATUS + 256;                            // uint32[frags] tile ids
@@ -32,7 +33,7 @@ constexpr size_t OFF_PV = OFF_PK + 4 * (size_t)NA_MAX_PAIRS;           // uint32
 constexpr size_t OFF_PK_ALT = OFF_PV + 4 * (size_t)NA_MAX_PAIRS;       // uint32[pairs]
 constexpr size_t OFF_PV_ALT = OFF_PK_ALT + 4 * (size_t)NA_MAX_PAIRS;   // uint32[pairs]
 constexpr size_t OFF_SORT = OFF_PV_ALT + 4 * (size_t)NA_MAX_PAIRS;     // sort temp, 640 KiB
-constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_SORT + 640 * 1024;        // 19.63 MiB
+constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_SORT + 640 * 1024;        // 20.63 MiB
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -85,8 +86,7 @@ extern "C" gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, 
     const int64_t n = (int64_t)B * proj->N;
     if (n > NA_MAX_PAIRS || out->capacity > NA_MAX_FRAGS) return GS_ERR_INVALID_ARG;   // beyond the fixed scratch
     if (n > 0 && (!proj->xy || !proj->radius || !proj->rgb_d)) return GS_ERR_INVALID_ARG;
-    if (scan_temp_bytes(n) > OFF_TOTAL - OFF_SCAN ||
-        sort_temp_bytes((uint64_t)n > out->capacity ? (uint64_t)n : out->capacity) > NOALLOC_SCRATCH_BYTES - OFF_SORT)
+    if (scan_temp_bytes(n) > OFF_TOTAL - OFF_SCAN || sort_temp_bytes((uint64_t)n, out->capacity) > NOALLOC_SCRATCH_BYTES - OFF_SORT)
         return GS_ERR_INVALID_ARG;
     // view batch (host-side validation of the cameras as in gs_bin)
     ViewBatch vb;
@@ -114,8 +114,9 @@ extern "C" gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     auto *offsets = reinterpret_cast<uint32_t *>(s + OFF_OFFSETS);
     auto *rect = reinterpret_cast<uint2 *>(s + OFF_RECT);
+    auto *area = reinterpret_cast<uint32_t *>(s + OFF_AREA);
     auto *total = reinterpret_cast<unsigned long long *>(s + OFF_TOTAL);
-    auto *pair_count = reinterpret_cast<uint32_t *>(s + OFF_TOTAL + 8);
+    auto *n_vis = reinterpret_cast<uint32_t *>(s + OFF_TOTAL + 8);
     auto *status = reinterpret_cast<DevStatus *>(s + OFF_STATUS);
     auto *tk = reinterpret_cast<uint32_t *>(s + OFF_TK);
     auto *tk_alt = reinterpret_cast<uint32_t *>(s + OFF_TK_ALT);
@@ -132,11 +133,14 @@ extern "C" gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, 
                       reinterpret_cast<float4 *>(proj->rgb_d), proj->radius, proj->N};
     const int high = bits_for(vb.total_tiles);
     const bool even = fragment_sort_passes(high) % 2 == 0;
-    launch_pair_keys(vb, pv, pk, pv_order, rect, pair_count, st);
-    launch_sort_pairs(pk, pv_order, pk_alt, pv_alt, (uint64_t)n, pair_count, sort_tmp, status, st);
-    launch_gather_counts(pv_order, rect, n, pv_alt, pk, pk_alt, st);   // depth keys dead: rectangles there
-    launch_exclusive_scan(pv_alt, offsets, n, total, s + OFF_SCAN, st);
-    launch_emit_keys(vb, pv.N, pv_order, pk, pk_alt, offsets, even ? tk : tk_alt, even ? out->vals : vals_alt,
+    uint32_t *order = launch_depth_order(vb, pv, false, rect, area, pk, pv_order, pk_alt, pv_alt, offsets, n_vis,
+                                         total, s + OFF_SCAN, sort_tmp, status, st);
+    // the sort's dead buffers take the counts and rectangles in depth order
+    uint32_t *counts = order == pv_order ? pk : pv_order;
+    uint32_t *rx = order == pv_order ? pv_alt : pk, *ry = pk_alt;
+    launch_gather_counts(order, rect, n, n_vis, counts, rx, ry, st);
+    launch_exclusive_scan(counts, offsets, n, total, s + OFF_SCAN, st, n_vis);
+    launch_emit_keys(vb, pv.N, n_vis, order, rx, ry, offsets, even ? tk : tk_alt, even ? out->vals : vals_alt,
                      out->capacity, total, status, out->count, st);
     launch_sort_fragments(even ? tk : tk_alt, even ? out->vals : vals_alt, even ? tk_alt : tk,
                           even ? vals_alt : out->vals, out->capacity, out->count, high, sort_tmp, status, st);

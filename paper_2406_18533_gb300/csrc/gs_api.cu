@@ -203,43 +203,46 @@ void trace_free(gs_ctx *c)
 }
 
 // Bins the fragments of `p` into (vals, ranges, count) in depth order; the
-// fragments' tile ids stay in c->keys.  With keys64 non-null it also writes
-// the public 64-bit keys (tile id << 32 | depth bits).
-gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, uint64_t *keys64, uint32_t *vals,
-                      uint2 *ranges, uint32_t *count, uint64_t capacity, cudaStream_t st)
+// fragments' tile ids stay in c->keys.  rect_ready: c->rect and c->ntiles
+// already hold the pairs' tile rectangles and counts (the transformation
+// kernel wrote them).  With keys64 non-null it also writes the public 64-bit
+// keys (tile id << 32 | depth bits).
+gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, bool rect_ready, uint64_t *keys64,
+                      uint32_t *vals, uint2 *ranges, uint32_t *count, uint64_t capacity, cudaStream_t st)
 {
     const int64_t n = (int64_t)vb.B * p.N;
     if ((uint64_t)n > GS_MAX_FRAGMENTS) return fail(c, GS_ERR_INVALID_ARG, "B*N above 2^30-1 (view, Gaussian) pairs");
     const size_t n1 = (size_t)(n > 0 ? n : 1);
     const uint64_t cap1 = capacity ? capacity : 1;
-    const uint64_t sort_cap = (uint64_t)n > capacity ? (uint64_t)n : capacity;
     gs_status r;
     if ((r = ensure(c, c->offsets, 4 * n1)) || (r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) ||
+        (r = ensure(c, c->ntiles, 4 * n1)) ||
         (r = ensure(c, c->total, 64)) || (r = ensure(c, c->pk, 4 * n1)) || (r = ensure(c, c->pv, 4 * n1)) ||
         (r = ensure(c, c->pk_alt, 4 * n1)) || (r = ensure(c, c->pv_alt, 4 * n1)) || (r = ensure(c, c->rect, 8 * n1)) ||
         (r = ensure(c, c->keys, 4 * (size_t)cap1)) || (r = ensure(c, c->keys_alt, 4 * (size_t)cap1)) ||
-        (r = ensure(c, c->vals_alt, 4 * (size_t)cap1)) || (r = ensure(c, c->sort_tmp, sort_temp_bytes(sort_cap))))
+        (r = ensure(c, c->vals_alt, 4 * (size_t)cap1)) || (r = ensure(c, c->sort_tmp, sort_temp_bytes((uint64_t)n, capacity))))
         return r;
     const int high = bits_for(vb.total_tiles);
     const bool even = fragment_sort_passes(high) % 2 == 0;
     auto *total = ptr<unsigned long long>(c->total);
-    uint32_t *pair_count = reinterpret_cast<uint32_t *>(ptr<char>(c->total) + 8);
-    uint32_t *pk = ptr<uint32_t>(c->pk), *pv = ptr<uint32_t>(c->pv);
+    uint32_t *n_vis = reinterpret_cast<uint32_t *>(ptr<char>(c->total) + 8);
+    uint32_t *pk = ptr<uint32_t>(c->pk), *pv = ptr<uint32_t>(c->pv), *pk_alt = ptr<uint32_t>(c->pk_alt);
     uint2 *rect = ptr<uint2>(c->rect);
     uint32_t *tk = ptr<uint32_t>(c->keys), *tk_alt = ptr<uint32_t>(c->keys_alt), *v_alt = ptr<uint32_t>(c->vals_alt);
-    // (1) the (view, Gaussian) pairs in depth order (4 passes: the result returns to pk / pv)
-    launch_pair_keys(vb, p, pk, pv, rect, pair_count, st);
-    launch_sort_pairs(pk, pv, ptr<uint32_t>(c->pk_alt), ptr<uint32_t>(c->pv_alt), (uint64_t)n, pair_count,
-                      c->sort_tmp.p, c->status, st);
-    // (2) their rectangles and tile counts in that order (the depth keys are
-    // dead: their buffers take the rectangles), counts scanned into offsets
-    uint32_t *rx = pk, *ry = ptr<uint32_t>(c->pk_alt), *counts = ptr<uint32_t>(c->pv_alt);
-    launch_gather_counts(pv, rect, n, counts, rx, ry, st);
-    launch_exclusive_scan(counts, ptr<uint32_t>(c->offsets), n, total, c->scan_tmp.p, st);
+    // (1) the visible (view, Gaussian) pairs in depth order
+    uint32_t *order = launch_depth_order(vb, p, rect_ready, rect, ptr<uint32_t>(c->ntiles), pk, pv, pk_alt,
+                                         ptr<uint32_t>(c->pv_alt), ptr<uint32_t>(c->offsets), n_vis, total,
+                                         c->scan_tmp.p, c->sort_tmp.p, c->status, st);
+    // (2) their rectangles and tile counts in that order (in the sort's dead
+    // buffers), counts scanned into fragment offsets
+    uint32_t *counts = order == pv ? pk : pv;
+    uint32_t *rx = order == pv ? ptr<uint32_t>(c->pv_alt) : pk, *ry = pk_alt;
+    launch_gather_counts(order, rect, n, n_vis, counts, rx, ry, st);
+    launch_exclusive_scan(counts, ptr<uint32_t>(c->offsets), n, total, c->scan_tmp.p, st, n_vis);
     mark(c, st, 2);
     // (3) fragments pair by pair in depth order, into the buffers the tile sort ends in
-    launch_emit_keys(vb, p.N, pv, rx, ry, ptr<uint32_t>(c->offsets), even ? tk : tk_alt, even ? vals : v_alt,
-                     capacity, total, c->status, count, st);
+    launch_emit_keys(vb, p.N, n_vis, order, rx, ry, ptr<uint32_t>(c->offsets), even ? tk : tk_alt,
+                     even ? vals : v_alt, capacity, total, c->status, count, st);
     mark(c, st, 3);
     // (4) stable sort on the tile id
     launch_sort_fragments(even ? tk : tk_alt, even ? vals : v_alt, even ? tk_alt : tk, even ? v_alt : vals, capacity,
@@ -264,7 +267,7 @@ gs_status ensure_iter(gs_ctx *c, int64_t N, const ViewBatch &vb, uint64_t cap)
         (r = ensure(c, c->pv_alt, 4 * n)) || (r = ensure(c, c->rect, 8 * n)) ||
         (r = ensure(c, c->scan_tmp, scan_temp_bytes((int64_t)n))) || (r = ensure(c, c->total, 64)) ||
         (r = ensure(c, c->keys_alt, 4 * (size_t)(cap ? cap : 1))) || (r = ensure(c, c->vals_alt, 4 * (size_t)(cap ? cap : 1))) ||
-        (r = ensure(c, c->sort_tmp, sort_temp_bytes((uint64_t)n > cap ? (uint64_t)n : cap))))
+        (r = ensure(c, c->sort_tmp, sort_temp_bytes((uint64_t)n, cap))))
         return r;
     if ((r = ensure(c, c->keys, 4 * (size_t)(cap ? cap : 1))) || (r = ensure(c, c->vals, 4 * (size_t)(cap ? cap : 1))) ||
         (r = ensure(c, c->ranges, 8 * (size_t)vb.total_tiles)) || (r = ensure(c, c->count, 64)))
@@ -332,7 +335,7 @@ gs_status check_hparams(gs_ctx *c, const gs_hparams *hp)
     if (!blend_config_ok(hp->tile, hp->smem_batch, hp->px_per_thread))
         return fail(c, GS_ERR_INVALID_ARG,
                     "unsupported (tile, smem_batch, px_per_thread): smem_batch 32, 64 or 128 (32 or 64 with tile 32 "
-                    "and one pixel per thread); two or four pixels per thread need tile 16 or 32");
+                    "and one pixel per thread); four pixels per thread need tile 16 or 32");
     if (!(hp->alpha_max > 0.f && hp->alpha_max < 1.f) || !(hp->alpha_min >= 0.f) || !(hp->T_min >= 0.f))
         return fail(c, GS_ERR_INVALID_ARG, "blend thresholds out of range");
     return GS_OK;
@@ -518,7 +521,7 @@ gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *ca
     }
     const size_t n = (size_t)B * (size_t)N;
     size_t s = n * (8 + 16 + 16 + 4 + 4 + 4 + 16 + 8 + 48) + frag_capacity * (8 * 2) +
-               sort_temp_bytes((uint64_t)n > frag_capacity ? (uint64_t)n : frag_capacity) +
+               sort_temp_bytes((uint64_t)n, frag_capacity) +
                scan_temp_bytes((int64_t)n) + tiles * 8 + pix * (4 + 4 + 12 + 12 + 36) + 4096;
     *bytes = s;
     return GS_OK;
@@ -537,7 +540,7 @@ gs_status gs_preprocess(gs_ctx *c, const gs_scene *scene, const gs_camera *cams,
     if (r != GS_OK) return r;
     const int64_t n = (int64_t)B * scene->N;
     if ((r = ensure(c, c->ntiles, 4 * (size_t)(n > 0 ? n : 1))) != GS_OK) return r;
-    launch_preprocess_fwd(view_of(scene), vb, proj_of(out), ptr<uint32_t>(c->ntiles), c->status,
+    launch_preprocess_fwd(view_of(scene), vb, proj_of(out), ptr<uint32_t>(c->ntiles), nullptr, c->status,
                           c->hp.strict_nonfinite, S(stream));
     return cuda_check(c, "gs_preprocess");
 }
@@ -554,7 +557,7 @@ gs_status gs_bin(gs_ctx *c, const gs_proj *proj, const gs_camera *cams, int32_t 
     gs_status r = make_views(c, cams, B, vb, false);
     if (r != GS_OK) return r;
     cudaStream_t st = S(stream);
-    r = run_binning(c, vb, proj_of(proj), out->keys, out->vals, reinterpret_cast<uint2 *>(out->ranges),
+    r = run_binning(c, vb, proj_of(proj), false, out->keys, out->vals, reinterpret_cast<uint2 *>(out->ranges),
                     out->count, out->capacity, st);
     if (r != GS_OK) return r;
     if (needed_host) {
@@ -672,7 +675,8 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     const SceneView sv = view_of(p);
     c->trace_on = c->trace_max > 0 && c->trace_step < c->trace_max;
     mark(c, st, 0);
-    launch_preprocess_fwd(sv, vb, pv, ptr<uint32_t>(c->ntiles), c->status, c->hp.strict_nonfinite, st);
+    launch_preprocess_fwd(sv, vb, pv, ptr<uint32_t>(c->ntiles), ptr<uint2>(c->rect), c->status,
+                          c->hp.strict_nonfinite, st);
     mark(c, st, 1);
     if (c->frag_cap == 0) {
         // first call on this context: size the fragment buffers from an exact count
@@ -686,7 +690,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
         c->frag_cap = cap;
         if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
     }
-    r = run_binning(c, vb, pv, nullptr, ptr<uint32_t>(c->vals),
+    r = run_binning(c, vb, pv, true, nullptr, ptr<uint32_t>(c->vals),
                     ptr<uint2>(c->ranges), ptr<uint32_t>(c->count), c->frag_cap, st);
     if (r != GS_OK) return r;
     set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
@@ -730,7 +734,8 @@ gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int
     if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
     gs_proj pr{ptr<float>(c->xy), ptr<float>(c->conic_o), ptr<float>(c->rgb_d), ptr<int32_t>(c->radius), N, B, 0};
     const ProjView pv = proj_of(&pr);
-    launch_preprocess_fwd(view_of(scene), vb, pv, ptr<uint32_t>(c->ntiles), c->status, c->hp.strict_nonfinite, st);
+    launch_preprocess_fwd(view_of(scene), vb, pv, ptr<uint32_t>(c->ntiles), ptr<uint2>(c->rect), c->status,
+                          c->hp.strict_nonfinite, st);
     if (c->frag_cap == 0) {
         if ((r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) || (r = ensure(c, c->total, 64))) return r;
         launch_exclusive_scan(ptr<uint32_t>(c->ntiles), ptr<uint32_t>(c->offsets), n,
@@ -742,7 +747,7 @@ gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int
         c->frag_cap = cap;
         if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
     }
-    r = run_binning(c, vb, pv, nullptr, ptr<uint32_t>(c->vals),
+    r = run_binning(c, vb, pv, true, nullptr, ptr<uint32_t>(c->vals),
                     ptr<uint2>(c->ranges), ptr<uint32_t>(c->count), c->frag_cap, st);
     if (r != GS_OK) return r;
     size_t off = 0;

@@ -80,37 +80,60 @@ struct DevStatus {
 void count_launches(int n);
 
 // Launchers (all asynchronous on `st`).
+// ntiles[i]: tiles covered by pair i; rect[i] (optional): its packed tile
+// rectangle (pack_rect, the same arithmetic as the binning's).
 void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, uint32_t *ntiles,
-                           DevStatus *status, int strict, cudaStream_t st);
+                           uint2 *rect, DevStatus *status, int strict, cudaStream_t st);
 void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
                            const SceneMut &out, cudaStream_t st);
 
 // Exclusive scan of n uint32 values (n < 2^31); total (uint64) to *total.
+// n_dev (optional): a device count that caps n (items past it are neither
+// read nor written); nonzero: scan (value != 0) instead of the value.
 size_t scan_temp_bytes(int64_t n);
 void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *total, void *temp,
-                           cudaStream_t st);
+                           cudaStream_t st, const uint32_t *n_dev = nullptr, bool nonzero = false);
 
-// Binning in depth order: (1) per (view, Gaussian) pair its tile rectangle
-// and a depth key (float bits of the depth; pairs on no tile last), sorted
-// stably (4 passes of 8-bit digits); (2) tile counts gathered in that order
-// and scanned; (3) fragments emitted pair by pair in that order, key = global
-// tile id, value = Gaussian index; (4) a stable sort on the tile id.  Within a
-// tile the fragments then follow (depth, Gaussian index).
-void launch_pair_keys(const ViewBatch &vb, const ProjView &p, uint32_t *keys, uint32_t *vals, uint2 *rect,
-                      uint32_t *count, cudaStream_t st);
-// counts / rx / ry: tile count and the two rectangle words of pair order[j]
-void launch_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n, uint32_t *counts, uint32_t *rx,
-                          uint32_t *ry, cudaStream_t st);
-void launch_emit_keys(const ViewBatch &vb, int64_t N, const uint32_t *order, const uint32_t *rx, const uint32_t *ry,
-                      const uint32_t *offsets, uint32_t *keys, uint32_t *vals, uint64_t capacity,
-                      const unsigned long long *total, DevStatus *status, uint32_t *count_out, cudaStream_t st);
+// A footprint's tile rectangle packed as {x0 | x1 << 16, y0 | y1 << 16}
+// (tile coordinates fit 16 bits); (1, 0) is the empty rectangle.
+__host__ __device__ __forceinline__ uint2 pack_rect(uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1)
+{
+    return make_uint2(x0 | (x1 << 16), y0 | (y1 << 16));
+}
 
-size_t sort_temp_bytes(uint64_t capacity);
-// Stable LSD radix sorts of 32-bit keys (one-sweep passes).  The result lands
-// in keys/vals when the number of passes is even, else in the alt buffers.  A
-// look-back wait that exceeds its spin limit sets GS_ERR_TIMEOUT in *status.
-void launch_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t capacity,
-                       const uint32_t *count, void *temp, DevStatus *status, cudaStream_t st);
+// Binning in depth order: (1) per (view, Gaussian) pair its tile rectangle;
+// the visible pairs (those covering a tile) compacted in index order and
+// sorted stably by depth (three passes of 10-bit digits); (2) tile counts
+// gathered in that order and scanned; (3) fragments emitted pair by pair in
+// that order, key = global tile id, value = Gaussian index; (4) a stable sort
+// on the tile id.  Within a tile the fragments then follow (depth, Gaussian
+// index).
+//
+// launch_depth_order: rect[i] and area[i] (tile count) for every pair, from
+// gs_proj unless rect_ready (the transformation kernel wrote them); returns
+// the buffer whose first *n_vis entries are the visible pair indices in depth
+// order (keys, keys_alt, order_alt and pos are scratch of n entries each;
+// *total also receives the visible count).
+uint32_t *launch_depth_order(const ViewBatch &vb, const ProjView &p, bool rect_ready, uint2 *rect, uint32_t *area,
+                             uint32_t *keys, uint32_t *order, uint32_t *keys_alt, uint32_t *order_alt,
+                             uint32_t *pos, uint32_t *n_vis, unsigned long long *total, void *scan_tmp,
+                             void *sort_tmp, DevStatus *status, cudaStream_t st);
+// counts / rx / ry: tile count and the two rectangle words of pair order[j],
+// j < *n_vis
+void launch_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n, const uint32_t *n_vis,
+                          uint32_t *counts, uint32_t *rx, uint32_t *ry, cudaStream_t st);
+void launch_emit_keys(const ViewBatch &vb, int64_t N, const uint32_t *n_vis, const uint32_t *order,
+                      const uint32_t *rx, const uint32_t *ry, const uint32_t *offsets, uint32_t *keys, uint32_t *vals,
+                      uint64_t capacity, const unsigned long long *total, DevStatus *status, uint32_t *count_out,
+                      cudaStream_t st);
+
+// Sort scratch for the pair sort of `pairs` keys and the fragment sort of
+// `fragments` keys (one buffer serves both, one after the other).
+size_t sort_temp_bytes(uint64_t pairs, uint64_t fragments);
+// Stable LSD radix sort of 32-bit tile ids (one-sweep passes).  The result
+// lands in keys/vals when the number of passes is even, else in the alt
+// buffers.  A look-back wait that exceeds its spin limit sets GS_ERR_TIMEOUT
+// in *status.
 int fragment_sort_passes(int tile_bits);
 void launch_sort_fragments(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                            uint64_t capacity, const uint32_t *count, int tile_bits, void *temp, DevStatus *status,

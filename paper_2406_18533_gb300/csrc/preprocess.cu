@@ -129,7 +129,7 @@ __device__ __forceinline__ Geom load_geom(const SceneView &s, int64_t g)
 }
 
 __global__ void __launch_bounds__(128) k_preprocess_fwd(SceneView s, ViewBatch vb, ProjView p, uint32_t *ntiles,
-                                                        DevStatus *status, int strict)
+                                                        uint2 *rect, DevStatus *status, int strict)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= s.N) return;
@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(128) k_preprocess_fwd(SceneView s, ViewBatch v
         const float pz = __double2float_rn(zd);
         uint32_t area = 0;
         int r_int = 0;
+        uint2 rc = pack_rect(1u, 0u, 0u, 0u);     // empty
         if (G.ok && zd > (double)c.near_z) {
             const float iz = 1.f / pz;
             const float u = c.fx * px * iz + c.cx;
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(128) k_preprocess_fwd(SceneView s, ViewBatch v
                 y1 = fminf(y1, (float)(c.TY - 1));
                 if (x0 <= x1 && y0 <= y1) {
                     area = (uint32_t)((int)(x1 - x0) + 1) * (uint32_t)((int)(y1 - y0) + 1);
+                    rc = pack_rect((uint32_t)x0, (uint32_t)x1, (uint32_t)y0, (uint32_t)y1);
                     r_int = (int)rf;
                     if (!sh_loaded) {
 #pragma unroll
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(128) k_preprocess_fwd(SceneView s, ViewBatch v
         }
         p.radius[idx] = r_int;
         ntiles[idx] = area;
+        if (rect) rect[idx] = rc;
     }
 }
 
@@ -415,12 +418,12 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(SceneView s, ViewBatch v
 }  // namespace
 
 void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, uint32_t *ntiles,
-                           DevStatus *status, int strict, cudaStream_t st)
+                           uint2 *rect, DevStatus *status, int strict, cudaStream_t st)
 {
     if (s.N == 0) return;
     const int threads = 128;
     const int64_t blocks = (s.N + threads - 1) / threads;
-    k_preprocess_fwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, ntiles, status, strict);
+    k_preprocess_fwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, ntiles, rect, status, strict);
     count_launches(1);
 }
 

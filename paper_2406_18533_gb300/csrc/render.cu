@@ -19,8 +19,8 @@
 // Backward: each warp walks back to front from its own largest n_contrib,
 // recovers the transmittance before each contributor by division from
 // T_final (no per-fragment state is stored), reduces a Gaussian's nine
-// gradient components over the warp with a reduce-scatter (14 shuffles) and
-// adds them as three float4 atomics from three lanes per (warp, Gaussian).
+// gradient components over the warp with a reduce-scatter (17 shuffles) and
+// adds them as three float4 atomics per (warp, Gaussian).
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -114,11 +114,13 @@ __device__ __forceinline__ int find_view(const ViewBatch &vb, uint32_t tile_id)
     return v;
 }
 
-// Sums 8 per-lane values over the warp with a reduce-scatter: at each level
-// a lane keeps half of its values and ships the other half, so the 8 sums
-// take 4 + 2 + 1 + 1 + 1 = 9 shuffles.  On return the lanes with lane % 4 == 0
-// hold the total of value ((lane >> 2) & 7).
-__device__ __forceinline__ float warp_reduce_scatter8(const float v[8], int lane)
+// Warp-wide sums of one entry's nine gradient values v[0..8], added to entry
+// idx.  v[0..7] go through a reduce-scatter (at each level a lane keeps half
+// of its values and ships the other half: 4 + 2 + 1 + 1 + 1 = 9 shuffles,
+// after which value k is in lanes 4k .. 4k+3), v[8] through a butterfly (5);
+// lanes 0..2 gather (3 shuffles) and add (u, v, opacity), conic and rgb as
+// one float4 atomic each.
+__device__ __forceinline__ void flush_one(const GradView &gv, int64_t idx, const float v[9], int lane)
 {
     float w[4], x[2];
     const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
@@ -134,11 +136,20 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float v[8], int lane
         const float keep = b3 ? w[j + 2] : w[j];
         x[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
-    const float send = b2 ? x[0] : x[1];
-    float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
     y += __shfl_xor_sync(0xffffffffu, y, 2);
     y += __shfl_xor_sync(0xffffffffu, y, 1);
-    return y;
+    float t = v[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    const int src = 12 * (lane < 3 ? lane : 0);
+    const float g0 = __shfl_sync(0xffffffffu, y, src);
+    const float g1 = __shfl_sync(0xffffffffu, y, src + 4);
+    const float g2 = __shfl_sync(0xffffffffu, y, (src + 8) & 31);
+    if (lane < 3) {
+        float4 *dst = lane == 0 ? &gv.d_xy_o[idx] : lane == 1 ? &gv.d_conic[idx] : &gv.d_rgb[idx];
+        atomicAdd(dst, make_float4(g0, g1, lane == 2 ? t : g2, 0.f));
+    }
 }
 
 // Tile-local geometry of this thread's PPT pixels (one column, rows 4 apart)
@@ -463,19 +474,8 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
                 }
                 continue;
             }
-            const float y = warp_reduce_scatter8(vv, lane);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) gbl += __shfl_xor_sync(0xffffffffu, gbl, o);
-            // value k lives in lanes 4k .. 4k+3: lane L < 3 gathers values 3L .. 3L+2
-            // and adds them as one float4 (lane 2 takes the ninth value, gbl)
-            const int src = 12 * (lane < 3 ? lane : 0);
-            const float a0 = __shfl_sync(0xffffffffu, y, src);
-            const float a1 = __shfl_sync(0xffffffffu, y, src + 4);
-            const float a2 = __shfl_sync(0xffffffffu, y, (src + 8) & 31);
-            if (lane < 3) {
-                float4 *dst = lane == 0 ? &gv.d_xy_o[idx] : lane == 1 ? &gv.d_conic[idx] : &gv.d_rgb[idx];
-                atomicAdd(dst, make_float4(a0, a1, lane == 2 ? gbl : a2, 0.f));
-            }
+            const float cur[9] = {vv[0], vv[1], vv[2], vv[3], vv[4], vv[5], vv[6], vv[7], gbl};
+            flush_one(gv, idx, cur, lane);
         }
         n = 0;
         __syncwarp();
@@ -530,19 +530,20 @@ void bwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, co
 // Built (tile, entries per warp refill, pixels per thread) combinations.
 // One pixel per thread (warp = 8 x 4 pixels): tile 8 or 16 with 32, 64 or
 // 128 entries; tile 32 with 32 or 64 (its 32 warps' slices must fit in shared
-// memory).  Two (warp = 8 x 8) or four (8 x 16): tile 16 or 32 with 32, 64
-// or 128.
+// memory).  Two (warp = 8 x 8): any tile with 32, 64 or 128.  Four (8 x 16):
+// tile 16 or 32 with 32, 64 or 128.
 bool blend_config_ok(int tile, int chunk, int ppt)
 {
     if (chunk != 32 && chunk != 64 && chunk != 128) return false;
     if (ppt == 1) return tile == 8 || tile == 16 || (tile == 32 && chunk <= 64);
-    if (ppt == 2 || ppt == 4) return tile == 16 || tile == 32;
+    if (ppt == 2) return true;
+    if (ppt == 4) return tile == 16 || tile == 32;
     return false;
 }
 
 #define GS_BLEND_CASES(X)                                                                                      \
     X(8, 32, 1) X(8, 64, 1) X(8, 128, 1) X(16, 32, 1) X(16, 64, 1) X(16, 128, 1) X(32, 32, 1) X(32, 64, 1)   \
-    X(16, 32, 2) X(16, 64, 2) X(16, 128, 2) X(32, 32, 2) X(32, 64, 2) X(32, 128, 2) X(16, 32, 4) X(16, 64, 4)   \
+    X(8, 32, 2) X(8, 64, 2) X(8, 128, 2) X(16, 32, 2) X(16, 64, 2) X(16, 128, 2) X(32, 32, 2) X(32, 64, 2) X(32, 128, 2) X(16, 32, 4) X(16, 64, 4)   \
     X(16, 128, 4) X(32, 32, 4) X(32, 64, 4) X(32, 128, 4)
 
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,

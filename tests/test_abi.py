@@ -80,7 +80,7 @@ def test_invalid_arguments_rejected_on_host(libgs):
     assert libgs.gs_create(ctypes.byref(h), ctypes.byref(hp)) == b.GS_ERR_INVALID_ARG
     hp = b.default_hparams(tile=32, smem_batch=128)
     assert libgs.gs_create(ctypes.byref(h), ctypes.byref(hp)) == b.GS_ERR_INVALID_ARG
-    for ppt, tile in ((0, 16), (3, 16), (2, 8), (4, 8)):   # 1, 2 or 4 pixels per thread; 2 and 4 need tile >= 16
+    for ppt, tile in ((0, 16), (3, 16), (4, 8)):   # 1, 2 or 4 pixels per thread; 4 needs tile >= 16
         hp = b.default_hparams(px_per_thread=ppt, tile=tile)
         assert libgs.gs_create(ctypes.byref(h), ctypes.byref(hp)) == b.GS_ERR_INVALID_ARG
     assert libgs.gs_create(None, None) == b.GS_ERR_INVALID_ARG

@@ -116,7 +116,7 @@ def _stage_case(eng, oracle, seed, W, H, n, tile, batch, ppt=1):
 
 @pytest.mark.parametrize("tile,batch,ppt", [(16, 64, 1), (8, 32, 1), (32, 64, 1), (16, 128, 1), (8, 128, 1),
                                             (32, 32, 1), (16, 64, 2), (16, 32, 2), (32, 128, 2), (32, 32, 2),
-                                            (16, 64, 4), (32, 32, 4)])
+                                            (16, 64, 4), (32, 32, 4), (8, 64, 2)])
 def test_render_fwd_stage(eng, oracle, tile, batch, ppt):
     W, H = 150, 90
     _, _, _, _, _, (img, T, nc), _, ref = _stage_case(eng, oracle, 5, W, H, 4000, tile, batch, ppt)
@@ -130,7 +130,7 @@ def test_render_fwd_stage(eng, oracle, tile, batch, ppt):
 
 
 @pytest.mark.parametrize("tile,batch,ppt", [(16, 64, 1), (8, 128, 1), (32, 32, 1), (16, 32, 1), (16, 64, 2),
-                                            (32, 64, 2), (16, 128, 2), (16, 64, 4), (32, 128, 4)])
+                                            (32, 64, 2), (16, 128, 2), (16, 64, 4), (32, 128, 4), (8, 32, 2)])
 def test_render_bwd_stage(eng, oracle, tile, batch, ppt):
     W, H = 120, 100
     ctx, pj, cam, proj, bins, (img, T, nc), (toff, gidx), ref = _stage_case(eng, oracle, 9, W, H, 3000, tile, batch,
@@ -573,7 +573,7 @@ def test_autotune_picks_a_supported_shape_and_leaves_the_scene(eng):
     targets = torch.rand(2, 3, H, W, generator=torch.Generator().manual_seed(0)).cuda()
     P = eng.DeviceScene.from_host(sc)
     before = P.flat().clone()
-    shapes = [(16, 64, 1), (16, 64, 2), (8, 32, 1), (8, 64, 2)]     # the last one is not built
+    shapes = [(16, 64, 1), (16, 64, 2), (8, 32, 1), (8, 64, 4)]     # the last one is not built
     best, trials = autotune.tune(P, cams, targets, shapes=shapes, warmup=1, steps=2)
     assert (best["tile"], best["smem_batch"], best["px_per_thread"]) in shapes[:3]
     assert [(t.tile, t.smem_batch, t.px_per_thread) for t in trials] == shapes[:3]
