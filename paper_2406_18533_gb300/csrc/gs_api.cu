@@ -609,6 +609,7 @@ gs_status gs_render_bwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, con
                 reinterpret_cast<float4 *>(out->d_rgb)};
     launch_blend_bwd(vb, proj_of(proj), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges), blend_of(c->hp),
                      c->hp.smem_batch, c->hp.px_per_thread, gv, c->status, st);
+    launch_moments_to_grads(proj_of(proj), (int64_t)B * proj->N, gv, st);
     return cuda_check(c, "gs_render_bwd");
 }
 
@@ -624,7 +625,7 @@ gs_status gs_preprocess_bwd(gs_ctx *c, const gs_scene *scene, const gs_camera *c
     if (r != GS_OK) return r;
     GradView gv{reinterpret_cast<float4 *>(dproj->d_xy_o), reinterpret_cast<float4 *>(dproj->d_conic),
                 reinterpret_cast<float4 *>(dproj->d_rgb)};
-    launch_preprocess_bwd(view_of(scene), vb, proj_of(proj), gv, mut_of(grad), S(stream));
+    launch_preprocess_bwd(view_of(scene), vb, proj_of(proj), gv, true, mut_of(grad), S(stream));
     return cuda_check(c, "gs_preprocess_bwd");
 }
 
@@ -709,7 +710,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
                      gv, c->status, st);
     mark(c, st, 9);
-    launch_preprocess_bwd(sv, vb, pv, gv, mut_of(g), st);
+    launch_preprocess_bwd(sv, vb, pv, gv, false, mut_of(g), st);
     mark(c, st, 10);
     launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), adam_args(c->hp, step, B, c->dstep), c->status, st);
     mark(c, st, 11);

@@ -61,10 +61,31 @@ struct ProjView {
 };
 
 // Gradients per (view, Gaussian) entry: three separate float4 arrays (the
-// three atomics of an entry then go to different L2 slices).
+// three atomics of an entry then go to different L2 slices).  The blending
+// backward accumulates, over the pixels where the Gaussian blends with alpha
+// below alpha_max, the moments of dpow = alpha dL/dalpha at offset
+// (dx, dy) = pixel - centre:
+//   d_xy_o = (M, Mx, My) = sum (dpow, dpow dx, dpow dy),
+//   d_conic = (Mxx, Mxy, Myy) = sum (dpow dx^2, dpow dx dy, dpow dy^2),
+// and d_rgb = sum T alpha dL/dC (the colour gradient itself);
+// moments_to_grads turns the first two into gradients.
 struct GradView {
     float4 *d_xy_o, *d_conic, *d_rgb;
 };
+
+// From the moments to dL/d(u, v, opacity) and dL/d(a, b, c) of one entry with
+// conic_o = (a, b, c, o).  With power = -(a dx^2 + 2 b dx dy + c dy^2) / 2,
+// dx = px - u and alpha = o exp(power): d alpha / d power = alpha, so
+// dL/du = sum dpow (a dx + b dy), dL/dv = sum dpow (b dx + c dy),
+// dL/dopacity = sum dL/dalpha G = M / o, dL/da = -Mxx / 2, dL/db = -Mxy,
+// dL/dc = -Myy / 2.
+__host__ __device__ __forceinline__ void moments_to_grads(const float4 &co, const float4 &m_xy,
+                                                          const float4 &m_cn, float4 &g_xy_o, float4 &g_conic)
+{
+    g_xy_o = make_float4(co.x * m_xy.y + co.y * m_xy.z, co.y * m_xy.y + co.z * m_xy.z,
+                         co.w > 0.f ? m_xy.x / co.w : 0.f, 0.f);
+    g_conic = make_float4(-0.5f * m_cn.x, -m_cn.y, -0.5f * m_cn.z, 0.f);
+}
 
 // Device status word layout (one per context).
 struct DevStatus {
@@ -84,8 +105,11 @@ void count_launches(int n);
 // rectangle (pack_rect, the same arithmetic as the binning's).
 void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, uint32_t *ntiles,
                            uint2 *rect, DevStatus *status, int strict, cudaStream_t st);
+// g holds the blending backward's moments (GradView) unless grads_ready.
 void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
-                           const SceneMut &out, cudaStream_t st);
+                           bool grads_ready, const SceneMut &out, cudaStream_t st);
+// In place: the moments of n entries -> gradients (moments_to_grads).
+void launch_moments_to_grads(const ProjView &p, int64_t n, const GradView &g, cudaStream_t st);
 
 // Exclusive scan of n uint32 values (n < 2^31); total (uint64) to *total.
 // n_dev (optional): a device count that caps n (items past it are neither

@@ -236,10 +236,21 @@ __global__ void __launch_bounds__(128) k_preprocess_fwd(SceneView s, ViewBatch v
     }
 }
 
+// The blending backward's moments -> gradients of gs_proj, in place.
+__global__ void __launch_bounds__(256) k_moments_to_grads(ProjView p, int64_t n, GradView gv)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 gxo, gco;
+    moments_to_grads(p.conic_o[i], gv.d_xy_o[i], gv.d_conic[i], gxo, gco);
+    gv.d_xy_o[i] = gxo;
+    gv.d_conic[i] = gco;
+}
+
 // K8: chain rule from dL/d(u, v, conic, opacity, rgb) per view to the 59
 // parameters; views summed in a fixed order (deterministic), times 1/B.
 __global__ void __launch_bounds__(128) k_preprocess_bwd(SceneView s, ViewBatch vb, ProjView p, GradView gv,
-                                                        SceneMut out)
+                                                        bool grads_ready, SceneMut out)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= s.N) return;
@@ -269,8 +280,10 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(SceneView s, ViewBatch v
         const int64_t idx = (int64_t)v * s.N + g;
         if (p.radius[idx] <= 0) continue;
         const ViewCam &c = vb.v[v];
-        const float4 gxo = gv.d_xy_o[idx], gco = gv.d_conic[idx], grg = gv.d_rgb[idx];
         const float4 co = p.conic_o[idx];
+        float4 gxo = gv.d_xy_o[idx], gco = gv.d_conic[idx];
+        const float4 grg = gv.d_rgb[idx];
+        if (!grads_ready) moments_to_grads(co, float4(gxo), float4(gco), gxo, gco);
         dlogit += gxo.z * G.o * (1.f - G.o);
         // ---- colour -> SH and viewing direction
         float ddx = G.x - c.C[0], ddy = G.y - c.C[1], ddz = G.z - c.C[2];
@@ -428,12 +441,19 @@ void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjVi
 }
 
 void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
-                           const SceneMut &out, cudaStream_t st)
+                           bool grads_ready, const SceneMut &out, cudaStream_t st)
 {
     if (s.N == 0) return;
     const int threads = 128;
     const int64_t blocks = (s.N + threads - 1) / threads;
-    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, g, out);
+    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, g, grads_ready, out);
+    count_launches(1);
+}
+
+void launch_moments_to_grads(const ProjView &p, int64_t n, const GradView &g, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_moments_to_grads<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n, g);
     count_launches(1);
 }
 

@@ -11,16 +11,19 @@
 // compaction into the warp's buffer of CH entries in shared memory, order
 // preserved), and walks the buffer when another round could overflow it.  So
 // a warp spends nothing on list entries that cannot reach its pixels, and
-// finishes as soon as its own pixels do.  The staged record holds
+// finishes as soon as its own pixels do (no block-wide barrier at all).  The staged record holds
 // the exponent below which alpha < alpha_min, so most (pixel, Gaussian) pairs
 // are rejected before the exponential.
 // Forward: a lane stops once its pixel saturates; the warp stops refilling
 // when all its lanes have (early termination on transmittance).
 // Backward: each warp walks back to front from its own largest n_contrib,
 // recovers the transmittance before each contributor by division from
-// T_final (no per-fragment state is stored), reduces a Gaussian's nine
-// gradient components over the warp with a reduce-scatter (17 shuffles) and
-// adds them as three float4 atomics per (warp, Gaussian).
+// T_final (no per-fragment state is stored), accumulates per Gaussian the
+// moments of dpow = alpha dL/dalpha (M, Mx, My, Mxx, Mxy, Myy; the mean,
+// conic and opacity gradients are linear in them) and the colour gradient,
+// reduces these nine values over the warp with a reduce-scatter (17 shuffles)
+// and adds them as three float4 atomics per (warp, Gaussian).  The moments
+// become gradients once per (view, Gaussian) afterwards (moments_to_grads).
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -114,12 +117,12 @@ __device__ __forceinline__ int find_view(const ViewBatch &vb, uint32_t tile_id)
     return v;
 }
 
-// Warp-wide sums of one entry's nine gradient values v[0..8], added to entry
-// idx.  v[0..7] go through a reduce-scatter (at each level a lane keeps half
-// of its values and ships the other half: 4 + 2 + 1 + 1 + 1 = 9 shuffles,
-// after which value k is in lanes 4k .. 4k+3), v[8] through a butterfly (5);
-// lanes 0..2 gather (3 shuffles) and add (u, v, opacity), conic and rgb as
-// one float4 atomic each.
+// Warp-wide sums of one entry's nine values v[0..8] (the moments and colour
+// sums of GradView), added to entry idx.  v[0..7] go through a reduce-scatter
+// (at each level a lane keeps half of its values and ships the other half:
+// 4 + 2 + 1 + 1 + 1 = 9 shuffles, after which value k is in lanes
+// 4k .. 4k+3), v[8] through a butterfly (5); lanes 0..2 gather three values
+// each (3 shuffles) and add one float4 each.
 __device__ __forceinline__ void flush_one(const GradView &gv, int64_t idx, const float v[9], int lane)
 {
     float w[4], x[2];
@@ -208,10 +211,10 @@ __device__ __forceinline__ Entry fetch_entry(const ProjView &p, const uint32_t *
 }
 
 // Bytes of dynamic shared memory per CTA.
-template <int TILE, int CH, int PPT, bool BWD>
+template <int TILE, int CH, int PPT>
 constexpr size_t smem_bytes()
 {
-    return (size_t)(TILE * TILE / (32 * PPT)) * CH * ((BWD ? 4 : 3) * sizeof(float4) + sizeof(uint32_t));
+    return (size_t)(TILE * TILE / (32 * PPT)) * CH * (3 * sizeof(float4) + sizeof(uint32_t));
 }
 
 template <int TILE, int CH, int PPT>
@@ -221,7 +224,6 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, Pr
 {
     constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
-    __shared__ uint32_t s_red[NW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 *s_xyc = smem + warp * CH;              // u, v, exponent cut, -
     float4 *s_q = smem + (NW + warp) * CH;         // A, B, C, opacity
@@ -328,16 +330,11 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, Pr
         c.n_contrib[pix] = nc[k];
         evals += ne[k];
     }
-    // (pixel, list position) evaluations until termination, for the roofline counters
+    // (pixel, list position) evaluations until termination, for the roofline
+    // counters; each warp adds its own (no block barrier: warps finish apart)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
-    if (lane == 0) s_red[warp] = evals;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long tot = 0;
-        for (int w = 0; w < NW; ++w) tot += s_red[w];
-        if (tot) atomicAdd(&status->counters[1], tot);
-    }
+    if (lane == 0 && evals) atomicAdd(&status->counters[1], (unsigned long long)evals);
 }
 
 template <int TILE, int CH, int PPT>
@@ -347,13 +344,11 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
 {
     constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
-    __shared__ unsigned long long s_red64[2][NW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 *s_xyc = smem + warp * CH;
     float4 *s_q = smem + (NW + warp) * CH;
-    float4 *s_cn = smem + (2 * NW + warp) * CH;     // a, b, c, -
-    float4 *s_rgb = smem + (3 * NW + warp) * CH;    // r, g, b, Gaussian index (bits)
-    uint32_t *s_pos = reinterpret_cast<uint32_t *>(smem + 4 * NW * CH) + warp * CH;
+    float4 *s_rgb = smem + (2 * NW + warp) * CH;    // r, g, b, Gaussian index (bits)
+    uint32_t *s_pos = reinterpret_cast<uint32_t *>(smem + 3 * NW * CH) + warp * CH;
 
     const uint32_t tile_id = blockIdx.x;
     const int v = find_view(vb, tile_id);
@@ -408,7 +403,6 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
             const float4 rgbd = p.rgb_d[vbase + e.g];
             s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_cut(q.w, bp.alpha_min), 0.f);
             s_q[slot] = q;
-            s_cn[slot] = e.co;
             s_rgb[slot] = make_float4(rgbd.x, rgbd.y, rgbd.z, __uint_as_float(e.g));
             s_pos[slot] = (uint32_t)(j - rg.x);
         }
@@ -421,7 +415,8 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
             const float4 q = s_q[i];
             const float dx = __fsub_rn(ps.fx, xyc.x);
             const DxTerms dt = dx_terms(q, dx);
-            // this lane's gradient contributions, summed over its pixels
+            // this lane's sums over its pixels (GradView): M, Mx, My, Mxx, Mxy,
+            // Myy, r, g in vv, b in gbl
             float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float gbl = 0.f;
             bool any = false;
@@ -450,16 +445,15 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
                 B1[k] += alpha * e1;
                 B2[k] += alpha * e2;
                 T[k] = Tj;
-                if (oG < bp.alpha_max) {
-                    const float4 cn = s_cn[i];
+                if (oG < bp.alpha_max) {                // alpha not clamped: geometry and opacity terms
                     const float dpow = alpha * dalpha;
-                    const float hx = -0.5f * dpow * dx;
-                    vv[2] += G * dalpha;
-                    vv[0] += (cn.x * dx + cn.y * dy) * dpow;
-                    vv[1] += (cn.y * dx + cn.z * dy) * dpow;
-                    vv[3] += hx * dx;
-                    vv[4] += (hx + hx) * dy;
-                    vv[5] += -0.5f * dpow * dy * dy;
+                    const float dpx = dpow * dx, dpy = dpow * dy;
+                    vv[0] += dpow;
+                    vv[1] += dpx;
+                    vv[2] += dpy;
+                    vv[3] = fmaf(dpx, dx, vv[3]);
+                    vv[4] = fmaf(dpx, dy, vv[4]);
+                    vv[5] = fmaf(dpy, dy, vv[5]);
                 }
             }
             const uint32_t ballot = __ballot_sync(0xffffffffu, any);
@@ -487,13 +481,9 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
         e += __shfl_xor_sync(0xffffffffu, e, o);
         wk += __shfl_xor_sync(0xffffffffu, wk, o);
     }
-    if (lane == 0) { s_red64[0][warp] = e; s_red64[1][warp] = wk; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long a = 0, b = 0;
-        for (int w = 0; w < NW; ++w) { a += s_red64[0][w]; b += s_red64[1][w]; }
-        if (a) atomicAdd(&status->counters[2], a);
-        if (b) atomicAdd(&status->counters[4], b);
+    if (lane == 0) {
+        if (e) atomicAdd(&status->counters[2], e);
+        if (wk) atomicAdd(&status->counters[4], wk);
     }
 }
 
@@ -509,7 +499,7 @@ template <int TILE, int CH, int PPT>
 void fwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                 const BlendParams &bp, DevStatus *status, cudaStream_t st)
 {
-    constexpr size_t sm = smem_bytes<TILE, CH, PPT, false>();
+    constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
     static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH, PPT>, sm);
     (void)ok;
     k_blend_fwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status);
@@ -519,7 +509,7 @@ template <int TILE, int CH, int PPT>
 void bwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                 const BlendParams &bp, const GradView &g, DevStatus *status, cudaStream_t st)
 {
-    constexpr size_t sm = smem_bytes<TILE, CH, PPT, true>();
+    constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
     static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH, PPT>, sm);
     (void)ok;
     k_blend_bwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status);
