@@ -3,8 +3,8 @@
 // and backward").  SSIM uses an 11x11 Gaussian window (sigma 1.5), zero
 // padding, C1 = 0.01^2, C2 = 0.03^2.
 //
-// Two passes over 16x16 pixel tiles with a 5-pixel halo staged in shared
-// memory, separable convolution in each:
+// Two passes, each a separable convolution sliding down strips of 128 x 64
+// pixels (see k_ssim_fwd):
 //   pass A: the five local moments -> SSIM map value and its partials with
 //           respect to (mu_x, sigma_xx, sigma_xy), stored as three maps
 //           m1 = dS/dmu - 2 mu_x dS/dsxx - mu_y dS/dsxy, m2 = dS/dsxx,
@@ -17,147 +17,194 @@
 namespace gs {
 namespace {
 
-constexpr int LT = 16;              // output tile edge
+constexpr int LC = 128;             // output columns per CTA, one per thread
+constexpr int LROWS = 64;           // output rows per CTA
 constexpr int HALO = 5;
-constexpr int LR = LT + 2 * HALO;   // 26: staged region edge
+constexpr int WIN = 11;
+constexpr int LW = LC + 2 * HALO;   // staged row width
 constexpr float SSIM_C1 = 0.0001f;
 constexpr float SSIM_C2 = 0.0009f;
 
 struct Win { float w[11]; };
 
-__global__ void __launch_bounds__(LT *LT) k_ssim_fwd(const float *img, const float *tgt, int W, int H, Win win,
-                                                    float *maps, double *acc)
+// Asynchronous 4-byte global -> shared copies (cp.async, sm_80+); an invalid
+// source copies nothing and zero-fills the destination.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
 {
-    __shared__ float sx[LR][LR], sy[LR][LR];
-    __shared__ float h[5][LR][LT];
-    const int plane = blockIdx.z;              // view * 3 + channel
-    const int view = plane / 3;
-    const int64_t hw = (int64_t)W * H;
-    const float *X = img + plane * hw;
-    const float *Y = tgt + plane * hw;
-    const int ox = blockIdx.x * LT - HALO, oy = blockIdx.y * LT - HALO;
-    const int t = threadIdx.x;
-    for (int i = t; i < LR * LR; i += LT * LT) {
-        const int r = i / LR, cc = i % LR;
-        const int gx = ox + cc, gy = oy + r;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        sx[r][cc] = in ? X[(int64_t)gy * W + gx] : 0.f;
-        sy[r][cc] = in ? Y[(int64_t)gy * W + gx] : 0.f;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Input rows r0 .. r0+10 of plane `src` (zero outside the image), columns
+// x0 - 5 .. x0 + LC + 4, into buf, asynchronously (one commit group).
+__device__ __forceinline__ void load_chunk(float (*buf)[LW], const float *src, int r0, int x0, int W, int H)
+{
+    for (int i = threadIdx.x; i < WIN * LW; i += LC) {
+        const int row = i / LW, col = i - row * LW;
+        const int r = r0 + row, gx = x0 - HALO + col;
+        const bool ok = r >= 0 && r < H && gx >= 0 && gx < W;
+        cp_async4(&buf[row][col], ok ? src + (int64_t)r * W + gx : src, ok);
     }
-    __syncthreads();
-    // horizontal pass over all LR rows, LT output columns
-    for (int i = t; i < LR * LT; i += LT * LT) {
-        const int r = i / LT, cc = i % LT;
-        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
-#pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float xv = sx[r][cc + k], yv = sy[r][cc + k], w = win.w[k];
-            a += w * xv;
-            b += w * yv;
-            aa += w * xv * xv;
-            bb += w * yv * yv;
-            ab += w * xv * yv;
-        }
-        h[0][r][cc] = a; h[1][r][cc] = b; h[2][r][cc] = aa; h[3][r][cc] = bb; h[4][r][cc] = ab;
-    }
-    __syncthreads();
-    const int lx = t % LT, ly = t / LT;
-    const int gx = blockIdx.x * LT + lx, gy = blockIdx.y * LT + ly;
-    float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
-#pragma unroll
-    for (int k = 0; k < 11; ++k) {
-        const float w = win.w[k];
-        mx += w * h[0][ly + k][lx];
-        my += w * h[1][ly + k][lx];
-        exx += w * h[2][ly + k][lx];
-        eyy += w * h[3][ly + k][lx];
-        exy += w * h[4][ly + k][lx];
-    }
+}
+
+// Both passes slide down a strip of LC columns x LROWS rows.  Input rows come
+// in chunks of 11, loaded asynchronously into a double buffer while the
+// previous chunk is used (two barriers per chunk).  Each thread convolves a
+// row horizontally at its column, keeps the last 11 horizontal results in a
+// register ring (the row loop is unrolled by 11, so ring slots are static),
+// and once 11 rows are in, convolves vertically for the output row 5 rows up.
+// Every input value is read once per strip (plus the 10-row and 10-column
+// halo).
+__global__ void __launch_bounds__(LC) k_ssim_fwd(const float *img, const float *tgt, int W, int H, Win win,
+                                                 float *maps, double *acc)
+{
+    __shared__ float sx[2][WIN][LW], sy[2][WIN][LW];
+    __shared__ float red[2][LC / 32];
+    const int plane = blockIdx.z, view = plane / 3;
+    const int64_t hw = (int64_t)W * H, tot = (int64_t)gridDim.z * hw;
+    const float *X = img + plane * hw, *Y = tgt + plane * hw;
+    const int x0 = blockIdx.x * LC, y0 = blockIdx.y * LROWS;
+    const int t = threadIdx.x, gx = x0 + t;
+    const int nrows = min(LROWS, H - y0);
+    const int nin = nrows + 2 * HALO;
+    float ring[WIN][5];
     float l1 = 0.f, ss = 0.f;
-    if (gx < W && gy < H) {
-        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-        const float n1 = 2.f * mx * my + SSIM_C1, n2 = 2.f * sxy + SSIM_C2;
-        const float d1 = mx * mx + my * my + SSIM_C1, d2 = sxx + syy + SSIM_C2;
-        const float id = 1.f / (d1 * d2);
-        const float S = n1 * n2 * id;
-        const float A = 2.f * my * n2 * id - S * 2.f * mx / d1;
-        const float Bm = -S / d2;
-        const float Cm = 2.f * n1 * id;
-        const int64_t pix = (int64_t)gy * W + gx;
-        const int64_t tot = (int64_t)gridDim.z * hw;
-        maps[plane * hw + pix] = A - 2.f * mx * Bm - my * Cm;
-        maps[tot + plane * hw + pix] = Bm;
-        maps[2 * tot + plane * hw + pix] = Cm;
-        l1 = fabsf(sx[ly + HALO][lx + HALO] - sy[ly + HALO][lx + HALO]);
-        ss = S;
+    load_chunk(sx[0], X, y0 - HALO, x0, W, H);
+    load_chunk(sy[0], Y, y0 - HALO, x0, W, H);
+    cp_async_commit();
+    for (int rb = 0, cb = 0; rb < nin; rb += WIN, cb ^= 1) {
+        if (rb + WIN < nin) {
+            load_chunk(sx[cb ^ 1], X, y0 - HALO + rb + WIN, x0, W, H);
+            load_chunk(sy[cb ^ 1], Y, y0 - HALO + rb + WIN, x0, W, H);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();                             // this chunk has landed
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < WIN; ++s) {
+            const int q = rb + s;                       // input row within the strip
+            if (q >= nin) break;                        // the same for every thread
+            const float *bx = sx[cb][s], *by = sy[cb][s];
+            float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+#pragma unroll
+            for (int k = 0; k < WIN; ++k) {
+                const float xv = bx[t + k], yv = by[t + k], w = win.w[k];
+                a += w * xv;
+                b += w * yv;
+                aa += w * xv * xv;
+                bb += w * yv * yv;
+                ab += w * xv * yv;
+            }
+            ring[s][0] = a; ring[s][1] = b; ring[s][2] = aa; ring[s][3] = bb; ring[s][4] = ab;
+            if (q < 2 * HALO) continue;
+            // rows q-10 .. q are in the ring, oldest at slot (s + 1) % 11
+            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+#pragma unroll
+            for (int k = 0; k < WIN; ++k) {
+                const int sl = (s + 1 + k) % WIN;
+                const float w = win.w[k];
+                mx += w * ring[sl][0];
+                my += w * ring[sl][1];
+                exx += w * ring[sl][2];
+                eyy += w * ring[sl][3];
+                exy += w * ring[sl][4];
+            }
+            const int gy = y0 + q - 2 * HALO;
+            if (gx < W) {
+                const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+                const float n1 = 2.f * mx * my + SSIM_C1, n2 = 2.f * sxy + SSIM_C2;
+                const float d1 = mx * mx + my * my + SSIM_C1, d2 = sxx + syy + SSIM_C2;
+                const float id = 1.f / (d1 * d2);
+                const float S = n1 * n2 * id;
+                const float A = 2.f * my * n2 * id - S * 2.f * mx / d1;
+                const float Bm = -S / d2;
+                const float Cm = 2.f * n1 * id;
+                const int64_t pix = (int64_t)gy * W + gx;
+                maps[plane * hw + pix] = A - 2.f * mx * Bm - my * Cm;
+                maps[tot + plane * hw + pix] = Bm;
+                maps[2 * tot + plane * hw + pix] = Cm;
+                l1 += fabsf(X[pix] - Y[pix]);     // (the previous chunk's buffer is being refilled)
+                ss += S;
+            }
+        }
+        __syncthreads();                                // the next chunk's load may overwrite cb ^ 1
     }
-    // block reduction of the two sums
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         l1 += __shfl_xor_sync(0xffffffffu, l1, o);
         ss += __shfl_xor_sync(0xffffffffu, ss, o);
     }
-    __shared__ float red[2][LT * LT / 32];
     if ((t & 31) == 0) { red[0][t >> 5] = l1; red[1][t >> 5] = ss; }
     __syncthreads();
     if (t == 0) {
         double a = 0.0, b = 0.0;
-        for (int w = 0; w < LT * LT / 32; ++w) { a += red[0][w]; b += red[1][w]; }
+        for (int w = 0; w < LC / 32; ++w) { a += red[0][w]; b += red[1][w]; }
         atomicAdd(&acc[2 * view], a);
         atomicAdd(&acc[2 * view + 1], b);
     }
 }
 
-__global__ void __launch_bounds__(LT *LT) k_ssim_bwd(const float *img, const float *tgt, int W, int H, Win win,
-                                                    const float *maps, float lambda, float *dimg)
+__global__ void __launch_bounds__(LC) k_ssim_bwd(const float *img, const float *tgt, int W, int H, Win win,
+                                                 const float *maps, float lambda, float *dimg)
 {
-    __shared__ float sm[3][LR][LR];
-    __shared__ float h[3][LR][LT];
+    __shared__ float sm[2][3][WIN][LW];
     const int plane = blockIdx.z;
-    const int64_t hw = (int64_t)W * H;
-    const int64_t tot = (int64_t)gridDim.z * hw;
-    const int ox = blockIdx.x * LT - HALO, oy = blockIdx.y * LT - HALO;
-    const int t = threadIdx.x;
-    for (int i = t; i < LR * LR; i += LT * LT) {
-        const int r = i / LR, cc = i % LR;
-        const int gx = ox + cc, gy = oy + r;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const int64_t o = plane * hw + (int64_t)gy * W + gx;
-        sm[0][r][cc] = in ? maps[o] : 0.f;
-        sm[1][r][cc] = in ? maps[tot + o] : 0.f;
-        sm[2][r][cc] = in ? maps[2 * tot + o] : 0.f;
-    }
-    __syncthreads();
-    for (int i = t; i < LR * LT; i += LT * LT) {
-        const int r = i / LT, cc = i % LT;
-        float a = 0.f, b = 0.f, c = 0.f;
-#pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = win.w[k];
-            a += w * sm[0][r][cc + k];
-            b += w * sm[1][r][cc + k];
-            c += w * sm[2][r][cc + k];
-        }
-        h[0][r][cc] = a; h[1][r][cc] = b; h[2][r][cc] = c;
-    }
-    __syncthreads();
-    const int lx = t % LT, ly = t / LT;
-    const int gx = blockIdx.x * LT + lx, gy = blockIdx.y * LT + ly;
-    if (gx >= W || gy >= H) return;
-    float a = 0.f, b = 0.f, c = 0.f;
-#pragma unroll
-    for (int k = 0; k < 11; ++k) {
-        const float w = win.w[k];
-        a += w * h[0][ly + k][lx];
-        b += w * h[1][ly + k][lx];
-        c += w * h[2][ly + k][lx];
-    }
-    const int64_t o = plane * hw + (int64_t)gy * W + gx;
-    const float x = img[o], y = tgt[o];
+    const int64_t hw = (int64_t)W * H, tot = (int64_t)gridDim.z * hw;
+    const float *M[3] = {maps + plane * hw, maps + tot + plane * hw, maps + 2 * tot + plane * hw};
+    const int x0 = blockIdx.x * LC, y0 = blockIdx.y * LROWS;
+    const int t = threadIdx.x, gx = x0 + t;
+    const int nrows = min(LROWS, H - y0);
+    const int nin = nrows + 2 * HALO;
     const float n = 3.f * (float)hw;
-    const float dS = a + 2.f * x * b + y * c;
-    const float sgn = x > y ? 1.f : (x < y ? -1.f : 0.f);
-    dimg[o] = ((1.f - lambda) * sgn - lambda * dS) / n;
+    float ring[WIN][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) load_chunk(sm[0][m], M[m], y0 - HALO, x0, W, H);
+    cp_async_commit();
+    for (int rb = 0, cb = 0; rb < nin; rb += WIN, cb ^= 1) {
+        if (rb + WIN < nin) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m) load_chunk(sm[cb ^ 1][m], M[m], y0 - HALO + rb + WIN, x0, W, H);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < WIN; ++s) {
+            const int q = rb + s;
+            if (q >= nin) break;
+            float h0 = 0.f, h1 = 0.f, h2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < WIN; ++k) {
+                const float w = win.w[k];
+                h0 += w * sm[cb][0][s][t + k];
+                h1 += w * sm[cb][1][s][t + k];
+                h2 += w * sm[cb][2][s][t + k];
+            }
+            ring[s][0] = h0; ring[s][1] = h1; ring[s][2] = h2;
+            if (q < 2 * HALO) continue;
+            float a = 0.f, bb = 0.f, c = 0.f;
+#pragma unroll
+            for (int k = 0; k < WIN; ++k) {
+                const int sl = (s + 1 + k) % WIN;
+                const float w = win.w[k];
+                a += w * ring[sl][0];
+                bb += w * ring[sl][1];
+                c += w * ring[sl][2];
+            }
+            const int gy = y0 + q - 2 * HALO;
+            if (gx < W) {
+                const int64_t o = plane * hw + (int64_t)gy * W + gx;
+                const float x = img[o], y = tgt[o];
+                const float dS = a + 2.f * x * bb + y * c;
+                const float sgn = x > y ? 1.f : (x < y ? -1.f : 0.f);
+                dimg[o] = ((1.f - lambda) * sgn - lambda * dS) / n;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void k_loss_finish(const double *acc, int B, double n, float lambda, float *loss_out)
@@ -186,9 +233,9 @@ void launch_loss(const float *img, const float *target, int B, int W, int H, flo
 {
     static const Win win = make_window();
     cudaMemsetAsync(acc, 0, sizeof(double) * 2 * B, st);
-    const dim3 grid((W + LT - 1) / LT, (H + LT - 1) / LT, 3 * B);
-    k_ssim_fwd<<<grid, LT * LT, 0, st>>>(img, target, W, H, win, maps, acc);
-    k_ssim_bwd<<<grid, LT * LT, 0, st>>>(img, target, W, H, win, maps, lambda, d_img);
+    const dim3 grid((W + LC - 1) / LC, (H + LROWS - 1) / LROWS, 3 * B);
+    k_ssim_fwd<<<grid, LC, 0, st>>>(img, target, W, H, win, maps, acc);
+    k_ssim_bwd<<<grid, LC, 0, st>>>(img, target, W, H, win, maps, lambda, d_img);
     k_loss_finish<<<1, 32, 0, st>>>(acc, B, 3.0 * (double)W * H, lambda, loss_out);
     count_launches(3);
 }
