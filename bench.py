@@ -189,6 +189,21 @@ def run_reference(args, rank):
 
 # ------------------------------------------------------------------ our arm
 
+# DRAM bytes (read + write) of one k_blend_bwd launch per walked (pixel, list
+# position) pair, from the ncu capture in profiles/k_blend_bwd_c1_train_1m_1080p.md
+# (tile 16, 64 entries, 2 pixels per thread on C1); the kernel's gathers and
+# atomics grow with the walked pairs, so the traffic of a bench launch is
+# taken as this times its walked count.
+BLEND_BWD_DRAM_BYTES_PER_WALKED = 1.097
+
+
+def stage_traffic(stage, counters):
+    """DRAM traffic of one launch of the stage from a capture, or None."""
+    if stage == "blend_bwd":
+        return BLEND_BWD_DRAM_BYTES_PER_WALKED * counters.get("walked_bwd", 0)
+    return None
+
+
 def stage_roofline(stage, ms, counters, N, Bv, pixels, passes, peaks, clock_mhz):
     """Algorithmic work of one launch of a stage, and the matching peak."""
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
@@ -407,7 +422,9 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     rf = stage_roofline(dom, stage_ms[dom], counters, sc.N, Bv, Bv * H * W, passes, peaks, clk)
     roofline = {"kernel": dom, "bound": rf["bound"], "achieved": rf["achieved"], "peak": rf["peak"],
-                "unit": rf["unit"], "frac": rf["achieved"] / rf["peak"], "traffic": None,
+                "unit": rf["unit"], "frac": rf["achieved"] / rf["peak"], "traffic": stage_traffic(dom, counters),
+                "traffic_unit": "bytes per launch (ncu dram bytes per walked pair on C1, scaled by this "
+                                "launch's walked pairs)" if dom == "blend_bwd" else None,
                 "peak_source": peak_kind, "work": rf["work_desc"]}
     per_stage_roofline = {}
     for s, ms in stage_ms.items():
