@@ -91,22 +91,23 @@ __device__ __forceinline__ bool alpha_box_hits(const float4 &co, float u, float 
     if (!(det > 0.f && a > 0.f && c > 0.f)) return true;
     const float ex = fminf(fmaxf(u, x0), x1), ey = fminf(fmaxf(v, y0), y1);
     if (ex == u && ey == v) return true;                   // centre inside the box
+    // approximate reciprocals (a few ulp): the threshold's 0.1 % widening covers them
     float fmin = INFINITY;
     if (ex != u) {                                         // edge x = ex
-        const float dx = ex - u;
-        const float dys = -b * dx / c;
+        const float dx = ex - u, ic = __fdividef(1.f, c);
+        const float dys = -b * dx * ic;
         const float t = fminf(fmaxf(dys, y0 - v), y1 - v) - dys;
-        fmin = c * t * t + det / c * (dx * dx);
+        fmin = c * t * t + det * ic * (dx * dx);
     }
     if (ey != v) {                                         // edge y = ey
-        const float dy = ey - v;
-        const float dxs = -b * dy / a;
+        const float dy = ey - v, ia = __fdividef(1.f, a);
+        const float dxs = -b * dy * ia;
         const float t = fminf(fmaxf(dxs, x0 - u), x1 - u) - dxs;
-        fmin = fminf(fmin, a * t * t + det / a * (dy * dy));
+        fmin = fminf(fmin, a * t * t + det * ia * (dy * dy));
     }
-    const float L = 2.f * __logf(co.w / alpha_min);
+    const float L = 2.f * __logf(__fdividef(co.w, alpha_min));
     const float tr = 0.5f * (a + c), r = sqrtf(0.25f * (a - c) * (a - c) + bb);
-    const float kappa = (tr + r) / fmaxf(tr - r, 1e-30f);  // condition number of the conic
+    const float kappa = __fdividef(tr + r, fmaxf(tr - r, 1e-30f));   // condition number of the conic
     return fmin <= L * (1.001f + 1e-6f * kappa) + 1e-4f;
 }
 
