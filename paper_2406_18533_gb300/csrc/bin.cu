@@ -214,13 +214,26 @@ __global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, co
                                                        const uint32_t *n_vis, uint32_t *counts, uint32_t *rx,
                                                        uint32_t *ry)
 {
+    // four slots per thread per round (j, j + S, j + 2S, j + 3S), their random
+    // reads issued together
     const int64_t nv = *n_vis;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nv; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t o = order[j];
-        const uint2 rc = o < n ? rect[o] : make_uint2(1u, 0u);   // o >= n only after a failed (timed-out) sort
-        counts[j] = rect_area(rc);
-        rx[j] = rc.x;
-        ry[j] = rc.y;
+    const int64_t S = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < nv; j0 += 4 * S) {
+        uint32_t o[4];
+        uint2 rc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[u] = j0 + u * S < nv ? order[j0 + u * S] : 0xffffffffu;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rc[u] = o[u] < n ? rect[o[u]] : make_uint2(1u, 0u);   // o >= n: past the end, or a failed sort
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = j0 + u * S;
+            if (j < nv) {
+                counts[j] = rect_area(rc[u]);
+                rx[j] = rc[u].x;
+                ry[j] = rc[u].y;
+            }
+        }
     }
 }
 
