@@ -207,32 +207,114 @@ __global__ void __launch_bounds__(256) k_pair_compact(int64_t n, const float4 *r
     }
 }
 
-// The visible pairs' tile rectangles and tile counts in depth order (the
-// counts are the input of the offsets scan): one random read per visible
-// pair, after which the emission reads everything in order.
-__global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n,
-                                                       const uint32_t *n_vis, uint32_t *counts, uint32_t *rx,
-                                                       uint32_t *ry)
+// Culls footprint tiles against the alpha >= cull_alpha ellipse, in pair
+// index order (coalesced reads): a warp lays the rectangles (of at most
+// TILE_CULL_MAX_AREA tiles) of its 32 pairs end to end and tests one (pair,
+// tile) slot per lane per round (ellipse_terms once per pair, the box test
+// per slot), so the work is balanced whatever the rectangle sizes; each
+// pair's lane collects its slots' ballot bits.  rm[i] = (rectangle words,
+// kept-tile bits low, high); larger rectangles and pairs not culled keep all
+// bits.  area[i] becomes the kept count (0 drops the pair from the binning).
+// Pairs with area[i] = 0 (not visible) are skipped.
+__global__ void __launch_bounds__(256) k_cull_tiles(ViewBatch vb, ProjView p, const uint2 *rect, uint32_t *area,
+                                                    float cull_alpha, uint4 *rm)
 {
-    // four slots per thread per round (j, j + S, j + 2S, j + 3S), their random
-    // reads issued together
-    const int64_t nv = *n_vis;
-    const int64_t S = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < nv; j0 += 4 * S) {
-        uint32_t o[4];
-        uint2 rc[4];
+    const int64_t n = (int64_t)vb.B * p.N;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i - lane >= n) return;                   // uniform over the warp
+    const uint32_t cnt0 = i < n ? area[i] : 0u;  // 0: not visible, nothing to do
+    if (!__any_sync(0xffffffffu, cnt0 > 0u)) return;
+    const uint2 rc = cnt0 ? rect[i] : make_uint2(1u, 0u);
+    const uint32_t ra = rect_area(rc);
+    const bool cull = cnt0 > 0u && ra <= TILE_CULL_MAX_AREA;
+    uint64_t mask = ~0ull;
+    if (__any_sync(0xffffffffu, cull)) {
+        float4 co = make_float4(0.f, 0.f, 0.f, 0.f), te = make_float4(-1.f, 0.f, 0.f, 0.f);
+        float2 uv = make_float2(0.f, 0.f);
+        if (cull) {
+            co = p.conic_o[i];
+            uv = p.xy[i];
+            te = ellipse_terms(co, cull_alpha);
+            mask = 0ull;
+        }
+        const uint32_t x0 = rc.x & 0xffffu, y0 = rc.y & 0xffffu, w = (rc.x >> 16) - x0 + 1u;
+        const uint32_t sa = cull ? ra : 0u;      // slots of this lane's pair
+        uint32_t incl = sa;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) o[u] = j0 + u * S < nv ? order[j0 + u * S] : 0xffffffffu;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const uint32_t rel = incl - sa;
+        const uint32_t span = __shfl_sync(0xffffffffu, incl, 31);
+        const float T = (float)vb.tile;
+        for (uint32_t r0 = 0; r0 < span; r0 += 32) {
+            const uint32_t f = r0 + lane;
+            int L = 0;                           // last lane with rel <= f
 #pragma unroll
-        for (int u = 0; u < 4; ++u) rc[u] = o[u] < n ? rect[o[u]] : make_uint2(1u, 0u);   // o >= n: past the end, or a failed sort
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t j = j0 + u * S;
-            if (j < nv) {
-                counts[j] = rect_area(rc[u]);
-                rx[j] = rc[u].x;
-                ry[j] = rc[u].y;
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t q = __shfl_sync(0xffffffffu, rel, L + step);
+                if (q <= f) L += step;
             }
+            const uint32_t local = f - __shfl_sync(0xffffffffu, rel, L);
+            const uint32_t lw = __shfl_sync(0xffffffffu, w, L);
+            const uint32_t lx0 = __shfl_sync(0xffffffffu, x0, L), ly0 = __shfl_sync(0xffffffffu, y0, L);
+            const float4 lt = make_float4(__shfl_sync(0xffffffffu, te.x, L), __shfl_sync(0xffffffffu, te.y, L),
+                                          __shfl_sync(0xffffffffu, te.z, L), __shfl_sync(0xffffffffu, te.w, L));
+            const float la = __shfl_sync(0xffffffffu, co.x, L), lb = __shfl_sync(0xffffffffu, co.y, L),
+                        lc = __shfl_sync(0xffffffffu, co.z, L);
+            const float lu = __shfl_sync(0xffffffffu, uv.x, L), lv = __shfl_sync(0xffffffffu, uv.y, L);
+            bool hit = false;
+            if (f < span) {
+                const uint32_t dy = local / lw, dx = local - dy * lw;
+                const float bx = __fmaf_rn((float)(lx0 + dx), T, 0.5f), by = __fmaf_rn((float)(ly0 + dy), T, 0.5f);
+                hit = ellipse_terms_box_hits(lt, la, lb, lc, lu, lv, bx, __fadd_rn(bx, T - 1.f), by,
+                                             __fadd_rn(by, T - 1.f));
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            // this lane's slots [rel, rel + sa) within the round's [r0, r0 + 32)
+            if (sa && rel < r0 + 32u && rel + sa > r0) {
+                const uint32_t lo = rel > r0 ? rel - r0 : 0u;
+                const uint32_t hi = rel + sa < r0 + 32u ? rel + sa - r0 : 32u;
+                const uint32_t width = hi - lo;
+                const uint32_t bits = (bal >> lo) & (width == 32u ? 0xffffffffu : ((1u << width) - 1u));
+                mask |= (uint64_t)bits << (r0 + lo - rel);
+            }
+        }
+    }
+    if (cnt0) {                                  // (rm is read for visible pairs only)
+        rm[i] = make_uint4(rc.x, rc.y, (uint32_t)mask, (uint32_t)(mask >> 32));
+        if (cull) area[i] = (uint32_t)__popcll(mask);
+    }
+}
+
+// The visible pairs' tile rectangles and tile counts in depth order (the
+// counts are the input of the offsets scan), so that the emission reads
+// everything in order; with culling (rm non-null) one 16-byte random read per
+// pair brings the rectangle and the kept-tile bits.
+__global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, const uint2 *rect,
+                                                       const uint32_t *area, const uint4 *rm, int64_t n,
+                                                       const uint32_t *n_vis, uint32_t *counts, uint32_t *rx,
+                                                       uint32_t *ry, uint2 *keep)
+{
+    const int64_t nv = (int64_t)*n_vis < n ? (int64_t)*n_vis : n;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nv; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t o = order[j];
+        const bool ok = o < n;                   // o >= n only after a failed (timed-out) sort
+        if (rm) {
+            const uint4 r = ok ? rm[o] : make_uint4(1u, 0u, 0u, 0u);
+            const uint32_t ra = rect_area(make_uint2(r.x, r.y));
+            const uint64_t m = ((uint64_t)r.w << 32) | r.z;
+            counts[j] = ra <= TILE_CULL_MAX_AREA ? (uint32_t)__popcll(m) : ra;
+            rx[j] = r.x;
+            ry[j] = r.y;
+            keep[j] = make_uint2(r.z, r.w);
+        } else {
+            const uint2 rc = ok ? rect[o] : make_uint2(1u, 0u);
+            counts[j] = ok ? area[o] : 0u;
+            rx[j] = rc.x;
+            ry[j] = rc.y;
         }
     }
 }
@@ -249,14 +331,15 @@ __global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, co
 // past capacity.
 __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, const uint32_t *n_vis,
                                                    const uint32_t *order, const uint32_t *rx, const uint32_t *ry,
-                                                   const uint32_t *offsets, uint32_t *keys,
+                                                   const uint2 *keep, const uint32_t *offsets, uint32_t *keys,
                                                    uint32_t *vals, uint64_t capacity,
                                                    const unsigned long long *total, DevStatus *status,
-                                                   uint32_t *count_out)
+                                                   uint32_t *count_out, float cull_alpha)
 {
     const int64_t nb = (int64_t)vb.B * N;
     const int64_t n = (int64_t)*n_vis < nb ? (int64_t)*n_vis : nb;   // pairs in depth order
     const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t j0 = j - lane;                 // the warp's first pair
     const unsigned long long F = *total;
@@ -274,25 +357,40 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
         }
     }
     if (F > capacity || j0 >= n) return;         // uniform over the warp
-    uint32_t start = 0u, cnt = 0u, g = 0u, corner = 0u, wdt = 1u, tx_row = 0u;
+    uint32_t start = 0u, area = 0u, g = 0u, corner = 0u, wdt = 1u, tx_row = 0u, mlo = 0xffffffffu,
+             mhi = 0xffffffffu;
     if (j < n) {
         start = offsets[j];
         const int64_t i = (int64_t)order[j];
         const uint2 rc = make_uint2(rx[j], ry[j]);
-        cnt = rect_area(rc);                     // 0 where the pair sort failed (i >= B * N)
-        if (cnt && i < nb) {
+        area = rect_area(rc);
+        if (area && i < nb) {                    // i >= B * N only after a failed (timed-out) pair sort
             const int v = (int)(i / N);
             g = (uint32_t)(i - (int64_t)v * N);
             const uint32_t x0 = rc.x & 0xffffu;
             wdt = (rc.x >> 16) - x0 + 1u;
             tx_row = (uint32_t)vb.v[v].TX;
             corner = vb.v[v].tile_base + (rc.y & 0xffffu) * tx_row + x0;   // tile (x0, y0)
+            if (cull_alpha > 0.f && area <= TILE_CULL_MAX_AREA) {
+                const uint2 k = keep[j];
+                mlo = k.x;
+                mhi = k.y;
+            }
+        } else {
+            area = 0u;
         }
     }
-    const int last = (int)(n - 1 - j0 < 31 ? n - 1 - j0 : 31);
+    // the lanes' rectangles laid end to end: exclusive prefix of their areas
+    uint32_t incl = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t rel = incl - area;            // lanes past n: rel = span, never matched
+    const uint32_t span = __shfl_sync(0xffffffffu, incl, 31);
     const uint32_t base = __shfl_sync(0xffffffffu, start, 0);
-    const uint32_t span = __shfl_sync(0xffffffffu, start + cnt, last) - base;
-    const uint32_t rel = j < n ? start - base : span;   // lanes past n never match
+    uint32_t out = 0;                            // fragments written so far by the warp
     for (uint32_t r0 = 0; r0 < span; r0 += 32) {
         const uint32_t f = r0 + lane;
         int L = 0;                               // last lane with rel <= f
@@ -306,13 +404,20 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
         const uint32_t ltx = __shfl_sync(0xffffffffu, tx_row, L);
         const uint32_t lc = __shfl_sync(0xffffffffu, corner, L);
         const uint32_t lg = __shfl_sync(0xffffffffu, g, L);
-        if (f < span) {
-            const uint32_t local = f - lrel;
-            const uint32_t dy = local / lw;
-            const uint64_t o = (uint64_t)base + f;
-            keys[o] = lc + dy * ltx + (local - dy * lw);
-            vals[o] = lg;
+        const uint32_t llo = __shfl_sync(0xffffffffu, mlo, L), lhi = __shfl_sync(0xffffffffu, mhi, L);
+        const uint32_t local = f - lrel;
+        const uint32_t dy = local / lw, dx = local - dy * lw;
+        // a rectangle's slot is kept unless its pair was culled and the slot's bit is clear
+        const bool keep_slot = f < span && ((local < 32u ? llo >> local : lhi >> ((local - 32u) & 31u)) & 1u);
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep_slot);
+        if (keep_slot) {
+            const uint64_t o = (uint64_t)base + out + __popc(bal & lt);
+            if (o < F) {                         // the kept slots match the counts by construction
+                keys[o] = lc + dy * ltx + dx;
+                vals[o] = lg;
+            }
         }
+        out += __popc(bal);
     }
 }
 
@@ -680,23 +785,34 @@ uint32_t *launch_depth_order(const ViewBatch &vb, const ProjView &p, bool rect_r
     return order;                                 // four passes: back in the first buffers
 }
 
-void launch_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n, const uint32_t *n_vis,
-                          uint32_t *counts, uint32_t *rx, uint32_t *ry, cudaStream_t st)
+void launch_cull_tiles(const ViewBatch &vb, const ProjView &p, const uint2 *rect, uint32_t *area, float cull_alpha,
+                       uint4 *rm, cudaStream_t st)
+{
+    const int64_t n = (int64_t)vb.B * p.N;
+    if (n <= 0) return;
+    k_cull_tiles<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vb, p, rect, area, cull_alpha, rm);
+    count_launches(1);
+}
+
+void launch_gather_counts(const uint32_t *order, const uint2 *rect, const uint32_t *area, const uint4 *rm, int64_t n,
+                          const uint32_t *n_vis, uint32_t *counts, uint32_t *rx, uint32_t *ry, uint2 *keep,
+                          cudaStream_t st)
 {
     if (n <= 0) return;
-    k_gather_counts<<<stride_blocks((uint64_t)n), 256, 0, st>>>(order, rect, n, n_vis, counts, rx, ry);
+    k_gather_counts<<<stride_blocks((uint64_t)n), 256, 0, st>>>(order, rect, area, rm, n, n_vis, counts, rx, ry,
+                                                               keep);
     count_launches(1);
 }
 
 void launch_emit_keys(const ViewBatch &vb, int64_t N, const uint32_t *n_vis, const uint32_t *order,
-                      const uint32_t *rx, const uint32_t *ry, const uint32_t *offsets, uint32_t *keys, uint32_t *vals,
-                      uint64_t capacity, const unsigned long long *total, DevStatus *status, uint32_t *count_out,
-                      cudaStream_t st)
+                      const uint32_t *rx, const uint32_t *ry, const uint2 *keep, const uint32_t *offsets,
+                      uint32_t *keys, uint32_t *vals, uint64_t capacity, const unsigned long long *total,
+                      DevStatus *status, uint32_t *count_out, float cull_alpha, cudaStream_t st)
 {
     const int64_t n = (int64_t)vb.B * N;
     const int64_t blocks = n > 0 ? (n + 255) / 256 : 1;
-    k_emit_keys<<<(unsigned)blocks, 256, 0, st>>>(vb, N, n_vis, order, rx, ry, offsets, keys, vals, capacity, total,
-                                                 status, count_out);
+    k_emit_keys<<<(unsigned)blocks, 256, 0, st>>>(vb, N, n_vis, order, rx, ry, keep, offsets, keys, vals, capacity,
+                                                 total, status, count_out, cull_alpha);
     count_launches(1);
 }
 

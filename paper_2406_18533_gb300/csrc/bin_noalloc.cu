@@ -138,10 +138,10 @@ extern "C" gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, 
     // the sort's dead buffers take the counts and rectangles in depth order
     uint32_t *counts = order == pv_order ? pk : pv_order;
     uint32_t *rx = order == pv_order ? pv_alt : pk, *ry = pk_alt;
-    launch_gather_counts(order, rect, n, n_vis, counts, rx, ry, st);
+    launch_gather_counts(order, rect, area, nullptr, n, n_vis, counts, rx, ry, nullptr, st);
     launch_exclusive_scan(counts, offsets, n, total, s + OFF_SCAN, st, n_vis);
-    launch_emit_keys(vb, pv.N, n_vis, order, rx, ry, offsets, even ? tk : tk_alt, even ? out->vals : vals_alt,
-                     out->capacity, total, status, out->count, st);
+    launch_emit_keys(vb, pv.N, n_vis, order, rx, ry, nullptr, offsets, even ? tk : tk_alt,
+                     even ? out->vals : vals_alt, out->capacity, total, status, out->count, 0.f, st);
     launch_sort_fragments(even ? tk : tk_alt, even ? out->vals : vals_alt, even ? tk_alt : tk,
                           even ? vals_alt : out->vals, out->capacity, out->count, high, sort_tmp, status, st);
     launch_tile_ranges(tk, out->count, out->capacity, reinterpret_cast<uint2 *>(out->ranges), vb.total_tiles, st);

@@ -37,6 +37,8 @@ struct gs_ctx {
     DBuf ntiles, offsets, scan_tmp, total, keys_alt, vals_alt, sort_tmp;
     DBuf pk, pv, pk_alt, pv_alt;   // (view, Gaussian) pairs sorted by depth
     DBuf rect;                     // their tile rectangles
+    DBuf kmask;                    // their kept tiles (bits of the rectangle), in depth order
+    DBuf rmask;                    // rectangle and kept tiles per pair, in index order
     // iteration scratch (gs_train_step / gs_render)
     DBuf xy, conic_o, rgb_d, radius, g_proj, keys, vals, ranges, count;
     DBuf img, dimg, T_final, n_contrib, maps, acc;
@@ -219,6 +221,7 @@ gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, bool re
         (r = ensure(c, c->ntiles, 4 * n1)) ||
         (r = ensure(c, c->total, 64)) || (r = ensure(c, c->pk, 4 * n1)) || (r = ensure(c, c->pv, 4 * n1)) ||
         (r = ensure(c, c->pk_alt, 4 * n1)) || (r = ensure(c, c->pv_alt, 4 * n1)) || (r = ensure(c, c->rect, 8 * n1)) ||
+        (r = ensure(c, c->kmask, 8 * n1)) || (r = ensure(c, c->rmask, 16 * n1)) ||
         (r = ensure(c, c->keys, 4 * (size_t)cap1)) || (r = ensure(c, c->keys_alt, 4 * (size_t)cap1)) ||
         (r = ensure(c, c->vals_alt, 4 * (size_t)cap1)) || (r = ensure(c, c->sort_tmp, sort_temp_bytes((uint64_t)n, capacity))))
         return r;
@@ -229,6 +232,11 @@ gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, bool re
     uint32_t *pk = ptr<uint32_t>(c->pk), *pv = ptr<uint32_t>(c->pv), *pk_alt = ptr<uint32_t>(c->pk_alt);
     uint2 *rect = ptr<uint2>(c->rect);
     uint32_t *tk = ptr<uint32_t>(c->keys), *tk_alt = ptr<uint32_t>(c->keys_alt), *v_alt = ptr<uint32_t>(c->vals_alt);
+    // a training step culls footprint tiles against the alpha ellipse; gs_bin keeps whole rectangles
+    const float cull_alpha = rect_ready ? c->hp.alpha_min : 0.f;
+    uint4 *rm = cull_alpha > 0.f ? ptr<uint4>(c->rmask) : nullptr;
+    uint2 *keep = ptr<uint2>(c->kmask);
+    if (rm) launch_cull_tiles(vb, p, rect, ptr<uint32_t>(c->ntiles), cull_alpha, rm, st);
     // (1) the visible (view, Gaussian) pairs in depth order
     uint32_t *order = launch_depth_order(vb, p, rect_ready, rect, ptr<uint32_t>(c->ntiles), pk, pv, pk_alt,
                                          ptr<uint32_t>(c->pv_alt), ptr<uint32_t>(c->offsets), n_vis, total,
@@ -237,12 +245,12 @@ gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, bool re
     // buffers), counts scanned into fragment offsets
     uint32_t *counts = order == pv ? pk : pv;
     uint32_t *rx = order == pv ? ptr<uint32_t>(c->pv_alt) : pk, *ry = pk_alt;
-    launch_gather_counts(order, rect, n, n_vis, counts, rx, ry, st);
+    launch_gather_counts(order, rect, ptr<uint32_t>(c->ntiles), rm, n, n_vis, counts, rx, ry, keep, st);
     launch_exclusive_scan(counts, ptr<uint32_t>(c->offsets), n, total, c->scan_tmp.p, st, n_vis);
     mark(c, st, 2);
     // (3) fragments pair by pair in depth order, into the buffers the tile sort ends in
-    launch_emit_keys(vb, p.N, n_vis, order, rx, ry, ptr<uint32_t>(c->offsets), even ? tk : tk_alt,
-                     even ? vals : v_alt, capacity, total, c->status, count, st);
+    launch_emit_keys(vb, p.N, n_vis, order, rx, ry, keep, ptr<uint32_t>(c->offsets), even ? tk : tk_alt,
+                     even ? vals : v_alt, capacity, total, c->status, count, cull_alpha, st);
     mark(c, st, 3);
     // (4) stable sort on the tile id
     launch_sort_fragments(even ? tk : tk_alt, even ? vals : v_alt, even ? tk_alt : tk, even ? v_alt : vals, capacity,
@@ -264,7 +272,8 @@ gs_status ensure_iter(gs_ctx *c, int64_t N, const ViewBatch &vb, uint64_t cap)
     if ((r = ensure(c, c->xy, 8 * n)) || (r = ensure(c, c->conic_o, 16 * n)) || (r = ensure(c, c->rgb_d, 16 * n)) ||
         (r = ensure(c, c->radius, 4 * n)) || (r = ensure(c, c->ntiles, 4 * n)) || (r = ensure(c, c->offsets, 4 * n)) ||
         (r = ensure(c, c->pk, 4 * n)) || (r = ensure(c, c->pv, 4 * n)) || (r = ensure(c, c->pk_alt, 4 * n)) ||
-        (r = ensure(c, c->pv_alt, 4 * n)) || (r = ensure(c, c->rect, 8 * n)) ||
+        (r = ensure(c, c->pv_alt, 4 * n)) || (r = ensure(c, c->rect, 8 * n)) || (r = ensure(c, c->kmask, 8 * n)) ||
+        (r = ensure(c, c->rmask, 16 * n)) ||
         (r = ensure(c, c->scan_tmp, scan_temp_bytes((int64_t)n))) || (r = ensure(c, c->total, 64)) ||
         (r = ensure(c, c->keys_alt, 4 * (size_t)(cap ? cap : 1))) || (r = ensure(c, c->vals_alt, 4 * (size_t)(cap ? cap : 1))) ||
         (r = ensure(c, c->sort_tmp, sort_temp_bytes((uint64_t)n, cap))))
@@ -435,7 +444,7 @@ gs_status gs_destroy(gs_ctx *c)
 {
     if (!c) return GS_ERR_INVALID_ARG;
     DBuf *bufs[] = {&c->ntiles, &c->offsets, &c->scan_tmp, &c->total, &c->keys_alt, &c->vals_alt, &c->sort_tmp,
-                    &c->pk, &c->pv, &c->pk_alt, &c->pv_alt, &c->rect,
+                    &c->pk, &c->pv, &c->pk_alt, &c->pv_alt, &c->rect, &c->kmask, &c->rmask,
                     &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_proj, &c->keys,
                     &c->vals, &c->ranges, &c->count, &c->img, &c->dimg, &c->T_final, &c->n_contrib, &c->maps,
                     &c->acc};
@@ -520,7 +529,7 @@ gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *ca
         pix += (size_t)cams[v].W * cams[v].H;
     }
     const size_t n = (size_t)B * (size_t)N;
-    size_t s = n * (8 + 16 + 16 + 4 + 4 + 4 + 16 + 8 + 48) + frag_capacity * (8 * 2) +
+    size_t s = n * (8 + 16 + 16 + 4 + 4 + 4 + 16 + 8 + 8 + 16 + 48) + frag_capacity * (8 * 2) +
                sort_temp_bytes((uint64_t)n, frag_capacity) +
                scan_temp_bytes((int64_t)n) + tiles * 8 + pix * (4 + 4 + 12 + 12 + 36) + 4096;
     *bytes = s;

@@ -118,6 +118,70 @@ size_t scan_temp_bytes(int64_t n);
 void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *total, void *temp,
                            cudaStream_t st, const uint32_t *n_dev = nullptr, bool nonzero = false);
 
+// Can alpha = o exp(-f/2), f(d) = a dx^2 + 2 b dx dy + c dy^2 (d = pixel -
+// (u, v)), reach alpha_min anywhere in the pixel-centre box [x0, x1] x
+// [y0, y1]?  f is convex with its minimum 0 at the centre, so for a centre
+// outside the box the minimum lies on an edge that faces it (x = clamp(u) or
+// y = clamp(v)); along such an edge f is a parabola, minimised at the clamp
+// of its vertex and evaluated as c (dy - dy*)^2 + (det / c) dx^2 (non-negative
+// terms, no cancellation; det by Kahan's form).  The acceptance bound
+// L = 2 ln(o / alpha_min) is widened by 0.1 %, 1e-6 x the conic's condition
+// number and 1e-4 -- beyond the rounding of the per-pixel exponent and of the
+// approximate reciprocals here -- so the test never drops a Gaussian the
+// per-pixel test would blend.  A non-positive-definite conic is kept.  Every
+// operation is explicitly rounded.
+// The per-Gaussian part of the test: (threshold, 1/a, 1/c, det);
+// threshold -1: alpha never reaches alpha_min; +inf: not positive definite.
+__device__ __forceinline__ float4 ellipse_terms(const float4 &co, float alpha_min)
+{
+    if (!(co.w > alpha_min)) return make_float4(-1.f, 0.f, 0.f, 0.f);
+    const float a = co.x, b = co.y, c = co.z;
+    const float bb = __fmul_rn(b, b);
+    const float det = __fadd_rn(__fmaf_rn(a, c, -bb), __fmaf_rn(-b, b, bb));
+    if (!(det > 0.f && a > 0.f && c > 0.f)) return make_float4(INFINITY, 0.f, 0.f, 0.f);
+    const float L = __fmul_rn(2.f, __logf(__fdividef(co.w, alpha_min)));
+    const float tr = __fmul_rn(0.5f, __fadd_rn(a, c)), hd = __fmul_rn(0.5f, __fsub_rn(a, c));
+    const float r = sqrtf(__fmaf_rn(hd, hd, bb));
+    const float kappa = __fdividef(__fadd_rn(tr, r), fmaxf(__fsub_rn(tr, r), 1e-30f));   // condition number
+    return make_float4(__fmaf_rn(L, __fmaf_rn(1e-6f, kappa, 1.001f), 1e-4f), __fdividef(1.f, a),
+                       __fdividef(1.f, c), det);
+}
+
+// The per-box part, with t = ellipse_terms(co) and (a, b, c) = co.xyz.
+__device__ __forceinline__ bool ellipse_terms_box_hits(const float4 &t, float a, float b, float c, float u, float v,
+                                                       float x0, float x1, float y0, float y1)
+{
+    if (!(t.x >= 0.f)) return false;                       // never reaches alpha_min
+    if (t.x == INFINITY) return true;                      // not positive definite: keep
+    const float ex = fminf(fmaxf(u, x0), x1), ey = fminf(fmaxf(v, y0), y1);
+    if (ex == u && ey == v) return true;                   // centre inside the box
+    float fmin = INFINITY;
+    if (ex != u) {                                         // edge x = ex
+        const float dx = __fsub_rn(ex, u);
+        const float dys = __fmul_rn(__fmul_rn(-b, dx), t.z);
+        const float s = __fsub_rn(fminf(fmaxf(dys, __fsub_rn(y0, v)), __fsub_rn(y1, v)), dys);
+        fmin = __fmaf_rn(__fmul_rn(c, s), s, __fmul_rn(__fmul_rn(t.w, t.z), __fmul_rn(dx, dx)));
+    }
+    if (ey != v) {                                         // edge y = ey
+        const float dy = __fsub_rn(ey, v);
+        const float dxs = __fmul_rn(__fmul_rn(-b, dy), t.y);
+        const float s = __fsub_rn(fminf(fmaxf(dxs, __fsub_rn(x0, u)), __fsub_rn(x1, u)), dxs);
+        fmin = fminf(fmin, __fmaf_rn(__fmul_rn(a, s), s, __fmul_rn(__fmul_rn(t.w, t.y), __fmul_rn(dy, dy))));
+    }
+    return fmin <= t.x;
+}
+
+__device__ __forceinline__ bool ellipse_box_hits(const float4 &co, float u, float v, float alpha_min, float x0,
+                                                 float x1, float y0, float y1)
+{
+    return ellipse_terms_box_hits(ellipse_terms(co, alpha_min), co.x, co.y, co.z, u, v, x0, x1, y0, y1);
+}
+
+// Footprint rectangles of at most this many tiles are culled tile by tile
+// against the alpha ellipse in a training step (one bit per tile of the
+// rectangle); larger ones keep every tile.
+constexpr uint32_t TILE_CULL_MAX_AREA = 64;
+
 // A footprint's tile rectangle packed as {x0 | x1 << 16, y0 | y1 << 16}
 // (tile coordinates fit 16 bits); (1, 0) is the empty rectangle.
 __host__ __device__ __forceinline__ uint2 pack_rect(uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1)
@@ -142,14 +206,23 @@ uint32_t *launch_depth_order(const ViewBatch &vb, const ProjView &p, bool rect_r
                              uint32_t *keys, uint32_t *order, uint32_t *keys_alt, uint32_t *order_alt,
                              uint32_t *pos, uint32_t *n_vis, unsigned long long *total, void *scan_tmp,
                              void *sort_tmp, DevStatus *status, cudaStream_t st);
-// counts / rx / ry: tile count and the two rectangle words of pair order[j],
-// j < *n_vis
-void launch_gather_counts(const uint32_t *order, const uint2 *rect, int64_t n, const uint32_t *n_vis,
-                          uint32_t *counts, uint32_t *rx, uint32_t *ry, cudaStream_t st);
+// Training steps cull footprint tiles against the alpha >= cull_alpha ellipse
+// (rectangles of at most TILE_CULL_MAX_AREA tiles; ellipse_box_hits on each
+// tile's pixel-centre box): rm[i] = (rectangle words, kept-tile bits, row-major
+// in the rectangle), area[i] = the kept count.
+void launch_cull_tiles(const ViewBatch &vb, const ProjView &p, const uint2 *rect, uint32_t *area, float cull_alpha,
+                       uint4 *rm, cudaStream_t st);
+// For pair order[j], j < *n_vis: rx / ry its rectangle words and counts its
+// tile count; with rm (culled) also keep[j] = its kept-tile bits, else counts
+// come from area[].
+void launch_gather_counts(const uint32_t *order, const uint2 *rect, const uint32_t *area, const uint4 *rm, int64_t n,
+                          const uint32_t *n_vis, uint32_t *counts, uint32_t *rx, uint32_t *ry, uint2 *keep,
+                          cudaStream_t st);
+// keep / cull_alpha: as given to launch_gather_counts.
 void launch_emit_keys(const ViewBatch &vb, int64_t N, const uint32_t *n_vis, const uint32_t *order,
-                      const uint32_t *rx, const uint32_t *ry, const uint32_t *offsets, uint32_t *keys, uint32_t *vals,
-                      uint64_t capacity, const unsigned long long *total, DevStatus *status, uint32_t *count_out,
-                      cudaStream_t st);
+                      const uint32_t *rx, const uint32_t *ry, const uint2 *keep, const uint32_t *offsets,
+                      uint32_t *keys, uint32_t *vals, uint64_t capacity, const unsigned long long *total,
+                      DevStatus *status, uint32_t *count_out, float cull_alpha, cudaStream_t st);
 
 // Sort scratch for the pair sort of `pairs` keys and the fragment sort of
 // `fragments` keys (one buffer serves both, one after the other).

@@ -69,48 +69,6 @@ __device__ __forceinline__ float exponent_cut(float o, float alpha_min)
     return o > alpha_min ? __log2f(__fdividef(alpha_min, o)) : 1.f;
 }
 
-// Can alpha reach alpha_min anywhere in the pixel-centre box [x0, x1] x
-// [y0, y1]?  That is: does min over the box of f(d) = a dx^2 + 2 b dx dy +
-// c dy^2 (d = pixel - centre) stay within L = 2 ln(o / alpha_min)?  f is
-// convex with its minimum 0 at the centre, so for a centre outside the box
-// the minimum lies on an edge that faces the centre (x = clamp(u) or y =
-// clamp(v)).  Along such an edge f is a parabola, minimised at the clamp of
-// its vertex and evaluated as c (dy - dy*)^2 + (det / c) dx^2 (a sum of
-// non-negative terms: no cancellation); the determinant uses Kahan's form.
-// The acceptance bound is widened (0.1 % + 1e-6 x the conic's condition
-// number, + 1e-4) beyond the rounding error of the per-pixel exponent, so
-// the test never drops a Gaussian the per-pixel test would blend.  A
-// non-positive-definite conic keeps the Gaussian.
-__device__ __forceinline__ bool alpha_box_hits(const float4 &co, float u, float v, float alpha_min, float x0,
-                                               float x1, float y0, float y1)
-{
-    if (!(co.w > alpha_min)) return false;                 // never reaches alpha_min
-    const float a = co.x, b = co.y, c = co.z;
-    const float bb = b * b;
-    const float det = __fmaf_rn(a, c, -bb) + __fmaf_rn(-b, b, bb);
-    if (!(det > 0.f && a > 0.f && c > 0.f)) return true;
-    const float ex = fminf(fmaxf(u, x0), x1), ey = fminf(fmaxf(v, y0), y1);
-    if (ex == u && ey == v) return true;                   // centre inside the box
-    // approximate reciprocals (a few ulp): the threshold's 0.1 % widening covers them
-    float fmin = INFINITY;
-    if (ex != u) {                                         // edge x = ex
-        const float dx = ex - u, ic = __fdividef(1.f, c);
-        const float dys = -b * dx * ic;
-        const float t = fminf(fmaxf(dys, y0 - v), y1 - v) - dys;
-        fmin = c * t * t + det * ic * (dx * dx);
-    }
-    if (ey != v) {                                         // edge y = ey
-        const float dy = ey - v, ia = __fdividef(1.f, a);
-        const float dxs = -b * dy * ia;
-        const float t = fminf(fmaxf(dxs, x0 - u), x1 - u) - dxs;
-        fmin = fminf(fmin, a * t * t + det * ia * (dy * dy));
-    }
-    const float L = 2.f * __logf(__fdividef(co.w, alpha_min));
-    const float tr = 0.5f * (a + c), r = sqrtf(0.25f * (a - c) * (a - c) + bb);
-    const float kappa = __fdividef(tr + r, fmaxf(tr - r, 1e-30f));   // condition number of the conic
-    return fmin <= L * (1.001f + 1e-6f * kappa) + 1e-4f;
-}
-
 __device__ __forceinline__ int find_view(const ViewBatch &vb, uint32_t tile_id)
 {
     int v = 0;
@@ -259,7 +217,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, Pr
         const Entry e = nxt;
         const uint32_t j = base + lane;
         if (base + 32 < rg.y) nxt = fetch_entry(p, vals, vbase, (int64_t)j + 32, j + 32 < rg.y);
-        const bool hit = e.ok && alpha_box_hits(e.co, e.xy.x, e.xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
+        const bool hit = e.ok && ellipse_box_hits(e.co, e.xy.x, e.xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
         const uint32_t bal = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             const int slot = n + __popc(bal & lt);
@@ -396,7 +354,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
         const Entry e = nxt;
         const int64_t j = hi - 1 - lane;
         if (hi - 32 > (int64_t)rg.x) nxt = fetch_entry(p, vals, vbase, j - 32, j - 32 >= (int64_t)rg.x);
-        const bool hit = e.ok && alpha_box_hits(e.co, e.xy.x, e.xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
+        const bool hit = e.ok && ellipse_box_hits(e.co, e.xy.x, e.xy.y, bp.alpha_min, ps.bx0, ps.bx1, ps.by0, ps.by1);
         const uint32_t bal = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             const int slot = n + __popc(bal & lt);
