@@ -382,6 +382,27 @@ def test_batched_render_equals_single_view(eng):
         assert torch.equal(mixed[b], alone), b
 
 
+@pytest.mark.parametrize("tile,ppt", [(16, 1), (16, 2), (8, 2), (32, 4)])
+def test_tile_culling_leaves_images_unchanged(eng, tile, ppt):
+    """gs_render bins with footprint tiles culled against the alpha ellipse;
+    gs_preprocess + gs_bin + gs_render_fwd keep whole rectangles.  Every
+    warp's refill rejects the culled tiles' entries anyway, so the images and
+    final transmittances must be identical bit for bit, while the culled path
+    holds fewer fragments."""
+    sc, rng = synth.aerial_scene(80_000, n_clusters=16, seed=9)
+    cams = synth.ring_cameras(rng, 3, (20.0, 120.0), W=333, H=187)
+    ctx = eng.Context(tile=tile, px_per_thread=ppt)
+    ds = eng.DeviceScene.from_host(sc)
+    culled = ctx.render(ds, cams, check=True)
+    F_culled = ctx.counters()["F"]
+    proj = ctx.preprocess(ds, cams)
+    bins = ctx.bin(proj, cams)
+    img, T, nc = ctx.render_fwd(proj, bins, cams)
+    for b in range(len(cams)):
+        assert torch.equal(culled[b], img[b]), b
+    assert bins.F > F_culled > 0
+
+
 def test_batched_train_gradient_is_mean_of_views(eng):
     sc, rng = synth.aerial_scene(50_000, n_clusters=16, seed=5)
     cams = synth.ring_cameras(rng, 4, (20.0, 120.0), W=256, H=144)
