@@ -144,8 +144,9 @@ class OracleSample:
                 f"views/s = crop fraction {self.frac:.4f} / step time")
 
 
-# pixels whose FP64 threshold decision sits within this relative margin are
-# flagged (float32 may decide them the other way); the tests derive it
+# pixels whose FP64 threshold decision sits within this relative margin, or
+# that a Gaussian of borderline tile membership reaches, are flagged (float32
+# may decide them the other way); the same rule as the parity tests
 PARITY_MARGIN = 1e-3
 PARITY_TOL = 1e-4
 
@@ -153,26 +154,23 @@ PARITY_TOL = 1e-4
 def parity_gate(ctx, P, cams, side=256):
     """The metric's gate: at a frozen snapshot of the trained parameters, the
     GPU image of view 0 (gs_render) against the FP64 oracle on a tile-aligned
-    crop, rendered from the Gaussians whose footprint meets it."""
+    window of that view (the oracle transforms with the view's own camera and
+    composites only the window's pixels)."""
     import oracle
     cam = cams[0]
+    t = ctx.tile
     gpu = ctx.render(P, [cam], check=True)[0].cpu().numpy()
     snap = synth.Scene(P.mo.cpu().numpy(), P.ls.cpu().numpy(), P.q.cpu().numpy(), P.sh.cpu().numpy())
     w, h = min(side, cam.W) // 16 * 16, min(side, cam.H) // 16 * 16
-    x0, y0 = ((cam.W - w) // 2) // 16 * 16, ((cam.H - h) // 2) // 16 * 16
-    pr = oracle.project(snap, cam)
-    u, v, r = pr["xy"][:, 0], pr["xy"][:, 1], pr["radius"]
-    idx = np.nonzero((r > 0) & (u + r >= x0) & (u - r < x0 + w) & (v + r >= y0) & (v - r < y0 + h))[0]
-    sub = synth.Scene(snap.mo[idx].copy(), snap.ls[idx].copy(), snap.q[idx].copy(), snap.sh[:, idx].copy())
-    ccam = synth.Camera(R=cam.R, t=cam.t, fx=cam.fx, fy=cam.fy, cx=np.float32(cam.cx - x0),
-                        cy=np.float32(cam.cy - y0), W=w, H=h, near=cam.near)
-    ref = oracle.render(sub, ccam)
-    ok = ref["margin"] > PARITY_MARGIN
-    err = np.abs(gpu[:, y0:y0 + h, x0:x0 + w] - ref["img"])[:, ok]
+    x0, y0 = ((cam.W - w) // 2) // t * t, ((cam.H - h) // 2) // t * t
+    ref = oracle.render_window(snap, cam, (x0, y0, w, h), t)
+    flag, nborder = oracle.fp32_flags(ref, w, h, t, PARITY_MARGIN)
+    err = np.abs(gpu[:, y0:y0 + h, x0:x0 + w] - ref["img"])[:, ~flag]
     max_err = float(err.max()) if err.size else 0.0
     return {"max_abs_err": max_err, "tol": PARITY_TOL, "pass": bool(max_err <= PARITY_TOL),
-            "pixels": int(w * h), "flagged_frac": float(1.0 - ok.mean()),
-            "crop": f"{w}x{h} at ({x0},{y0}) of view 0, {len(idx)} Gaussians, parameters after the timed steps"}
+            "pixels": int(w * h), "flagged_frac": float(flag.mean()),
+            "window": f"{w}x{h} at ({x0},{y0}) of view 0, {len(ref['index'])} Gaussians, tile {t}, "
+                      f"parameters after the timed steps"}
 
 
 def pick_crop(sc, cams, tg, lr6, budget_s):

@@ -199,6 +199,77 @@ def render(scene, cam, tile=16, **kw):
     return out
 
 
+def render_window(scene, cam, window, tile=16, **kw):
+    """Forward of one view over a tile-aligned pixel window (x0, y0, w, h):
+    the same image as ``render`` on those pixels, for views too large to
+    composite whole.
+
+    The transformation runs with the view's own camera, so that the off-axis
+    clamp of the EWA Jacobian (1.3 times the half field of view of the whole
+    view) is the view's; a smaller camera covering only the window would clamp
+    differently.  Lists hold the Gaussians whose tile rectangle meets the
+    window's tiles, in the order ``render`` gives them (float32 depth, then
+    index).  The returned ``proj`` is restricted to those Gaussians (``index``
+    gives their positions in the scene) with centres in window coordinates."""
+    x0, y0, w, h = (int(a) for a in window)
+    if x0 % tile or y0 % tile or w < 1 or h < 1 or x0 + w > cam.W or y0 + h > cam.H:
+        raise ValueError("window must start on the tile grid and lie inside the view")
+    pr = project(scene, cam, tile)
+    tx0, ty0 = x0 // tile, y0 // tile
+    TXw, TYw = (w + tile - 1) // tile, (h + tile - 1) // tile
+    r = pr["rect"]
+    keep = (pr["vis"] > 0) & (r[:, 1] >= tx0) & (r[:, 0] < tx0 + TXw) & (r[:, 3] >= ty0) & (r[:, 2] < ty0 + TYw)
+    idx = np.nonzero(keep)[0]
+    sub = {k: v[idx].copy() for k, v in pr.items()}
+    rect = sub["rect"]
+    rect[:, 0] = np.maximum(rect[:, 0] - tx0, 0)
+    rect[:, 1] = np.minimum(rect[:, 1] - tx0, TXw - 1)
+    rect[:, 2] = np.maximum(rect[:, 2] - ty0, 0)
+    rect[:, 3] = np.minimum(rect[:, 3] - ty0, TYw - 1)
+    sub["xy"] = sub["xy"] - np.array([x0, y0], np.float64)
+    toff, gidx = bin_view(rect, sub["vis"], sub["depth"].astype(np.float32), w, h, tile)
+    out = render_fwd(w, h, tile, toff, gidx, sub["xy"], sub["conic_o"], sub["rgb"], **kw)
+    out.update(proj=sub, toff=toff, gidx=gidx, index=idx)
+    return out
+
+
+def fp32_flags(fw, W, H, tile=16, margin=1e-3):
+    """Pixels of a forward (``render`` or ``render_window`` output) whose value
+    float32 arithmetic may legitimately decide otherwise: pixels within the
+    relative ``margin`` of an alpha, opacity-clamp or transmittance threshold
+    (the compositor's own record), and pixels that a Gaussian with borderline
+    tile membership (its 3-sigma radius within rounding of an integer, or a
+    rectangle edge within rounding of a tile line) could reach at half the
+    alpha cut, in the outermost tile rows and columns of its rectangle.
+    Returns (flag [H, W] bool, number of borderline Gaussians)."""
+    pr = fw["proj"]
+    bad = fw["margin"] <= margin
+    e = pr["ext3"]
+    border = (pr["radius"] > 0) & (np.abs(e - np.round(e)) < 1e-4)
+    for k in range(2):
+        for sgn in (-1, 1):
+            edge = (pr["xy"][:, k] + sgn * np.maximum(pr["radius"], np.ceil(e))) / tile
+            border |= (np.abs(edge - np.round(edge)) * tile < 1e-3) & (e > 0)
+    TX = (W + tile - 1) // tile
+    TY = (H + tile - 1) // tile
+    tiles_px = np.zeros((H, W), bool)
+    for g in np.nonzero(border)[0]:
+        r = max(int(math.ceil(e[g])), 0)
+        x0, x1 = int((pr["xy"][g, 0] - r) // tile), int((pr["xy"][g, 0] + r) // tile)
+        y0, y1 = int((pr["xy"][g, 1] - r) // tile), int((pr["xy"][g, 1] + r) // tile)
+        for ty in range(max(0, y0 - 1), min(TY - 1, y1 + 1) + 1):
+            for tx in range(max(0, x0 - 1), min(TX - 1, x1 + 1) + 1):
+                if tx <= x0 or tx >= x1 or ty <= y0 or ty >= y1:
+                    ys = np.arange(ty * tile, min(H, (ty + 1) * tile)) + 0.5 - pr["xy"][g, 1]
+                    xs = np.arange(tx * tile, min(W, (tx + 1) * tile)) + 0.5 - pr["xy"][g, 0]
+                    DX, DY = np.meshgrid(xs, ys)
+                    a, b, c, o = pr["conic_o"][g]
+                    reach = o * np.exp(-0.5 * (a * DX * DX + c * DY * DY) - b * DX * DY) >= 0.5 / 255
+                    view = tiles_px[ty * tile:ty * tile + DX.shape[0], tx * tile:tx * tile + DX.shape[1]]
+                    view |= reach
+    return bad | tiles_px, int(border.sum())
+
+
 def grad_view(scene, cam, dimg, tile=16, **kw):
     """dL/dparams [N, 60] of one view for an upstream image gradient."""
     fw = render(scene, cam, tile, **kw)

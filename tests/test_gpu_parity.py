@@ -11,7 +11,6 @@ the exponent's slope is at most sqrt(1/0.3) sqrt(2 ln 255) ~ 6.1 per pixel
 carry up to 6e-5 px of rounding, i.e. ~3.7e-4 relative alpha error; twice
 that for the projection's own rounding stays under 1e-3.
 """
-import math
 
 import numpy as np
 import pytest
@@ -258,38 +257,9 @@ def test_adam_stage(eng, oracle, Bv, step):
 # ------------------------------------------------------------------ end to end
 
 def _flags_from_oracle(oracle, fw, cam, tile=16):
-    """Pixels whose result FP32 may legitimately decide differently: threshold
-    margins, and tiles touched by a Gaussian whose radius or rectangle edge sits
-    within rounding of a boundary (borderline membership)."""
-    pr = fw["proj"]
-    bad = fw["margin"] <= MARGIN
-    e = pr["ext3"]
-    border = (pr["radius"] > 0) & (np.abs(e - np.round(e)) < 1e-4)
-    for k in range(2):
-        for sgn in (-1, 1):
-            edge = (pr["xy"][:, k] + sgn * np.maximum(pr["radius"], np.ceil(e))) / tile
-            border |= (np.abs(edge - np.round(edge)) * tile < 1e-3) & (e > 0)
-    TX = (cam.W + tile - 1) // tile
-    TY = (cam.H + tile - 1) // tile
-    tiles_px = np.zeros((cam.H, cam.W), bool)
-    for g in np.nonzero(border)[0]:
-        # membership can only change in the outermost tile rows / columns of the
-        # rectangle (radius off by one, or an edge on the other side of a tile line)
-        r = max(int(math.ceil(e[g])), 0)
-        x0, x1 = int((pr["xy"][g, 0] - r) // tile), int((pr["xy"][g, 0] + r) // tile)
-        y0, y1 = int((pr["xy"][g, 1] - r) // tile), int((pr["xy"][g, 1] + r) // tile)
-        for ty in range(max(0, y0 - 1), min(TY - 1, y1 + 1) + 1):
-            for tx in range(max(0, x0 - 1), min(TX - 1, x1 + 1) + 1):
-                if tx <= x0 or tx >= x1 or ty <= y0 or ty >= y1:
-                    # only pixels where this Gaussian could reach half the alpha cut
-                    ys = np.arange(ty * tile, min(cam.H, (ty + 1) * tile)) + 0.5 - pr["xy"][g, 1]
-                    xs = np.arange(tx * tile, min(cam.W, (tx + 1) * tile)) + 0.5 - pr["xy"][g, 0]
-                    DX, DY = np.meshgrid(xs, ys)
-                    a, b, c, o = pr["conic_o"][g]
-                    reach = o * np.exp(-0.5 * (a * DX * DX + c * DY * DY) - b * DX * DY) >= 0.5 / 255
-                    sub = tiles_px[ty * tile:ty * tile + DX.shape[0], tx * tile:tx * tile + DX.shape[1]]
-                    sub |= reach
-    return bad | tiles_px, int(border.sum())
+    """Pixels whose result FP32 may legitimately decide differently (threshold
+    margins and borderline tile membership; ``oracle.fp32_flags``)."""
+    return oracle.fp32_flags(fw, cam.W, cam.H, tile, MARGIN)
 
 
 def test_end_to_end_c0_autograd(eng, oracle):

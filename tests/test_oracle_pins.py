@@ -301,6 +301,36 @@ def test_permutation_invariance(oracle):
     assert np.abs(a - b).max() < 1e-13
 
 
+@pytest.mark.parametrize("tile,window", [(16, (32, 16, 48, 32)), (8, (8, 40, 40, 24)), (32, (64, 0, 32, 64))])
+def test_window_render_equals_whole_view(oracle, tile, window):
+    """A window of a view composited alone equals the same pixels of the whole
+    view, including Gaussians outside the window whose Jacobian is clamped at
+    the whole view's field of view; a camera cut down to the window would clamp
+    them at its own narrower field of view and give another image."""
+    sc = synth.tiny_scene(400, seed=3, spread=1.6, log_s=(-2.5, -0.3))
+    cam = synth.test_camera(W=128, H=96)
+    x0, y0, w, h = window
+    full = oracle.render(sc, cam, tile)
+    win = oracle.render_window(sc, cam, window, tile)
+    ref = full["img"][:, y0:y0 + h, x0:x0 + w]
+    assert np.abs(win["img"] - ref).max() < 1e-12
+    assert np.array_equal(win["n_contrib"], full["n_contrib"][y0:y0 + h, x0:x0 + w])
+    assert np.allclose(win["margin"], full["margin"][y0:y0 + h, x0:x0 + w], rtol=1e-9, atol=1e-12)
+    assert win["n_contrib"].max() > 3
+    cut = synth.Camera(R=cam.R, t=cam.t, fx=cam.fx, fy=cam.fy, cx=np.float32(cam.cx - x0),
+                       cy=np.float32(cam.cy - y0), W=w, H=h, near=cam.near)
+    assert np.abs(oracle.render(sc, cut, tile)["img"] - ref).max() > 1e-6
+
+
+def test_window_must_start_on_the_tile_grid(oracle):
+    sc = synth.tiny_scene(10, seed=0)
+    cam = synth.test_camera(W=64, H=48)
+    with pytest.raises(ValueError):
+        oracle.render_window(sc, cam, (8, 0, 32, 32), 16)
+    with pytest.raises(ValueError):
+        oracle.render_window(sc, cam, (48, 0, 32, 32), 16)
+
+
 # ---------------------------------------------------------------- finite differences
 
 def _fd_ok_scene(oracle, seed, N, cam, dimg):
