@@ -21,9 +21,11 @@
 // T_final (no per-fragment state is stored), accumulates per Gaussian the
 // moments of dpow = alpha dL/dalpha (M, Mx, My, Mxx, Mxy, Myy; the mean,
 // conic and opacity gradients are linear in them) and the colour gradient,
-// reduces these nine values over the warp with a reduce-scatter (17 shuffles)
-// and adds them as three float4 atomics per (warp, Gaussian).  The moments
-// become gradients once per (view, Gaussian) afterwards (moments_to_grads).
+// and adds these nine values to the Gaussian as three float4 atomics: from
+// each contributing lane directly when few lanes contribute, after a
+// reduce-scatter over the warp (17 shuffles) or a fold of the upper half-warp
+// when many do (add_sums, flush_one).  The moments become gradients once per
+// (view, Gaussian) afterwards (moments_to_grads).
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -113,6 +115,24 @@ __device__ __forceinline__ void flush_one(const GradView &gv, int64_t idx, const
         atomicAdd(dst, make_float4(g0, g1, lane == 2 ? t : g2, 0.f));
     }
 }
+
+// One lane's own sums of an entry (moments in vv[0..5], colour sums in
+// vv[6], vv[7], b), added to entry idx as three float4 atomics.
+__device__ __forceinline__ void add_sums(const GradView &gv, int64_t idx, const float vv[8], float b)
+{
+    atomicAdd(&gv.d_xy_o[idx], make_float4(vv[0], vv[1], vv[2], 0.f));
+    atomicAdd(&gv.d_conic[idx], make_float4(vv[3], vv[4], vv[5], 0.f));
+    atomicAdd(&gv.d_rgb[idx], make_float4(vv[6], vv[7], b, 0.f));
+}
+
+// How an entry's sums leave the warp, by the number of contributing lanes
+// (measured on GB300 over the launch shapes the autotuner picks).  Float4
+// atomics from many lanes to one address are cheap next to the 17-shuffle
+// reduce-scatter until about 20 lanes contribute; with 4 pixels per thread,
+// folding the upper half-warp (9 shuffles) and adding from at most 16 lanes
+// beats both.
+constexpr int DIRECT_UP_TO = 20;   // 1 or 2 pixels per thread: lanes adding directly, else reduce-scatter
+constexpr int FOLD_ABOVE = 16;     // 4 pixels per thread: fold when more lanes contribute
 
 // Tile-local geometry of this thread's PPT pixels (one column, rows 4 apart)
 // and its warp's 8 x 4 PPT block.
@@ -418,17 +438,25 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
             const uint32_t ballot = __ballot_sync(0xffffffffu, any);
             if (ballot == 0u) continue;
             const int64_t idx = vbase + __float_as_uint(s_rgb[i].w);
-            if (__popc(ballot) == 1) {
-                // one contributing lane in this warp: no reduction needed
-                if (any) {
-                    atomicAdd(&gv.d_xy_o[idx], make_float4(vv[0], vv[1], vv[2], 0.f));
-                    atomicAdd(&gv.d_conic[idx], make_float4(vv[3], vv[4], vv[5], 0.f));
-                    atomicAdd(&gv.d_rgb[idx], make_float4(vv[6], vv[7], gbl, 0.f));
+            const int contributing = __popc(ballot);
+            if constexpr (PPT == 4) {
+                // fold the upper half-warp onto the lower one when it pays,
+                // then every contributing lane adds its own sums
+                if (contributing > FOLD_ABOVE) {
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) vv[m] += __shfl_down_sync(0xffffffffu, vv[m], 16);
+                    gbl += __shfl_down_sync(0xffffffffu, gbl, 16);
+                    any = lane < 16 && ((ballot >> lane) & 0x10001u) != 0u;
                 }
-                continue;
+                if (any) add_sums(gv, idx, vv, gbl);
+            } else {
+                if (contributing <= DIRECT_UP_TO) {
+                    if (any) add_sums(gv, idx, vv, gbl);
+                    continue;
+                }
+                const float cur[9] = {vv[0], vv[1], vv[2], vv[3], vv[4], vv[5], vv[6], vv[7], gbl};
+                flush_one(gv, idx, cur, lane);
             }
-            const float cur[9] = {vv[0], vv[1], vv[2], vv[3], vv[4], vv[5], vv[6], vv[7], gbl};
-            flush_one(gv, idx, cur, lane);
         }
         n = 0;
         __syncwarp();
