@@ -189,11 +189,11 @@ __device__ __forceinline__ Entry fetch_entry(const ProjView &p, const uint32_t *
     return e;
 }
 
-// Bytes of dynamic shared memory per CTA.
+// Bytes of dynamic shared memory per CTA: three float4 per staged entry.
 template <int TILE, int CH, int PPT>
 constexpr size_t smem_bytes()
 {
-    return (size_t)(TILE * TILE / (32 * PPT)) * CH * (3 * sizeof(float4) + sizeof(uint32_t));
+    return (size_t)(TILE * TILE / (32 * PPT)) * CH * 3 * sizeof(float4);
 }
 
 template <int TILE, int CH, int PPT>
@@ -204,10 +204,9 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, Pr
     constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4 *s_xyc = smem + warp * CH;              // u, v, exponent cut, -
+    float4 *s_xyc = smem + warp * CH;              // u, v, exponent cut, list position + 1 (bits)
     float4 *s_q = smem + (NW + warp) * CH;         // A, B, C, opacity
     float4 *s_rgb = smem + (2 * NW + warp) * CH;
-    uint32_t *s_pos = reinterpret_cast<uint32_t *>(smem + 3 * NW * CH) + warp * CH;
 
     const uint32_t tile_id = blockIdx.x;
     const int v = find_view(vb, tile_id);
@@ -242,10 +241,9 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, Pr
         if (hit) {
             const int slot = n + __popc(bal & lt);
             const float4 q = stage_q(e.co);
-            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_cut(q.w, bp.alpha_min), 0.f);
+            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_cut(q.w, bp.alpha_min), __uint_as_float(j - rg.x + 1u));
             s_q[slot] = q;
             s_rgb[slot] = p.rgb_d[vbase + e.g];
-            s_pos[slot] = j - rg.x;
         }
         n += __popc(bal);
         const bool last = base + 32 >= rg.y;
@@ -259,30 +257,56 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, Pr
                     const float4 xyc = s_xyc[i];
                     const float4 q = s_q[i];
                     const DxTerms dt = dx_terms(q, __fsub_rn(ps.fx, xyc.x));
-                    bool still = false;
-#pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        if (done[k]) continue;
-                        still = true;
-                        const float pw = power2(q, dt, __fsub_rn(ps.fy[k], xyc.y));
-                        if (!(pw >= xyc.z && pw <= 0.f)) continue;  // below the alpha cut, or power > 0
-                        const float alpha = fminf(bp.alpha_max, q.w * ex2(pw));
-                        if (alpha < bp.alpha_min) continue;
-                        const float Tn = T[k] * (1.f - alpha);
-                        if (Tn < bp.T_min) {
-                            done[k] = true;
-                            ne[k] = s_pos[i] + 1;
-                            continue;
+                    const uint32_t pos1 = __float_as_uint(xyc.w);
+                    if constexpr (PPT == 1) {
+                        // one pixel: without branches (a miss blends with weight 0)
+                        if (done[0]) break;
+                        const float pw = power2(q, dt, __fsub_rn(ps.fy[0], xyc.y));
+                        const float a0 = fminf(bp.alpha_max, q.w * ex2(pw));
+                        bool hit = pw >= xyc.z && pw <= 0.f && a0 >= bp.alpha_min;
+                        const float Tn = T[0] * (1.f - a0);
+                        if (hit && Tn < bp.T_min) {
+                            done[0] = true;
+                            ne[0] = pos1;
+                            hit = false;
                         }
                         const float4 rgb = s_rgb[i];
-                        const float w = alpha * T[k];
-                        C0[k] += rgb.x * w;
-                        C1[k] += rgb.y * w;
-                        C2[k] += rgb.z * w;
-                        T[k] = Tn;
-                        nc[k] = s_pos[i] + 1;
+                        const float w = hit ? a0 * T[0] : 0.f;
+                        C0[0] += rgb.x * w;
+                        C1[0] += rgb.y * w;
+                        C2[0] += rgb.z * w;
+                        T[0] = hit ? Tn : T[0];
+                        nc[0] = hit ? pos1 : nc[0];
+                    } else {
+                        float4 rgb_early;
+                        if constexpr (PPT == 4) rgb_early = s_rgb[i];    // four pixels: load ahead of the tests
+                        bool still = false;
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) {
+                            if (done[k]) continue;
+                            still = true;
+                            const float pw = power2(q, dt, __fsub_rn(ps.fy[k], xyc.y));
+                            if (!(pw >= xyc.z && pw <= 0.f)) continue;  // below the alpha cut, or power > 0
+                            const float alpha = fminf(bp.alpha_max, q.w * ex2(pw));
+                            if (alpha < bp.alpha_min) continue;
+                            const float Tn = T[k] * (1.f - alpha);
+                            if (Tn < bp.T_min) {
+                                done[k] = true;
+                                ne[k] = pos1;
+                                continue;
+                            }
+                            float4 rgb;
+                            if constexpr (PPT == 4) rgb = rgb_early;
+                            else rgb = s_rgb[i];
+                            const float w = alpha * T[k];
+                            C0[k] += rgb.x * w;
+                            C1[k] += rgb.y * w;
+                            C2[k] += rgb.z * w;
+                            T[k] = Tn;
+                            nc[k] = pos1;
+                        }
+                        if (!still) break;
                     }
-                    if (!still) break;
                 }
 #pragma unroll
                 for (int k = 0; k < PPT; ++k)
@@ -324,10 +348,9 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
     constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4 *s_xyc = smem + warp * CH;
+    float4 *s_xyc = smem + warp * CH;                // u, v, exponent cut, list position (bits)
     float4 *s_q = smem + (NW + warp) * CH;
     float4 *s_rgb = smem + (2 * NW + warp) * CH;    // r, g, b, Gaussian index (bits)
-    uint32_t *s_pos = reinterpret_cast<uint32_t *>(smem + 3 * NW * CH) + warp * CH;
 
     const uint32_t tile_id = blockIdx.x;
     const int v = find_view(vb, tile_id);
@@ -380,17 +403,17 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_bwd(ViewBatch vb, Pr
             const int slot = n + __popc(bal & lt);
             const float4 q = stage_q(e.co);
             const float4 rgbd = p.rgb_d[vbase + e.g];
-            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_cut(q.w, bp.alpha_min), 0.f);
+            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_cut(q.w, bp.alpha_min),
+                                      __uint_as_float((uint32_t)(j - rg.x)));
             s_q[slot] = q;
             s_rgb[slot] = make_float4(rgbd.x, rgbd.y, rgbd.z, __uint_as_float(e.g));
-            s_pos[slot] = (uint32_t)(j - rg.x);
         }
         n += __popc(bal);
         if (n <= CH - 32 && hi - 32 > (int64_t)rg.x) continue;
         __syncwarp();
         for (int i = 0; i < n; ++i) {
-            const uint32_t rel = s_pos[i];
             const float4 xyc = s_xyc[i];
+            const uint32_t rel = __float_as_uint(xyc.w);
             const float4 q = s_q[i];
             const float dx = __fsub_rn(ps.fx, xyc.x);
             const DxTerms dt = dx_terms(q, dx);
