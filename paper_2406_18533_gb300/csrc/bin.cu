@@ -321,6 +321,28 @@ __global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, co
 
 // ---------------------------------------------------------------- K3 emit
 
+// Position of the k-th (from 0) set bit of m; m has more than k set bits.
+__device__ __forceinline__ uint32_t select_bit32(uint32_t m, uint32_t k)
+{
+    uint32_t pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const uint32_t c = (uint32_t)__popc(m & ((1u << w) - 1u));   // set bits in the low w
+        const bool up = k >= c;
+        k = up ? k - c : k;
+        m = up ? m >> w : m;
+        pos += up ? (uint32_t)w : 0u;
+    }
+    return pos;
+}
+
+// The same for the 64-bit mask (hi:lo).
+__device__ __forceinline__ uint32_t select_bit64(uint32_t lo, uint32_t hi, uint32_t k)
+{
+    const uint32_t c = (uint32_t)__popc(lo);
+    return k < c ? select_bit32(lo, k) : 32u + select_bit32(hi, k - c);
+}
+
 // Emits the fragments of pair order[j] at offsets[j]: key = global tile id,
 // value = Gaussian index.  Visiting the pairs in depth order puts every
 // tile's fragments in (depth, index) order, so a stable sort on the tile id
@@ -339,7 +361,6 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
     const int64_t nb = (int64_t)vb.B * N;
     const int64_t n = (int64_t)*n_vis < nb ? (int64_t)*n_vis : nb;   // pairs in depth order
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t j0 = j - lane;                 // the warp's first pair
     const unsigned long long F = *total;
@@ -380,17 +401,19 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
             area = 0u;
         }
     }
-    // the lanes' rectangles laid end to end: exclusive prefix of their areas
-    uint32_t incl = area;
+    // the lanes' kept tiles laid end to end: a whole rectangle (mask all ones),
+    // or the set bits of a culled one's mask (bits past its area are clear)
+    const bool whole = (mlo & mhi) == 0xffffffffu;
+    const uint32_t kept = whole ? area : (uint32_t)(__popc(mlo) + __popc(mhi));
+    uint32_t incl = kept;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
-    const uint32_t rel = incl - area;            // lanes past n: rel = span, never matched
+    const uint32_t rel = incl - kept;            // lanes past n: rel = span, never matched
     const uint32_t span = __shfl_sync(0xffffffffu, incl, 31);
     const uint32_t base = __shfl_sync(0xffffffffu, start, 0);
-    uint32_t out = 0;                            // fragments written so far by the warp
     for (uint32_t r0 = 0; r0 < span; r0 += 32) {
         const uint32_t f = r0 + lane;
         int L = 0;                               // last lane with rel <= f
@@ -405,19 +428,14 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
         const uint32_t lc = __shfl_sync(0xffffffffu, corner, L);
         const uint32_t lg = __shfl_sync(0xffffffffu, g, L);
         const uint32_t llo = __shfl_sync(0xffffffffu, mlo, L), lhi = __shfl_sync(0xffffffffu, mhi, L);
-        const uint32_t local = f - lrel;
-        const uint32_t dy = local / lw, dx = local - dy * lw;
-        // a rectangle's slot is kept unless its pair was culled and the slot's bit is clear
-        const bool keep_slot = f < span && ((local < 32u ? llo >> local : lhi >> ((local - 32u) & 31u)) & 1u);
-        const uint32_t bal = __ballot_sync(0xffffffffu, keep_slot);
-        if (keep_slot) {
-            const uint64_t o = (uint64_t)base + out + __popc(bal & lt);
-            if (o < F) {                         // the kept slots match the counts by construction
-                keys[o] = lc + dy * ltx + dx;
-                vals[o] = lg;
-            }
+        const uint32_t local = f - lrel;         // the pair's local-th kept tile
+        const uint32_t slot = (llo & lhi) == 0xffffffffu ? local : select_bit64(llo, lhi, local);
+        const uint32_t dy = slot / lw, dx = slot - dy * lw;
+        const uint64_t o = (uint64_t)base + f;
+        if (f < span && o < F) {                 // the kept tiles match the counts by construction
+            keys[o] = lc + dy * ltx + dx;
+            vals[o] = lg;
         }
-        out += __popc(bal);
     }
 }
 
