@@ -239,7 +239,7 @@ def stage_roofline(stage, ms, counters, N, Bv, pixels, passes, peaks, clock_mhz)
     F, Ef, Eb = counters["F"], counters["evals_fwd"], counters["evals_bwd"]
     Wb = counters.get("walked_bwd", Eb)
     alu_peak = N_SM * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    sec = ms * 1e-3
+    sec = max(ms, 1e-6) * 1e-3
     # FP32 flops of the method per (pixel, list position) examined and per
     # blended (pixel, Gaussian) pair; an FMA counts 2, the exponential 1
     if stage == "blend_bwd":
