@@ -42,6 +42,7 @@ struct gs_ctx {
     // iteration scratch (gs_train_step / gs_render)
     DBuf xy, conic_o, rgb_d, radius, g_proj, keys, vals, ranges, count;
     DBuf img, dimg, T_final, n_contrib, maps, acc;
+    DBuf tile_order;               // blending launch order (tiles) + 64 words of counters
     uint64_t frag_cap = 0;
     // tracing: events around the stages of gs_train_step
     int trace_max = 0, trace_step = 0;
@@ -279,10 +280,22 @@ gs_status ensure_iter(gs_ctx *c, int64_t N, const ViewBatch &vb, uint64_t cap)
         (r = ensure(c, c->sort_tmp, sort_temp_bytes((uint64_t)n, cap))))
         return r;
     if ((r = ensure(c, c->keys, 4 * (size_t)(cap ? cap : 1))) || (r = ensure(c, c->vals, 4 * (size_t)(cap ? cap : 1))) ||
-        (r = ensure(c, c->ranges, 8 * (size_t)vb.total_tiles)) || (r = ensure(c, c->count, 64)))
+        (r = ensure(c, c->ranges, 8 * (size_t)vb.total_tiles)) || (r = ensure(c, c->count, 64)) ||
+        (r = ensure(c, c->tile_order, 4 * ((size_t)vb.total_tiles + 64))))
         return r;
     if ((r = ensure(c, c->T_final, 4 * pix)) || (r = ensure(c, c->n_contrib, 4 * pix))) return r;
     return GS_OK;
+}
+
+// Launch order of the blending kernels' tiles (launch_tile_order), or null
+// when index order is as fast; the context's buffer must hold the batch's
+// tiles (ensure_iter).
+const uint32_t *tile_order_for(gs_ctx *c, const ViewBatch &vb, const uint2 *ranges, cudaStream_t st)
+{
+    if (!tile_order_pays(vb.total_tiles) || c->tile_order.cap < 4 * ((size_t)vb.total_tiles + 64)) return nullptr;
+    uint32_t *order = ptr<uint32_t>(c->tile_order);
+    launch_tile_order(ranges, vb.total_tiles, order, order + vb.total_tiles, st);
+    return order;
 }
 
 gs_status ensure_train(gs_ctx *c, int64_t N, const ViewBatch &vb)
@@ -447,7 +460,7 @@ gs_status gs_destroy(gs_ctx *c)
                     &c->pk, &c->pv, &c->pk_alt, &c->pv_alt, &c->rect, &c->kmask, &c->rmask,
                     &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_proj, &c->keys,
                     &c->vals, &c->ranges, &c->count, &c->img, &c->dimg, &c->T_final, &c->n_contrib, &c->maps,
-                    &c->acc};
+                    &c->acc, &c->tile_order};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     trace_free(c);
@@ -531,7 +544,7 @@ gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *ca
     const size_t n = (size_t)B * (size_t)N;
     size_t s = n * (8 + 16 + 16 + 4 + 4 + 4 + 16 + 8 + 8 + 16 + 48) + frag_capacity * (8 * 2) +
                sort_temp_bytes((uint64_t)n, frag_capacity) +
-               scan_temp_bytes((int64_t)n) + tiles * 8 + pix * (4 + 4 + 12 + 12 + 36) + 4096;
+               scan_temp_bytes((int64_t)n) + tiles * (8 + 4) + 256 + pix * (4 + 4 + 12 + 12 + 36) + 4096;
     *bytes = s;
     return GS_OK;
 }
@@ -589,8 +602,11 @@ gs_status gs_render_fwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, con
     gs_status r = make_views(c, cams, B, vb, true);
     if (r != GS_OK) return r;
     set_images(vb, img, T_final, n_contrib, nullptr);
-    launch_blend_fwd(vb, proj_of(proj), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges), blend_of(c->hp),
-                     c->hp.smem_batch, c->hp.px_per_thread, c->status, S(stream));
+    const uint2 *ranges = reinterpret_cast<const uint2 *>(bins->ranges);
+    if (tile_order_pays(vb.total_tiles) && (r = ensure(c, c->tile_order, 4 * ((size_t)vb.total_tiles + 64))) != GS_OK)
+        return r;
+    launch_blend_fwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c->hp), c->hp.smem_batch, c->hp.px_per_thread,
+                     c->status, tile_order_for(c, vb, ranges, S(stream)), S(stream));
     return cuda_check(c, "gs_render_fwd");
 }
 
@@ -616,8 +632,11 @@ gs_status gs_render_bwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, con
     }
     GradView gv{reinterpret_cast<float4 *>(out->d_xy_o), reinterpret_cast<float4 *>(out->d_conic),
                 reinterpret_cast<float4 *>(out->d_rgb)};
-    launch_blend_bwd(vb, proj_of(proj), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges), blend_of(c->hp),
-                     c->hp.smem_batch, c->hp.px_per_thread, gv, c->status, st);
+    const uint2 *ranges = reinterpret_cast<const uint2 *>(bins->ranges);
+    if (tile_order_pays(vb.total_tiles) && (r = ensure(c, c->tile_order, 4 * ((size_t)vb.total_tiles + 64))) != GS_OK)
+        return r;
+    launch_blend_bwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c->hp), c->hp.smem_batch, c->hp.px_per_thread, gv,
+                     c->status, tile_order_for(c, vb, ranges, st), st);
     launch_moments_to_grads(proj_of(proj), (int64_t)B * proj->N, gv, st);
     return cuda_check(c, "gs_render_bwd");
 }
@@ -705,8 +724,9 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     if (r != GS_OK) return r;
     set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
     const BlendParams bp = blend_of(c->hp);
+    const uint32_t *order = tile_order_for(c, vb, ptr<uint2>(c->ranges), st);   // shared by both passes
     launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
-                     c->status, st);
+                     c->status, order, st);
     mark(c, st, 6);
     launch_loss(ptr<float>(c->img), targets, B, vb.v[0].W, vb.v[0].H, c->hp.lambda_dssim, loss_out,
                 ptr<float>(c->dimg), ptr<float>(c->maps), ptr<double>(c->acc), st);
@@ -717,7 +737,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     float4 *gp = ptr<float4>(c->g_proj);
     const GradView gv{gp, gp + n, gp + 2 * n};
     launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
-                     gv, c->status, st);
+                     gv, c->status, order, st);
     mark(c, st, 9);
     launch_preprocess_bwd(sv, vb, pv, gv, false, mut_of(g), st);
     mark(c, st, 10);
@@ -768,8 +788,9 @@ gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int
         vb.v[v].n_contrib = ptr<uint32_t>(c->n_contrib) + off;
         off += hw;
     }
-    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), blend_of(c->hp), c->hp.smem_batch, c->hp.px_per_thread,
-                     c->status, st);
+    const uint32_t *order = tile_order_for(c, vb, ptr<uint2>(c->ranges), st);
+    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), blend_of(c->hp), c->hp.smem_batch,
+                     c->hp.px_per_thread, c->status, order, st);
     return cuda_check(c, "gs_render");
 }
 

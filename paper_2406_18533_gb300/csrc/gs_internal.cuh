@@ -125,8 +125,8 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigne
 // y = clamp(v)); along such an edge f is a parabola, minimised at the clamp
 // of its vertex and evaluated as c (dy - dy*)^2 + (det / c) dx^2 (non-negative
 // terms, no cancellation; det by Kahan's form).  The acceptance bound
-// L = 2 ln(o / alpha_min) is widened by 0.1 %, 1e-6 x the conic's condition
-// number and 1e-4 -- beyond the rounding of the per-pixel exponent and of the
+// L = 2 ln(o / alpha_min) is widened by 0.1 %, 1e-6 x a bound on the conic's
+// condition number and 1e-4 -- beyond the rounding of the per-pixel exponent and of the
 // approximate reciprocals here -- so the test never drops a Gaussian the
 // per-pixel test would blend.  A non-positive-definite conic is kept.  Every
 // operation is explicitly rounded.
@@ -140,9 +140,10 @@ __device__ __forceinline__ float4 ellipse_terms(const float4 &co, float alpha_mi
     const float det = __fadd_rn(__fmaf_rn(a, c, -bb), __fmaf_rn(-b, b, bb));
     if (!(det > 0.f && a > 0.f && c > 0.f)) return make_float4(INFINITY, 0.f, 0.f, 0.f);
     const float L = __fmul_rn(2.f, __logf(__fdividef(co.w, alpha_min)));
-    const float tr = __fmul_rn(0.5f, __fadd_rn(a, c)), hd = __fmul_rn(0.5f, __fsub_rn(a, c));
-    const float r = sqrtf(__fmaf_rn(hd, hd, bb));
-    const float kappa = __fdividef(__fadd_rn(tr, r), fmaxf(__fsub_rn(tr, r), 1e-30f));   // condition number
+    // (a + c)^2 / det = 4 tr^2 / (tr^2 - r^2) >= (tr + r) / (tr - r), the
+    // condition number (eigenvalues tr +- r): a bound without the square root
+    const float apc = __fadd_rn(a, c);
+    const float kappa = __fdividef(__fmul_rn(apc, apc), det);
     return make_float4(__fmaf_rn(L, __fmaf_rn(1e-6f, kappa, 1.001f), 1e-4f), __fdividef(1.f, a),
                        __fdividef(1.f, c), det);
 }
@@ -247,10 +248,16 @@ void launch_compose_keys(const ViewBatch &vb, int64_t N, const uint32_t *tiles, 
 // ppt: pixels per thread (blend_config_ok says which combinations are built).
 bool blend_config_ok(int tile, int chunk, int ppt);
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                      const BlendParams &bp, int chunk, int ppt, DevStatus *status, cudaStream_t st);
+                      const BlendParams &bp, int chunk, int ppt, DevStatus *status, const uint32_t *order,
+                      cudaStream_t st);
 void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                       const BlendParams &bp, int chunk, int ppt, const GradView &g, DevStatus *status,
-                      cudaStream_t st);
+                      const uint32_t *order, cudaStream_t st);
+// Tile launch order for the blending kernels (order: launch slot -> tile;
+// null = index order): heaviest list first, worth it only for a few waves of
+// CTAs (tile_order_pays).  buckets: 64 words of scratch.
+bool tile_order_pays(uint32_t total_tiles);
+void launch_tile_order(const uint2 *ranges, uint32_t n, uint32_t *order, uint32_t *buckets, cudaStream_t st);
 
 void launch_loss(const float *img, const float *target, int B, int W, int H, float lambda, float *loss_out,
                  float *d_img, float *maps, double *acc, cudaStream_t st);
