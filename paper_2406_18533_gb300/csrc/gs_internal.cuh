@@ -192,7 +192,8 @@ __host__ __device__ __forceinline__ uint2 pack_rect(uint32_t x0, uint32_t x1, ui
 
 // Binning in depth order: (1) per (view, Gaussian) pair its tile rectangle;
 // the visible pairs (those covering a tile) compacted in index order and
-// sorted stably by depth (three passes of 10-bit digits); (2) tile counts
+// sorted stably by depth (four passes of 8-bit digits over an order-preserving
+// integer image of the float32 depth); (2) tile counts
 // gathered in that order and scanned; (3) fragments emitted pair by pair in
 // that order, key = global tile id, value = Gaussian index; (4) a stable sort
 // on the tile id.  Within a tile the fragments then follow (depth, Gaussian
