@@ -223,7 +223,7 @@ def run_reference(args, rank):
 # (tile 16, 64 entries, 2 pixels per thread on C1); the kernel's gathers and
 # atomics grow with the walked pairs, so the traffic of a bench launch is
 # taken as this times its walked count.
-BLEND_BWD_DRAM_BYTES_PER_WALKED = 1.041
+BLEND_BWD_DRAM_BYTES_PER_WALKED = 1.047
 
 
 def stage_traffic(stage, counters):
