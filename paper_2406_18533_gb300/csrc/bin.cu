@@ -298,23 +298,51 @@ __global__ void __launch_bounds__(256) k_gather_counts(const uint32_t *order, co
                                                        const uint32_t *n_vis, uint32_t *counts, uint32_t *rx,
                                                        uint32_t *ry, uint2 *keep)
 {
+    // GU pairs per thread per round, all their loads issued before any is
+    // used: the random record reads are latency-bound, so more in flight
+    constexpr int GU = 4;
     const int64_t nv = (int64_t)*n_vis < n ? (int64_t)*n_vis : n;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nv; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t o = order[j];
-        const bool ok = o < n;                   // o >= n only after a failed (timed-out) sort
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < nv; j0 += GU * stride) {
+        uint32_t o[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const int64_t j = j0 + u * stride;
+            o[u] = j < nv ? order[j] : 0xffffffffu;
+        }
         if (rm) {
-            const uint4 r = ok ? rm[o] : make_uint4(1u, 0u, 0u, 0u);
-            const uint32_t ra = rect_area(make_uint2(r.x, r.y));
-            const uint64_t m = ((uint64_t)r.w << 32) | r.z;
-            counts[j] = ra <= TILE_CULL_MAX_AREA ? (uint32_t)__popcll(m) : ra;
-            rx[j] = r.x;
-            ry[j] = r.y;
-            keep[j] = make_uint2(r.z, r.w);
+            uint4 r[GU];
+#pragma unroll
+            for (int u = 0; u < GU; ++u)       // o >= n only past nv or after a failed (timed-out) sort
+                r[u] = o[u] < n ? rm[o[u]] : make_uint4(1u, 0u, 0u, 0u);
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int64_t j = j0 + u * stride;
+                if (j >= nv) break;
+                const uint32_t ra = rect_area(make_uint2(r[u].x, r[u].y));
+                const uint64_t m = ((uint64_t)r[u].w << 32) | r[u].z;
+                counts[j] = ra <= TILE_CULL_MAX_AREA ? (uint32_t)__popcll(m) : ra;
+                rx[j] = r[u].x;
+                ry[j] = r[u].y;
+                keep[j] = make_uint2(r[u].z, r[u].w);
+            }
         } else {
-            const uint2 rc = ok ? rect[o] : make_uint2(1u, 0u);
-            counts[j] = ok ? area[o] : 0u;
-            rx[j] = rc.x;
-            ry[j] = rc.y;
+            uint2 rc[GU];
+            uint32_t ar[GU];
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const bool ok = o[u] < n;
+                rc[u] = ok ? rect[o[u]] : make_uint2(1u, 0u);
+                ar[u] = ok ? area[o[u]] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int64_t j = j0 + u * stride;
+                if (j >= nv) break;
+                counts[j] = ar[u];
+                rx[j] = rc[u].x;
+                ry[j] = rc[u].y;
+            }
         }
     }
 }
