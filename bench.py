@@ -219,8 +219,8 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------ our arm
 
 # DRAM bytes (read + write) of one k_blend_bwd launch per walked (pixel, list
-# position) pair, from the ncu capture in profiles/k_blend_bwd_c1_train_1m_1080p.md
-# (tile 16, 64 entries, 2 pixels per thread on C1); the kernel's gathers and
+# position) pair, from an ncu capture of the blending kernels on C1 (tile 16,
+# 64 entries, 2 pixels per thread; summary under profiles/); the kernel's gathers and
 # atomics grow with the walked pairs, so the traffic of a bench launch is
 # taken as this times its walked count.
 BLEND_BWD_DRAM_BYTES_PER_WALKED = 1.047
