@@ -66,6 +66,27 @@ def load_peaks():
     return PEAKS_FALLBACK, "fallback"
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(x):
+    """The maximum of x over all ranks; x itself without a process group.
+    NCCL reduces a CUDA tensor, gloo a host one."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed, over the slowest
+    rank's time (each rank runs the same replica of the workload)."""
+    return units_per_rank * world / seconds
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -350,11 +371,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     launches = int(binding.lib().gs_kernel_launches() - l0) + graph_launches * (args.steps if graph is not None else 0)
-    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
     if dist:
-        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_total = float(t.item())
         tdist.barrier()
     code, needed = ctx.status()
     if code != 0:
@@ -433,14 +451,10 @@ def run_ours(args, rank, world, local_rank):
     code, needed = ctx.status()
     if code != 0:
         raise SystemExit(f"device status {code} (needed {needed}) in the end-to-end leg")
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s)
 
-    views = args.steps * Bv * world
-    value = views / (ms_total * 1e-3)
-    e2e_value = views / e2e_s
+    value = job_throughput(args.steps * Bv, world, ms_total * 1e-3)
+    e2e_value = job_throughput(args.steps * Bv, world, e2e_s)
     if rank != 0:
         return 0
     dom = max(stage_ms, key=stage_ms.get)
