@@ -96,3 +96,35 @@ def test_workspace_size_grows_with_problem(libgs):
     assert libgs.gs_workspace_size(None, 1000, cams, 1, 10000, ctypes.byref(s1)) == 0
     assert libgs.gs_workspace_size(None, 100000, cams, 1, 10000, ctypes.byref(s2)) == 0
     assert s2.value > s1.value > 0
+
+
+def test_bin_noalloc_rejects_bad_arguments_on_host(libgs):
+    """gs_bin_noalloc checks its sizes before touching the device: views,
+    tile edge, null outputs, and the fixed scratch's limits (2^18 pairs,
+    2^20 fragments)."""
+    from paper_2406_18533_gb300 import binding as b, synth
+    fake = 256                                          # never dereferenced: every case fails first
+    cams = b.camera_array([synth.test_camera(64, 48)] * 2)
+    needed = ctypes.c_uint64(0)
+
+    def call(B=1, N=100, tile=16, cap=1000, ranges=fake, count=fake, keys=fake, vals=fake, W=None):
+        proj = b.gs_proj(fake, fake, fake, fake, N, B, 0)
+        out = b.gs_bins(keys, vals, ranges, count, cap)
+        cs = cams
+        if W is not None:
+            cs = b.camera_array([synth.test_camera(64, 48)] * B)
+            cs[0].W = W
+        return libgs.gs_bin_noalloc(ctypes.byref(proj), cs, B, tile, ctypes.byref(out), ctypes.byref(needed), None)
+
+    bad = b.GS_ERR_INVALID_ARG
+    assert call(B=0) == bad
+    assert call(B=b.GS_MAX_VIEWS + 1) == bad
+    assert call(tile=12) == bad
+    assert call(ranges=None) == bad
+    assert call(count=None) == bad
+    assert call(keys=None) == bad                       # capacity > 0 needs key and value arrays
+    assert call(N=(1 << 18) + 1) == bad                 # B * N above the scratch's pair limit
+    assert call(B=2, N=1 << 17 | 1) == bad
+    assert call(cap=(1 << 20) + 1) == bad               # fragment capacity above the limit
+    assert call(W=0) == bad                             # camera sizes checked on the host
+    assert libgs.gs_bin_noalloc(None, cams, 1, 16, None, ctypes.byref(needed), None) == bad
