@@ -1,14 +1,13 @@
 """Host-side pieces of the torch glue, on CPU tensors: the parameter planes'
 layout (the 60-float record of each Gaussian, the same on the host scene and
 the device planes, and in the ABI struct) and the tile count of a batch."""
-import ctypes
 
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
-from paper_2406_18533_gb300 import binding, engine, synth  # noqa: E402
+from paper_2406_18533_gb300 import engine, synth  # noqa: E402
 
 
 def test_planes_flatten_like_the_host_scene():
