@@ -233,41 +233,139 @@ def render_window(scene, cam, window, tile=16, **kw):
     return out
 
 
-def fp32_flags(fw, W, H, tile=16, margin=1e-3):
-    """Pixels of a forward (``render`` or ``render_window`` output) whose value
-    float32 arithmetic may legitimately decide otherwise: pixels within the
-    relative ``margin`` of an alpha, opacity-clamp or transmittance threshold
-    (the compositor's own record), and pixels that a Gaussian with borderline
-    tile membership (its 3-sigma radius within rounding of an integer, or a
-    rectangle edge within rounding of a tile line) could reach at half the
-    alpha cut, in the outermost tile rows and columns of its rectangle.
-    Returns (flag [H, W] bool, number of borderline Gaussians)."""
-    pr = fw["proj"]
-    bad = fw["margin"] <= margin
-    e = pr["ext3"]
-    border = (pr["radius"] > 0) & (np.abs(e - np.round(e)) < 1e-4)
-    for k in range(2):
-        for sgn in (-1, 1):
-            edge = (pr["xy"][:, k] + sgn * np.maximum(pr["radius"], np.ceil(e))) / tile
-            border |= (np.abs(edge - np.round(edge)) * tile < 1e-3) & (e > 0)
-    TX = (W + tile - 1) // tile
-    TY = (H + tile - 1) // tile
-    tiles_px = np.zeros((H, W), bool)
-    for g in np.nonzero(border)[0]:
-        r = max(int(math.ceil(e[g])), 0)
-        x0, x1 = int((pr["xy"][g, 0] - r) // tile), int((pr["xy"][g, 0] + r) // tile)
-        y0, y1 = int((pr["xy"][g, 1] - r) // tile), int((pr["xy"][g, 1] + r) // tile)
-        for ty in range(max(0, y0 - 1), min(TY - 1, y1 + 1) + 1):
-            for tx in range(max(0, x0 - 1), min(TX - 1, x1 + 1) + 1):
-                if tx <= x0 or tx >= x1 or ty <= y0 or ty >= y1:
-                    ys = np.arange(ty * tile, min(H, (ty + 1) * tile)) + 0.5 - pr["xy"][g, 1]
-                    xs = np.arange(tx * tile, min(W, (tx + 1) * tile)) + 0.5 - pr["xy"][g, 0]
-                    DX, DY = np.meshgrid(xs, ys)
-                    a, b, c, o = pr["conic_o"][g]
-                    reach = o * np.exp(-0.5 * (a * DX * DX + c * DY * DY) - b * DX * DY) >= 0.5 / 255
-                    view = tiles_px[ty * tile:ty * tile + DX.shape[0], tx * tile:tx * tile + DX.shape[1]]
-                    view |= reach
-    return bad | tiles_px, int(border.sum())
+# ----------------------------------------------------------------------------
+# Every result a float32 evaluation may legitimately give (Sec. 2.1 step 2
+# decided in single precision)
+# ----------------------------------------------------------------------------
+
+EVAL_M0 = 4e-6   # relative alpha error of the float32 exponential and of the
+                 # float32 constants 1/255, 0.99, 1e-4 (see or_render_fwd_set)
+
+
+def rect_f64(u, v, radius, W, H, tile=16):
+    """The transformation's double-precision tile rectangles for given centres
+    and integer radii (the routine ``project`` uses)."""
+    u = np.ascontiguousarray(u, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    r = np.ascontiguousarray(radius, np.int32)
+    n = u.shape[0]
+    rect = np.zeros((n, 4), np.int32)
+    vis = np.zeros(n, np.int32)
+    lib().or_rect_f64(_i64(n), _p(u), _p(v), _p(r), ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(tile),
+                      _p(rect), _p(vis))
+    return rect, vis
+
+
+def fp32_bounds(scene, cam, tile=16):
+    """Per Gaussian of one view, bounds on a float32 transformation's error
+    (``or_fp32_bounds``): err [N, 6] = (du, dv, kc, t0, t1, rinv), de [N]
+    (error of the 3-sigma extent), rect_in / rect_out [N, 4] (tiles covered by
+    every / by some such evaluation; empty when x0 > x1), vis_out [N]."""
+    mo, ls, q, sh = _scene_arrays(scene)
+    N = mo.shape[0]
+    out = dict(err=np.zeros((N, 6)), de=np.zeros(N), rect_in=np.zeros((N, 4), np.int32),
+               rect_out=np.zeros((N, 4), np.int32), vis_out=np.zeros(N, np.int32))
+    c = cam16(cam)
+    lib().or_fp32_bounds(_i64(N), _p(mo), _p(ls), _p(q), _p(sh), ctypes.c_int(scene.sh_degree), _p(c),
+                         ctypes.c_int(cam.W), ctypes.c_int(cam.H), ctypes.c_double(cam.near), ctypes.c_int(tile),
+                         _p(out["err"]), _p(out["de"]), _p(out["rect_in"]), _p(out["rect_out"]), _p(out["vis_out"]))
+    return out
+
+
+def render_set(W, H, tile, toff, gidx, xy, conic_o, rgb, err=None, rect=None, rect_in=None,
+               bg=(0.0, 0.0, 0.0), alpha_min=ALPHA_MIN, alpha_max=ALPHA_MAX, T_min=T_MIN, m0=EVAL_M0, cap=256):
+    """Compositing (``or_render_fwd_set``): the exact result of every pixel
+    (``img``, ``T_final``, ``n_contrib``, equal to ``render_fwd``) and every
+    other result a float32 evaluation may give (``alt_off`` [H*W+1] offsets
+    into ``alt`` [n, 5] = r, g, b, T, n_contrib), with ``flags`` [H, W]
+    (1: other results exist; 2: alpha near its clamp at a blended entry;
+    4: more than ``cap`` results, the set is incomplete).  ``err`` = None:
+    exact screen-space inputs; ``rect`` = None: exact tile membership."""
+    xy = np.ascontiguousarray(xy, np.float64)
+    conic_o = np.ascontiguousarray(conic_o, np.float64)
+    rgb = np.ascontiguousarray(rgb, np.float64)
+    toff = np.ascontiguousarray(toff, np.int64)
+    gidx = np.ascontiguousarray(gidx, np.int32)
+    e = None if err is None else np.ascontiguousarray(err, np.float64)
+    r = None if rect is None else np.ascontiguousarray(rect, np.int32)
+    ri = None if rect_in is None else np.ascontiguousarray(rect_in, np.int32)
+    img = np.zeros((3, H, W))
+    Tf = np.zeros((H, W))
+    nc = np.zeros((H, W), np.int32)
+    flags = np.zeros((H, W), np.int32)
+    n_alt = np.zeros((H, W), np.int32)
+    prm = _blend_params(bg, alpha_min, alpha_max, T_min)
+    pe = None if e is None else _p(e)
+    pr_ = None if r is None else _p(r)
+    pri = None if ri is None else _p(ri)
+    args = (ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(tile), _p(toff), _p(gidx), _p(xy), _p(conic_o), _p(rgb),
+            _p(prm), pe, pr_, pri, ctypes.c_double(m0), ctypes.c_int(cap))
+    lib().or_render_fwd_set(*args, _p(img), _p(Tf), _p(nc), _p(flags), _p(n_alt), None, None)
+    alt_off = np.zeros(H * W + 1, np.int64)
+    np.cumsum(n_alt.reshape(-1), out=alt_off[1:])
+    alt = np.zeros((max(int(alt_off[-1]), 1), 5))
+    if alt_off[-1] > 0:
+        lib().or_render_fwd_set(*args, _p(img), _p(Tf), _p(nc), _p(flags), _p(n_alt), _p(alt_off), _p(alt))
+    return dict(img=img, T_final=Tf, n_contrib=nc, flags=flags, alt_off=alt_off, alt=alt[:int(alt_off[-1])])
+
+
+def _primary_rects(pr):
+    """Exact rectangles with invisible Gaussians as empty ones (x0 > x1)."""
+    r = pr["rect"].copy()
+    r[pr["vis"] == 0] = (1, 0, 1, 0)
+    return r
+
+
+def render_admissible(scene, cam, tile=16, **kw):
+    """Every result a float32 pipeline (float32 transformation within
+    ``fp32_bounds``, float32 compositing) may give for one view: the exact
+    result (``render``'s image) plus the alternatives of ``render_set``, with
+    tile lists that hold every Gaussian some such evaluation may place in a
+    tile."""
+    pr = project(scene, cam, tile)
+    bd = fp32_bounds(scene, cam, tile)
+    toff, gidx = bin_view(bd["rect_out"], bd["vis_out"], pr["depth"].astype(np.float32), cam.W, cam.H, tile)
+    out = render_set(cam.W, cam.H, tile, toff, gidx, pr["xy"], pr["conic_o"], pr["rgb"], err=bd["err"],
+                     rect=_primary_rects(pr), rect_in=bd["rect_in"], **kw)
+    out.update(proj=pr, bounds=bd)
+    return out
+
+
+def render_window_admissible(scene, cam, window, tile=16, **kw):
+    """``render_admissible`` on a tile-aligned window (x0, y0, w, h) of a view
+    (the transformation runs with the view's own camera, as in
+    ``render_window``); ``index`` lists the Gaussians some evaluation may
+    place in the window's tiles."""
+    x0, y0, w, h = (int(a) for a in window)
+    if x0 % tile or y0 % tile or w < 1 or h < 1 or x0 + w > cam.W or y0 + h > cam.H:
+        raise ValueError("window must start on the tile grid and lie inside the view")
+    pr = project(scene, cam, tile)
+    bd = fp32_bounds(scene, cam, tile)
+    tx0, ty0 = x0 // tile, y0 // tile
+    TXw, TYw = (w + tile - 1) // tile, (h + tile - 1) // tile
+
+    def clip(r):
+        r = r.copy()
+        r[:, 0] = np.maximum(r[:, 0] - tx0, 0)
+        r[:, 1] = np.minimum(r[:, 1] - tx0, TXw - 1)
+        r[:, 2] = np.maximum(r[:, 2] - ty0, 0)
+        r[:, 3] = np.minimum(r[:, 3] - ty0, TYw - 1)
+        empty = (r[:, 0] > r[:, 1]) | (r[:, 2] > r[:, 3])
+        r[empty] = (1, 0, 1, 0)
+        return r, ~empty
+
+    ro = bd["rect_out"].copy()
+    ro[bd["vis_out"] == 0] = (1, 0, 1, 0)
+    ro_w, keep = clip(ro)
+    idx = np.nonzero(keep)[0]
+    rect_w, _ = clip(_primary_rects(pr)[idx])
+    rin_w, _ = clip(bd["rect_in"][idx])
+    xy = pr["xy"][idx] - np.array([x0, y0], np.float64)
+    toff, gidx = bin_view(ro_w[idx], np.ones(len(idx), np.int32), pr["depth"][idx].astype(np.float32), w, h, tile)
+    out = render_set(w, h, tile, toff, gidx, xy, pr["conic_o"][idx], pr["rgb"][idx], err=bd["err"][idx],
+                     rect=rect_w, rect_in=rin_w, **kw)
+    out.update(index=idx)
+    return out
 
 
 def grad_view(scene, cam, dimg, tile=16, **kw):

@@ -321,6 +321,128 @@ void or_preprocess(int64_t N, const float *mo, const float *ls, const float *q, 
  * 1/tile, floor), for the bit-exact stage check of binning.  radius <= 0 means
  * not visible.  Returns per Gaussian rect[4] and vis (0/1).
  */
+/* or_rect_f64: the double-precision tile rectangle of the transformation
+ * (rect_f64) for given centres and integer radii, exported for its pin. */
+void or_rect_f64(int64_t n, const double *u, const double *v, const int32_t *radius,
+                 int W, int H, int tile, int32_t *rect, int32_t *vis)
+{
+    for (int64_t g = 0; g < n; ++g) {
+        int r4[4];
+        vis[g] = radius[g] > 0 ? rect_f64(u[g], v[g], radius[g], W, H, tile, r4) : 0;
+        if (!vis[g]) r4[0] = r4[1] = r4[2] = r4[3] = 0;
+        for (int i = 0; i < 4; ++i) rect[4 * g + i] = r4[i];
+    }
+}
+
+/*
+ * or_fp32_bounds: a model of how far a float32 evaluation of the
+ * transformation (the same float32 parameters and camera; IEEE single
+ * operations in any order, fused multiply-adds allowed) can land from the
+ * exact values of or_preprocess.  It is the standard forward error analysis
+ * (each operation rounds with relative error at most u = 2^-24, a sum of n
+ * terms errs by at most about n u times the sum of the terms' magnitudes),
+ * widened by a factor of 4.  Per Gaussian of one view:
+ *   err[6g..6g+5] = (du, dv, kc, t0, t1, rinv):
+ *     du, dv  bound the error of the projected centre (pixels);
+ *     kc      scales the error of the 2D covariance: |dSigma'_ij| <=
+ *             kc t_i t_j, with t = the row sums of |J R| and kc a multiple of
+ *             u times the trace of the 3D covariance (the rotation matrix of
+ *             the normalised quaternion errs absolutely, so the bound is in
+ *             the trace, not componentwise);
+ *     rinv    the relative error added by inverting the 2D covariance;
+ *   de[g]     bounds the error of 3 sqrt(lambda_max) (pixels), including the
+ *             cancellation in m^2 - det for nearly isotropic footprints;
+ *   rect_in   the tiles every such evaluation covers (empty: x0 > x1);
+ *   rect_out  the tiles some such evaluation may cover, vis_out = nonempty.
+ * The float32 pipeline's tile rectangle then lies between rect_in and
+ * rect_out.  Culling at the near plane is taken as decided alike on both
+ * sides (no Gaussian of these workloads lies near z = near).
+ */
+void or_fp32_bounds(int64_t N, const float *mo, const float *ls, const float *q, const float *sh,
+                    int deg, const double *cam16, int W, int H, double near_z, int tile,
+                    double *err, double *de, int32_t *rect_in, int32_t *rect_out, int32_t *vis_out)
+{
+    const ocam cam = mk_cam(cam16, W, H, near_z);
+    const double u = ldexp(1.0, -24), safety = 4.0;
+    const int TX = (W + tile - 1) / tile, TY = (H + tile - 1) / tile;
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < N; ++g) {
+        gfwd f;
+        load_params(mo, ls, q, sh, N, g, &f);
+        g_forward(&cam, deg, tile, &f);
+        double *e = err + 6 * g;
+        for (int i = 0; i < 6; ++i) e[i] = 0;
+        de[g] = 0;
+        int32_t *ri = rect_in + 4 * g, *ro = rect_out + 4 * g;
+        ri[0] = 1; ri[1] = 0; ri[2] = 1; ri[3] = 0;
+        ro[0] = 1; ro[1] = 0; ro[2] = 1; ro[3] = 0;
+        vis_out[g] = 0;
+        if (f.culled) continue;
+        const double z = f.pc[2];
+        /* camera-space x, y: three products and three sums each */
+        double sx = fabs(cam.t[0]), sy = fabs(cam.t[1]);
+        for (int k = 0; k < 3; ++k) {
+            sx += fabs(cam.R[k] * f.x[k]);
+            sy += fabs(cam.R[3 + k] * f.x[k]);
+        }
+        const double epx = 8 * u * sx, epy = 8 * u * sy;
+        /* u = fx x (1/z) + cx: z rounded once, a division, two products, a sum */
+        const double du = fabs(cam.fx / z) * epx + 6 * u * fabs(cam.fx * f.pc[0] / z) + u * fabs(f.u);
+        const double dv = fabs(cam.fy / z) * epy + 6 * u * fabs(cam.fy * f.pc[1] / z) + u * fabs(f.v);
+        /* 2D covariance: M = Rq diag(s) errs by <= 6u s_j per entry, Sigma =
+         * M M^T by <= 15u tr(Sigma), J R by a few u relative; Sigma' = T
+         * Sigma T^T then errs by <= gamma tr(Sigma) t_i t_j */
+        double trS = f.s[0] * f.s[0] + f.s[1] * f.s[1] + f.s[2] * f.s[2];
+        double t0 = 0, t1 = 0;
+        for (int k = 0; k < 3; ++k) { t0 += fabs(f.T[k]); t1 += fabs(f.T[3 + k]); }
+        const double kc = safety * 32 * u * trS;
+        const double A = f.S2[0], B = f.S2[1], C = f.S2[2];
+        const double rinv = safety * (4 * u + 2 * u * (A * C + B * B) / f.det);
+        e[0] = safety * du;
+        e[1] = safety * dv;
+        e[2] = kc;
+        e[3] = t0;
+        e[4] = t1;
+        e[5] = rinv;
+        /* lambda_max = m + sqrt(m^2 - det) */
+        const double dA = kc * t0 * t0 + u * A, dC = kc * t1 * t1 + u * C, dB = kc * t0 * t1 + u * fabs(B);
+        const double m = 0.5 * (A + C);
+        const double dm = 0.5 * (dA + dC) + u * m;
+        const double ddet = dA * C + A * dC + 2 * fabs(B) * dB + 2 * u * (A * C + B * B);
+        double disc = m * m - f.det;
+        if (disc < 0) disc = 0;
+        const double ddisc = 2 * m * dm + ddet + 2 * u * (m * m + f.det);
+        const double dsq = ddisc / sqrt(disc > ddisc ? disc : ddisc) + u * sqrt(disc);
+        const double dlam = dm + dsq + u * f.lam;
+        const double dext = 2 * (1.5 * dlam / sqrt(f.lam) + 4 * u * f.ext3);
+        de[g] = dext;
+        /* radius and tile edges of any such evaluation */
+        double rlo = ceil(f.ext3 - dext), rhi = ceil(f.ext3 + dext);
+        if (rlo < 0) rlo = 0;
+        const double cu[2] = {f.u, f.v}, dd[2] = {safety * du, safety * dv};
+        const int lim[2] = {TX - 1, TY - 1};
+        int lo_min[2], lo_max[2], hi_min[2], hi_max[2];
+        for (int a = 0; a < 2; ++a) {
+            const double r1 = u * (fabs(cu[a]) + rhi);   /* rounding of u -+ r */
+            lo_min[a] = (int)floor((cu[a] - dd[a] - rhi - r1) / tile);
+            lo_max[a] = (int)floor((cu[a] + dd[a] - rlo + r1) / tile);
+            hi_min[a] = (int)floor((cu[a] - dd[a] + rlo - r1) / tile);
+            hi_max[a] = (int)floor((cu[a] + dd[a] + rhi + r1) / tile);
+            if (lo_min[a] < 0) lo_min[a] = 0;
+            if (lo_max[a] < 0) lo_max[a] = 0;
+            if (hi_min[a] > lim[a]) hi_min[a] = lim[a];
+            if (hi_max[a] > lim[a]) hi_max[a] = lim[a];
+        }
+        if (lo_min[0] <= hi_max[0] && lo_min[1] <= hi_max[1]) {
+            ro[0] = lo_min[0]; ro[1] = hi_max[0]; ro[2] = lo_min[1]; ro[3] = hi_max[1];
+            vis_out[g] = 1;
+        }
+        if (rlo > 0 && lo_max[0] <= hi_min[0] && lo_max[1] <= hi_min[1]) {
+            ri[0] = lo_max[0]; ri[1] = hi_min[0]; ri[2] = lo_max[1]; ri[3] = hi_min[1];
+        }
+    }
+}
+
 void or_rect_f32(int64_t n, const float *u, const float *v, const int32_t *radius,
                  int W, int H, int tile, int32_t *rect, int32_t *vis)
 {
@@ -454,6 +576,198 @@ void or_render_fwd(int W, int H, int tile, const int64_t *toff, const int32_t *g
             n_contrib[p] = nc;
             if (margin) margin[p] = marg;
             if (n_eval) n_eval[p] = ne;
+        }
+}
+
+/*
+ * The set of results a float32 evaluation of the compositing may give.
+ *
+ * The definition above decides, per pixel and list entry, three things with
+ * a threshold: whether the Gaussian is in the pixel's tile list (tile
+ * membership of its rectangle), whether it passes (power <= 0 and alpha >=
+ * alpha_min), and whether blending it would take T below T_min (stop).  A
+ * float32 evaluation with inputs within the bounds of or_fp32_bounds may
+ * decide any of them the other way when the exact quantity lies within that
+ * evaluation's error of the threshold; everywhere else both decide alike and
+ * differ only by rounding.  or_render_fwd_set walks each pixel's list as
+ * or_render_fwd does (the primary result, identical to it), and wherever a
+ * decision is ambiguous it also follows the other outcome to the end of the
+ * list: every leaf of that tree is an admissible result.
+ *
+ * Relative error bound of alpha at an entry (from the power's error dp):
+ *   dp = m0 + 8u (|a| dx^2/2 + |b dx dy| + |c| dy^2/2)     (evaluation)
+ *        + |g_x| du + |g_y| dv                              (centre)
+ *        + kc (t0 |g_x| + t1 |g_y|)^2 / 2                   (2D covariance)
+ *        + |power| rinv                                     (inversion)
+ * with g = (a dx + b dy, b dx + c dy) the gradient of power in the centre
+ * (err == NULL: exact screen-space inputs, only the first line), and
+ * m_alpha = expm1(dp).  The transmittance carries, after each blend, the
+ * relative error bound sum alpha/(1 - alpha) m_alpha + 2u/(1 - alpha).
+ *
+ * Membership: with rect != NULL the lists are built from the rectangles
+ * every evaluation may cover (or_fp32_bounds' rect_out); an entry belongs to
+ * the primary list when its tile lies in rect[g] (the exact rectangle) and
+ * is certain when it lies in rect_in[g].
+ */
+typedef struct {
+    double C[3], T, eT;
+    int32_t nc, pos;
+} or_state;
+
+typedef struct {
+    int W, H, tile, TX;
+    const int64_t *toff;
+    const int32_t *gidx;
+    const double *xy, *conic_o, *rgb, *err;
+    const int32_t *rect, *rect_in;
+    oblend bp;
+    double m0;
+} or_setin;
+
+typedef struct {
+    double *alt;        /* NULL: count only; else 5 doubles per leaf */
+    int n, cap, overflow, clamp_amb;
+} or_setout;
+
+enum { OUT_SKIP = 1, OUT_BLEND = 2, OUT_STOP = 4 };
+
+static int in_rect(const int32_t *r, int tx, int ty) { return r[0] <= tx && tx <= r[1] && r[2] <= ty && ty <= r[3]; }
+
+static void set_leaf(const or_setin *s, const or_state *st, or_setout *o)
+{
+    if (o->n >= o->cap) { o->overflow = 1; return; }
+    if (o->alt) {
+        double *a = o->alt + 5 * (int64_t)o->n;
+        for (int ch = 0; ch < 3; ++ch) a[ch] = st->C[ch] + st->T * s->bp.bg[ch];
+        a[3] = st->T;
+        a[4] = st->nc;
+    }
+    o->n++;
+}
+
+/* Walks pixel (px, py) of tile t from list index k in state st; alternative
+ * outcomes are walked recursively and recorded as leaves; the walk's own end
+ * state is returned in *end (the primary result at the top level). */
+static void set_walk(const or_setin *s, int px, int py, int64_t t, int64_t k, or_state st, int primary,
+                     or_setout *o, or_state *end)
+{
+    const double u = ldexp(1.0, -24);
+    const int tx = px / s->tile, ty = py / s->tile;
+    for (; k < s->toff[t + 1]; ++k) {
+        const int32_t g = s->gidx[k];
+        int prim = 1, amb_memb = 0;
+        if (s->rect) {
+            prim = in_rect(s->rect + 4 * g, tx, ty);
+            amb_memb = !in_rect(s->rect_in + 4 * g, tx, ty);
+        }
+        const double dx = px + 0.5 - s->xy[2 * g], dy = py + 0.5 - s->xy[2 * g + 1];
+        const double a = s->conic_o[4 * g], b = s->conic_o[4 * g + 1], c = s->conic_o[4 * g + 2];
+        const double o_ = s->conic_o[4 * g + 3];
+        const double power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
+        double dp = s->m0 + 8 * u * (0.5 * fabs(a) * dx * dx + fabs(b * dx * dy) + 0.5 * fabs(c) * dy * dy);
+        if (s->err) {
+            const double *e = s->err + 6 * g;
+            const double gx = fabs(a * dx + b * dy), gy = fabs(b * dx + c * dy);
+            const double w = e[3] * gx + e[4] * gy;
+            dp += gx * e[0] + gy * e[1] + 0.5 * e[2] * w * w + fabs(power) * e[5];
+        }
+        const double ma = expm1(dp);
+        const double oa = o_ * exp(power);
+        const double alpha = oa < s->bp.alpha_max ? oa : s->bp.alpha_max;
+        /* pass: power <= 0 and alpha >= alpha_min */
+        const int pass_p = power <= 0 && alpha >= s->bp.alpha_min;
+        const int pass_amb = (fabs(power) <= dp && alpha >= s->bp.alpha_min * (1 - ma))
+                          || (fabs(alpha - s->bp.alpha_min) <= s->bp.alpha_min * ma && power <= dp);
+        const double Tn = st.T * (1.0 - alpha);
+        const double eTn = st.eT + alpha / (1.0 - alpha) * ma + 2 * u / (1.0 - alpha);
+        const int stop_p = Tn < s->bp.T_min;
+        const int stop_amb = fabs(Tn - s->bp.T_min) <= s->bp.T_min * (eTn + 4 * u);
+        /* outcome of the exact decisions, and the set of possible ones */
+        const int out_p = !(prim && pass_p) ? OUT_SKIP : stop_p ? OUT_STOP : OUT_BLEND;
+        int outs = 0;
+        for (int inc = 0; inc < 2; ++inc) {
+            if (inc != prim && !amb_memb) continue;
+            if (!inc) { outs |= OUT_SKIP; continue; }
+            for (int ps = 0; ps < 2; ++ps) {
+                if (ps != pass_p && !pass_amb) continue;
+                if (!ps) { outs |= OUT_SKIP; continue; }
+                outs |= stop_p ? OUT_STOP : OUT_BLEND;
+                if (stop_amb) outs |= stop_p ? OUT_BLEND : OUT_STOP;
+            }
+        }
+        if (primary && out_p == OUT_BLEND && fabs(oa - s->bp.alpha_max) <= s->bp.alpha_max * ma) o->clamp_amb = 1;
+        for (int alt = OUT_SKIP; alt <= OUT_STOP; alt <<= 1) {
+            if (alt == out_p || !(outs & alt)) continue;
+            if (o->n >= o->cap) { o->overflow = 1; continue; }
+            or_state sa = st;
+            if (alt == OUT_STOP) { set_leaf(s, &sa, o); continue; }
+            if (alt == OUT_SKIP) {
+                sa.pos += prim;
+            } else {
+                sa.pos += 1;
+                for (int ch = 0; ch < 3; ++ch) sa.C[ch] += s->rgb[3 * g + ch] * alpha * sa.T;
+                sa.T = Tn;
+                sa.eT = eTn;
+                sa.nc = sa.pos;
+            }
+            or_state e2;
+            set_walk(s, px, py, t, k + 1, sa, 0, o, &e2);
+            set_leaf(s, &e2, o);
+        }
+        if (out_p == OUT_STOP) break;
+        if (out_p == OUT_SKIP) { st.pos += prim; continue; }
+        st.pos += 1;
+        for (int ch = 0; ch < 3; ++ch) st.C[ch] += s->rgb[3 * g + ch] * alpha * st.T;
+        st.T = Tn;
+        st.eT = eTn;
+        st.nc = st.pos;
+    }
+    *end = st;
+}
+
+/*
+ * or_render_fwd_set: img, T_final and n_contrib as or_render_fwd (the exact
+ * decisions), plus the other admissible results of every pixel.
+ * flags[p]: 1 = other results exist, 2 = alpha within its bound of the
+ * alpha_max clamp at a blended entry (the value is continuous there, the
+ * gradient is not), 4 = more than `cap` leaves (the set is incomplete).
+ * With alt == NULL only n_alt[p] (the count of other results) is written;
+ * with alt != NULL (5 doubles per result: r, g, b, T, n_contrib, pixel by
+ * pixel at alt_off[p]) the results are written.  err == NULL: exact
+ * screen-space inputs; rect == NULL: exact membership (lists as given).
+ */
+void or_render_fwd_set(int W, int H, int tile, const int64_t *toff, const int32_t *gidx,
+                       const double *xy, const double *conic_o, const double *rgb, const double *params5,
+                       const double *err, const int32_t *rect, const int32_t *rect_in, double m0, int cap,
+                       double *img, double *T_final, int32_t *n_contrib, int32_t *flags, int32_t *n_alt,
+                       const int64_t *alt_off, double *alt)
+{
+    or_setin s;
+    s.W = W; s.H = H; s.tile = tile; s.TX = (W + tile - 1) / tile;
+    s.toff = toff; s.gidx = gidx; s.xy = xy; s.conic_o = conic_o; s.rgb = rgb; s.err = err;
+    s.rect = rect; s.rect_in = rect_in; s.m0 = m0;
+    s.bp.alpha_min = params5[0]; s.bp.alpha_max = params5[1]; s.bp.T_min = params5[2];
+    for (int ch = 0; ch < 3; ++ch) s.bp.bg[ch] = params5[3 + ch];
+    const int64_t HW = (int64_t)H * W;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            const int64_t p = (int64_t)py * W + px;
+            const int64_t t = (int64_t)(py / tile) * s.TX + px / tile;
+            or_setout o;
+            o.alt = alt ? alt + 5 * alt_off[p] : NULL;
+            o.n = 0; o.cap = cap; o.overflow = 0; o.clamp_amb = 0;
+            if (alt) o.cap = (int)(alt_off[p + 1] - alt_off[p]);
+            or_state st = {{0, 0, 0}, 1.0, 0.0, 0, 0};
+            or_state end;
+            set_walk(&s, px, py, t, toff[t], st, 1, &o, &end);
+            if (!alt) {
+                for (int ch = 0; ch < 3; ++ch) img[ch * HW + p] = end.C[ch] + end.T * s.bp.bg[ch];
+                T_final[p] = end.T;
+                n_contrib[p] = end.nc;
+                flags[p] = (o.n > 0 ? 1 : 0) | (o.clamp_amb ? 2 : 0) | (o.overflow ? 4 : 0);
+                n_alt[p] = o.n;
+            }
         }
 }
 

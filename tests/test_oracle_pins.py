@@ -134,35 +134,6 @@ def test_closed_form_clamp_and_cut(oracle):
     assert cut.sum() > 0 and np.all(c[cut] == 0.0) and np.all(c[~cut] > 0)
 
 
-def test_fp32_flags_against_closed_form(oracle):
-    """fp32_flags on one isotropic Gaussian on the axis, its 3-sigma extent put
-    on an integer (a borderline radius).  Pixels whose closed-form o G lies
-    within 0.1 % of the alpha clamp or of the alpha cut are flagged.  So are
-    pixels of the rectangle's outer tiles that the Gaussian reaches at half the
-    cut.  No other pixel is flagged."""
-    cam = synth.test_camera(W=64, H=48)
-    z, k = 3.0, 7
-    sigma = z / cam.fx * math.sqrt((k / 3) ** 2 - 0.3)      # 3 sqrt((f s/z)^2 + 0.3) = k
-    sc, eff = _iso_scene(z, sigma, 3.0, np.array([1.0, 1.0, 1.0]))
-    sigma, logit = eff["s"][0], eff["logit"]
-    fw = oracle.render(sc, cam)
-    e3 = fw["proj"]["ext3"][0]
-    assert abs(e3 - k) < 1e-4                                # borderline by construction
-    flag, nborder = oracle.fp32_flags(fw, cam.W, cam.H, 16, 1e-3)
-    assert nborder == 1
-    o = 1 / (1 + math.exp(-logit))
-    cf = _iso_closed_form(cam, z, sigma, sigma, o, 1.0)
-    oG = o * cf["G"]
-    near = (np.abs(oG - 0.99) / 0.99 <= 1e-3) | (np.abs(np.minimum(oG, 0.99) - 1 / 255) * 255 <= 1e-3)
-    # outer tiles of the (k-pixel) rectangle: every tile of this 4 x 3 image
-    # lies in or next to its outermost rows and columns
-    reach = oG >= 0.5 / 255
-    assert np.all(flag[near])
-    assert np.all(flag[reach])
-    assert not np.any(flag[~near & ~reach])
-    assert reach.sum() > 0 and (~reach).sum() > 0
-
-
 def test_closed_form_isotropic_gradients(oracle):
     """dC/du = rgb alpha dx / s^2, du/dx = f/z (the Jacobian's x-terms vanish on
     the axis), dC/dlog(sx) = rgb alpha dx^2/(2 s^4) * 2 (f sx/z)^2, and
