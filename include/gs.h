@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 1
+#define GS_ABI_VERSION 2
 #define GS_MAX_VIEWS 32   /* views per call (training batch or render batch) */
 #define GS_MAX_FRAGMENTS 1073741823ull  /* 2^30 - 1: largest fragment capacity of one call */
 
@@ -166,8 +166,10 @@ gs_status gs_get_status(gs_ctx *ctx, void *stream, int32_t *status, uint64_t *ne
  * out[0] = fragments F, out[1] = (pixel, fragment) evaluations in the
  * forward, out[2] = (pixel, Gaussian) pairs blended in the backward,
  * out[3] = (pixel, list position) pairs the backward walked, out[4] =
- * Gaussians culled for non-finite parameters (cumulative). */
-gs_status gs_get_counters(gs_ctx *ctx, void *stream, uint64_t out[5]);
+ * Gaussians culled for non-finite parameters (cumulative), out[5] = the sum
+ * of n_contrib over the forward's pixels (list positions the backward
+ * covers, before any culling).  out holds 6 values (ABI version 2). */
+gs_status gs_get_counters(gs_ctx *ctx, void *stream, uint64_t out[6]);
 
 /*
  * Tracing (profiling aid, no paper counterpart): when enabled with
@@ -188,6 +190,29 @@ gs_status gs_trace_read(gs_ctx *ctx, float *ms, int32_t *steps);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all contexts); differences count the kernels of a region. */
 uint64_t gs_kernel_launches(void);
+
+/*
+ * Test hooks for the failure paths (no paper counterpart).  Both settings are
+ * process-wide (all contexts, all threads) and meant for tests only.
+ *
+ * gs_debug_set_lookback: a tile of the radix sort waits for the digit counts
+ * of earlier tiles (decoupled look-back).  Each such wait polls at most
+ * spin_limit times (0 = the default, 2^22) and then gives up, setting
+ * GS_ERR_TIMEOUT in the device status word.  withhold_first_tile != 0 makes
+ * tile 0 of every sort pass keep its counts to itself, so the waits of later
+ * tiles run out: the binning then finishes with wrong but in-bounds results
+ * (every store of the sort, and every read of the kernels after it, is
+ * checked against its buffer), gs_get_status reports GS_ERR_TIMEOUT, and the
+ * context stays usable.  Reset with (0, 0).
+ *
+ * gs_debug_fail_alloc: after = -1 turns the injection off; after = n >= 0
+ * lets the library's next n device allocations succeed and fails the one
+ * after that with GS_ERR_OOM, without calling cudaMalloc, then turns itself
+ * off.  after < -1 returns GS_ERR_INVALID_ARG.  The call that meets the
+ * failure returns GS_ERR_OOM; the context keeps what it had and can retry.
+ */
+gs_status gs_debug_set_lookback(uint32_t spin_limit, int32_t withhold_first_tile);
+gs_status gs_debug_fail_alloc(int64_t after);
 
 /*
  * Sec. 2.1 step 1 (Gaussian transformation), fused over B views: reads each
@@ -228,10 +253,15 @@ gs_status gs_bin(gs_ctx *ctx, const gs_proj *proj, const gs_camera *cams, int32_
  * the caller's, exactly as for gs_bin; a capacity overflow is handled as in
  * gs_bin (nothing written past capacity; with needed_host the call
  * synchronises the stream and returns GS_ERR_CAPACITY with the needed count).
- * The first call on a device looks up the array's device address (once per
- * device, with that device current), so make that first call before any
- * stream capture.  Every call uses the same array: calls that overlap on the
- * GPU (other streams, other threads) race and corrupt each other's results.
+ * There is no status word a caller can read: without needed_host an overflow
+ * leaves *count == 0, which cannot be told from a binning with no fragments,
+ * so a caller whose fragments may exceed out->capacity must pass needed_host.
+ * The array's device address is looked up on every call made outside stream
+ * capture (so a cudaDeviceReset between calls is harmless); a call during
+ * stream capture reuses the address of the last call outside capture on that
+ * device, so make a first call on each device before any capture.  Every
+ * call uses the same array: calls that overlap on the GPU (other streams,
+ * other threads) race and corrupt each other's results.
  */
 gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, int32_t B, int32_t tile, gs_bins *out,
                          uint64_t *needed_host, void *stream);
@@ -282,7 +312,8 @@ gs_status gs_loss(gs_ctx *ctx, const float *img, const float *target, int32_t B,
  * hyperparameter flags ask for them.  In place on p, m, v.  step == 0 takes
  * the step from the context's device-side counter, incremented by the call
  * itself (first call: step 1), so a call captured in a CUDA graph advances the
- * step on every replay.  A pending GS_ERR_CAPACITY skips the update.
+ * step on every replay.  A pending GS_ERR_CAPACITY or GS_ERR_TIMEOUT in the
+ * device status word skips the update (and the device step counter).
  */
 gs_status gs_adam_step(gs_ctx *ctx, gs_scene *p, const gs_scene *g, gs_scene *m, gs_scene *v,
                        int64_t step, int32_t B, void *stream);

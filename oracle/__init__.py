@@ -258,7 +258,7 @@ def rect_f64(u, v, radius, W, H, tile=16):
 
 def fp32_bounds(scene, cam, tile=16):
     """Per Gaussian of one view, bounds on a float32 transformation's error
-    (``or_fp32_bounds``): err [N, 6] = (du, dv, kc, t0, t1, rinv), de [N]
+    (``or_fp32_bounds``): err [N, 6] = (du, dv, dA, dB, dC, rinv), de [N]
     (error of the 3-sigma extent), rect_in / rect_out [N, 4] (tiles covered by
     every / by some such evaluation; empty when x0 > x1), vis_out [N]."""
     mo, ls, q, sh = _scene_arrays(scene)

@@ -341,15 +341,17 @@ void or_rect_f64(int64_t n, const double *u, const double *v, const int32_t *rad
  * exact values of or_preprocess.  It is the standard forward error analysis
  * (each operation rounds with relative error at most u = 2^-24, a sum of n
  * terms errs by at most about n u times the sum of the terms' magnitudes),
- * widened by a factor of 4.  Per Gaussian of one view:
- *   err[6g..6g+5] = (du, dv, kc, t0, t1, rinv):
- *     du, dv  bound the error of the projected centre (pixels);
- *     kc      scales the error of the 2D covariance: |dSigma'_ij| <=
- *             kc t_i t_j, with t = the row sums of |J R| and kc a multiple of
- *             u times the trace of the 3D covariance (the rotation matrix of
- *             the normalised quaternion errs absolutely, so the bound is in
- *             the trace, not componentwise);
- *     rinv    the relative error added by inverting the 2D covariance;
+ * componentwise, widened by a factor of 2.  Per Gaussian of one view:
+ *   err[6g..6g+5] = (du, dv, dA, dB, dC, rinv):
+ *     du, dv      bound the error of the projected centre (pixels);
+ *     dA, dB, dC  bound the error of the 2D covariance entries (pixels^2)
+ *                 formed as T Sigma T^T + 0.3 I with T = J R and Sigma =
+ *                 M M^T, M = Rq diag(s): the rotation of the normalised
+ *                 quaternion errs absolutely (a few u per entry), so M errs
+ *                 by <= 9u s_k per entry of column k, Sigma by that times
+ *                 |M|, and T Sigma T^T carries those and T's own rounding
+ *                 through |T|;
+ *     rinv        the relative error added by inverting the 2D covariance;
  *   de[g]     bounds the error of 3 sqrt(lambda_max) (pixels), including the
  *             cancellation in m^2 - det for nearly isotropic footprints;
  *   rect_in   the tiles every such evaluation covers (empty: x0 > x1);
@@ -363,7 +365,7 @@ void or_fp32_bounds(int64_t N, const float *mo, const float *ls, const float *q,
                     double *err, double *de, int32_t *rect_in, int32_t *rect_out, int32_t *vis_out)
 {
     const ocam cam = mk_cam(cam16, W, H, near_z);
-    const double u = ldexp(1.0, -24), safety = 4.0;
+    const double u = ldexp(1.0, -24), safety = 2.0;
     const int TX = (W + tile - 1) / tile, TY = (H + tile - 1) / tile;
 #pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < N; ++g) {
@@ -389,23 +391,46 @@ void or_fp32_bounds(int64_t N, const float *mo, const float *ls, const float *q,
         /* u = fx x (1/z) + cx: z rounded once, a division, two products, a sum */
         const double du = fabs(cam.fx / z) * epx + 6 * u * fabs(cam.fx * f.pc[0] / z) + u * fabs(f.u);
         const double dv = fabs(cam.fy / z) * epy + 6 * u * fabs(cam.fy * f.pc[1] / z) + u * fabs(f.v);
-        /* 2D covariance: M = Rq diag(s) errs by <= 6u s_j per entry, Sigma =
-         * M M^T by <= 15u tr(Sigma), J R by a few u relative; Sigma' = T
-         * Sigma T^T then errs by <= gamma tr(Sigma) t_i t_j */
-        double trS = f.s[0] * f.s[0] + f.s[1] * f.s[1] + f.s[2] * f.s[2];
-        double t0 = 0, t1 = 0;
-        for (int k = 0; k < 3; ++k) { t0 += fabs(f.T[k]); t1 += fabs(f.T[3 + k]); }
-        const double kc = safety * 32 * u * trS;
+        /* Sigma = M M^T with |dM_ak| <= 9u s_k (the rotation errs
+         * absolutely); Sigma' = T Sigma T^T + 0.3 I with T = J R, carried
+         * through |T| (sums of the terms' magnitudes), plus T's own rounding */
+        double dS[9], aS[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0, am = 0;
+                for (int k = 0; k < 3; ++k) {
+                    acc += 9 * u * f.s[k] * (fabs(f.M[3 * a + k]) + fabs(f.M[3 * b + k]));
+                    am += fabs(f.M[3 * a + k]) * fabs(f.M[3 * b + k]);
+                }
+                dS[3 * a + b] = acc + 4 * u * am;
+                aS[3 * a + b] = am;            /* >= |Sigma_ab| */
+            }
+        double Ta[6];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double acc = 0;
+                for (int k = 0; k < 3; ++k) acc += fabs(f.J[3 * i + k] * cam.R[3 * k + j]);
+                Ta[3 * i + j] = acc;
+            }
+        double dSig2[4];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                double acc = 0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        acc += Ta[3 * i + a] * (dS[3 * a + b] + 20 * u * aS[3 * a + b]) * Ta[3 * j + b];
+                dSig2[2 * i + j] = safety * (acc + 2 * u * fabs(f.S2[i + j]));
+            }
         const double A = f.S2[0], B = f.S2[1], C = f.S2[2];
         const double rinv = safety * (4 * u + 2 * u * (A * C + B * B) / f.det);
         e[0] = safety * du;
         e[1] = safety * dv;
-        e[2] = kc;
-        e[3] = t0;
-        e[4] = t1;
+        e[2] = dSig2[0];
+        e[3] = dSig2[1];
+        e[4] = dSig2[3];
         e[5] = rinv;
         /* lambda_max = m + sqrt(m^2 - det) */
-        const double dA = kc * t0 * t0 + u * A, dC = kc * t1 * t1 + u * C, dB = kc * t0 * t1 + u * fabs(B);
+        const double dA = dSig2[0], dC = dSig2[3], dB = dSig2[1];
         const double m = 0.5 * (A + C);
         const double dm = 0.5 * (dA + dC) + u * m;
         const double ddet = dA * C + A * dC + 2 * fabs(B) * dB + 2 * u * (A * C + B * B);
@@ -414,7 +439,7 @@ void or_fp32_bounds(int64_t N, const float *mo, const float *ls, const float *q,
         const double ddisc = 2 * m * dm + ddet + 2 * u * (m * m + f.det);
         const double dsq = ddisc / sqrt(disc > ddisc ? disc : ddisc) + u * sqrt(disc);
         const double dlam = dm + dsq + u * f.lam;
-        const double dext = 2 * (1.5 * dlam / sqrt(f.lam) + 4 * u * f.ext3);
+        const double dext = safety * (1.5 * dlam / sqrt(f.lam) + 4 * u * f.ext3);
         de[g] = dext;
         /* radius and tile edges of any such evaluation */
         double rlo = ceil(f.ext3 - dext), rhi = ceil(f.ext3 + dext);
@@ -597,12 +622,15 @@ void or_render_fwd(int W, int H, int tile, const int64_t *toff, const int32_t *g
  * Relative error bound of alpha at an entry (from the power's error dp):
  *   dp = m0 + 8u (|a| dx^2/2 + |b dx dy| + |c| dy^2/2)     (evaluation)
  *        + |g_x| du + |g_y| dv                              (centre)
- *        + kc (t0 |g_x| + t1 |g_y|)^2 / 2                   (2D covariance)
+ *        + (g_x^2 dA + 2 |g_x g_y| dB + g_y^2 dC) / 2       (2D covariance)
  *        + |power| rinv                                     (inversion)
  * with g = (a dx + b dy, b dx + c dy) the gradient of power in the centre
- * (err == NULL: exact screen-space inputs, only the first line), and
- * m_alpha = expm1(dp).  The transmittance carries, after each blend, the
- * relative error bound sum alpha/(1 - alpha) m_alpha + 2u/(1 - alpha).
+ * (err == NULL: exact screen-space inputs, only the first line).  The alpha
+ * cut (and the clamp) can go the other way only where ln(o) + power lies
+ * within dp of ln(alpha_min) (of ln(alpha_max)); a blended alpha errs by at
+ * most m_alpha = expm1(dp) relative, and the transmittance carries, after
+ * each blend, the relative error bound sum alpha/(1 - alpha) m_alpha +
+ * 2u/(1 - alpha).
  *
  * Membership: with rect != NULL the lists are built from the rectangles
  * every evaluation may cover (or_fp32_bounds' rect_out); an entry belongs to
@@ -668,16 +696,20 @@ static void set_walk(const or_setin *s, int px, int py, int64_t t, int64_t k, or
         if (s->err) {
             const double *e = s->err + 6 * g;
             const double gx = fabs(a * dx + b * dy), gy = fabs(b * dx + c * dy);
-            const double w = e[3] * gx + e[4] * gy;
-            dp += gx * e[0] + gy * e[1] + 0.5 * e[2] * w * w + fabs(power) * e[5];
+            dp += gx * e[0] + gy * e[1] + 0.5 * (gx * gx * e[2] + 2 * gx * gy * e[3] + gy * gy * e[4])
+                + fabs(power) * e[5];
         }
         const double ma = expm1(dp);
         const double oa = o_ * exp(power);
         const double alpha = oa < s->bp.alpha_max ? oa : s->bp.alpha_max;
-        /* pass: power <= 0 and alpha >= alpha_min */
+        /* pass: power <= 0 and alpha >= alpha_min.  A float32 evaluation has
+         * o exp(power') with |power' - power| <= dp, so the alpha cut can go
+         * the other way only when ln(o) + power lies within dp of
+         * ln(alpha_min) (the clamp at alpha_max is far above the cut) */
+        const double lcut = log(s->bp.alpha_min / o_);
         const int pass_p = power <= 0 && alpha >= s->bp.alpha_min;
-        const int pass_amb = (fabs(power) <= dp && alpha >= s->bp.alpha_min * (1 - ma))
-                          || (fabs(alpha - s->bp.alpha_min) <= s->bp.alpha_min * ma && power <= dp);
+        const int pass_amb = (fabs(power) <= dp && power + dp >= lcut)
+                          || (fabs(power - lcut) <= dp && power <= dp);
         const double Tn = st.T * (1.0 - alpha);
         const double eTn = st.eT + alpha / (1.0 - alpha) * ma + 2 * u / (1.0 - alpha);
         const int stop_p = Tn < s->bp.T_min;
@@ -695,7 +727,7 @@ static void set_walk(const or_setin *s, int px, int py, int64_t t, int64_t k, or
                 if (stop_amb) outs |= stop_p ? OUT_BLEND : OUT_STOP;
             }
         }
-        if (primary && out_p == OUT_BLEND && fabs(oa - s->bp.alpha_max) <= s->bp.alpha_max * ma) o->clamp_amb = 1;
+        if (primary && out_p == OUT_BLEND && fabs(power - log(s->bp.alpha_max / o_)) <= dp) o->clamp_amb = 1;
         for (int alt = OUT_SKIP; alt <= OUT_STOP; alt <<= 1) {
             if (alt == out_p || !(outs & alt)) continue;
             if (o->n >= o->cap) { o->overflow = 1; continue; }

@@ -85,6 +85,8 @@ SIGNATURES = {
     "gs_trace_enable": [_vp, _i32],
     "gs_trace_read": [_vp, P(ctypes.c_float), P(_i32)],
     "gs_kernel_launches": [],
+    "gs_debug_set_lookback": [ctypes.c_uint32, _i32],
+    "gs_debug_fail_alloc": [_i64],
     "gs_bin_noalloc": [P(gs_proj), P(gs_camera), _i32, _i32, P(gs_bins), P(ctypes.c_uint64), _vp],
 }
 NOALLOC_MAX_PAIRS = 1 << 18

@@ -38,11 +38,20 @@ __device__ __forceinline__ void adam4(float4 &p, const float4 &g, float4 &m, flo
     adam1(p.w, g.w, m.w, v.w, lr.w, b1, b2, ibc1, ibc2, eps);
 }
 
+// A step whose binning overflowed the fragment buffer or whose sort gave up
+// (a look-back wait ran out) has an incomplete or wrong gradient: the update
+// and the step counter are skipped, so the parameters stay as they were.
+__device__ __forceinline__ bool step_failed(const DevStatus *status)
+{
+    const int c = status->code;
+    return c == GS_ERR_CAPACITY || c == GS_ERR_TIMEOUT;
+}
+
 // Advances the device-side step counter (graph-replayable training loops) and
 // stores the bias corrections 1 - b1^t, 1 - b2^t next to it for the update.
 __global__ void k_step_tick(long long *dstep, float b1, float b2, const DevStatus *status)
 {
-    if (status->code == GS_ERR_CAPACITY) return;
+    if (step_failed(status)) return;
     const long long t = dstep[0] + 1;
     dstep[0] = t;
     float *bc = reinterpret_cast<float *>(dstep + 1);
@@ -57,7 +66,7 @@ __global__ void k_step_tick(long long *dstep, float b1, float b2, const DevStatu
 __global__ void __launch_bounds__(256) k_adam(SceneMut P, SceneView G, SceneMut M, SceneMut V, AdamArgs a,
                                               const DevStatus *status)
 {
-    if (status->code == GS_ERR_CAPACITY) return;   // the step's gradient is incomplete: skip the update
+    if (step_failed(status)) return;             // the step's gradient is incomplete: skip the update
     float bc1 = a.bc1, bc2 = a.bc2;
     if (a.dstep) {
         const float *bc = reinterpret_cast<const float *>(a.dstep + 1);

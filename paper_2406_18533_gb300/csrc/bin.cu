@@ -398,6 +398,7 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
         status->counters[1] = 0ull;
         status->counters[2] = 0ull;
         status->counters[4] = 0ull;
+        status->counters[5] = 0ull;
         if (F > capacity) {
             atomicCAS(&status->code, 0, (int)GS_ERR_CAPACITY);
             *count_out = 0u;
@@ -478,7 +479,10 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
 // shared memory in output order and writes them out so that consecutive
 // threads store consecutive addresses of a digit's run.  The look-back spin
 // is bounded: a wait that runs out sets GS_ERR_TIMEOUT and the pass finishes
-// with in-bounds (but wrong) positions instead of hanging.
+// with wrong positions instead of hanging.  Every store is checked against
+// the key count, so even a pass whose input came out of a failed pass (keys
+// duplicated or missing, so the up-front digit histogram no longer matches)
+// stays inside the buffers.
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 16;
@@ -489,8 +493,14 @@ constexpr int RS_MAX_NB = 512;
 constexpr uint32_t LB_AGG = 1u << 30;               // look-back flag: tile count available
 constexpr uint32_t LB_PRE = 2u << 30;               // look-back flag: inclusive prefix available
 constexpr uint32_t LB_VAL = (1u << 30) - 1u;
-constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;
+constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;        // default polls of one look-back wait
 constexpr int LB_BATCH = 8;                         // look-back words read per round
+
+// Test hooks (gs_debug_set_lookback): the spin limit, and whether tile 0 of
+// every pass withholds its look-back words (a flag nothing sets), so that a
+// test can make the bounded wait run out.
+uint32_t g_lb_spin_limit = LB_SPIN_LIMIT;
+int g_lb_withhold = 0;
 
 // Digit histograms of every pass.  A thread takes 16 consecutive keys (four
 // 16-byte loads: the key buffers are 16-byte aligned) and adds runs of equal
@@ -583,7 +593,8 @@ template <int RB>
 __global__ void __launch_bounds__(RS_THREADS, 4) k_onesweep(const uint32_t *kin, const uint32_t *vin,
                                                             uint32_t *kout, uint32_t *vout, const uint32_t *count,
                                                             int shift, const uint32_t *doff, uint32_t *look,
-                                                            uint32_t *tile_ctr, DevStatus *status)
+                                                            uint32_t *tile_ctr, DevStatus *status,
+                                                            uint32_t spin_limit, int withhold_first)
 {
     constexpr int NB = 1 << RB, DPT = NB / RS_THREADS;
     constexpr int UNION_WORDS = RS_WARPS * NB > 2 * RS_TILE ? RS_WARPS * NB : 2 * RS_TILE;
@@ -635,7 +646,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_onesweep(const uint32_t *kin,
             run += c;
         }
         cnt[k] = run;
-        atomicExch(look + (size_t)tile * NB + d, (tile == 0 ? LB_PRE : LB_AGG) | run);
+        if (!(withhold_first && tile == 0)) atomicExch(look + (size_t)tile * NB + d, (tile == 0 ? LB_PRE : LB_AGG) | run);
     }
     uint32_t tsum = 0;
 #pragma unroll
@@ -673,7 +684,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_onesweep(const uint32_t *kin,
                     const volatile uint32_t *q = look + (size_t)pt * NB + d;
                     bool timed_out = false;
                     while ((*q & (LB_AGG | LB_PRE)) == 0u) {
-                        if (++spins > LB_SPIN_LIMIT) {   // give up: report instead of hanging
+                        if (++spins > spin_limit) {      // give up: report instead of hanging
                             atomicCAS(&status->code, 0, (int)GS_ERR_TIMEOUT);
                             timed_out = true;
                             break;
@@ -710,8 +721,10 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_onesweep(const uint32_t *kin,
         if (idx < tile_n) {
             const uint32_t kk = skey[idx];
             const uint32_t dst = gofs[(kk >> shift) & (uint32_t)(NB - 1)] + idx;
-            kout[dst] = kk;
-            vout[dst] = sval[idx];
+            if (dst < n) {                            // always, unless an earlier pass failed
+                kout[dst] = kk;
+                vout[dst] = sval[idx];
+            }
         }
     }
 }
@@ -766,6 +779,12 @@ __global__ void __launch_bounds__(256) k_compose_keys(ViewBatch vb, int64_t N, c
 }
 
 }  // namespace
+
+void set_lookback_debug(uint32_t spin_limit, int withhold_first)
+{
+    g_lb_spin_limit = spin_limit ? spin_limit : LB_SPIN_LIMIT;
+    g_lb_withhold = withhold_first ? 1 : 0;
+}
 
 // Blocks of 256 threads for a grid-stride loop over `items`: enough to fill
 // every SM several times, no more (small blocks are bound by block launches).
@@ -895,7 +914,7 @@ static void radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint3
     for (int ps = 0; ps < passes; ++ps) {
         cudaMemsetAsync(look, 0, (size_t)tiles * NB * 4, st);
         k_onesweep<RB><<<(unsigned)tiles, RS_THREADS, 0, st>>>(ki, vi, ko, vo, count, RB * ps, ghist + NB * ps, look,
-                                                              ctr + ps, status);
+                                                              ctr + ps, status, g_lb_spin_limit, g_lb_withhold);
         count_launches(1);
         uint32_t *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;

@@ -41,17 +41,26 @@ constexpr int MAX_DEVICES = 64;
 unsigned char *g_scratch_ptr[MAX_DEVICES] = {};
 std::mutex g_scratch_mu;
 
-// Device address of the scratch array on the current device (set up once per
-// device, with that device current).
-gs_status scratch_on_current_device(unsigned char **out)
+// Device address of the scratch array on the current device, with that device
+// current.  Outside stream capture it is looked up on every call (a cheap
+// query that allocates nothing), so an address made stale by a
+// cudaDeviceReset is never used; during capture the address of the last call
+// outside capture on this device is used (module loading may not happen
+// inside a capture).
+gs_status scratch_on_current_device(cudaStream_t st, unsigned char **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
         cudaGetLastError();
         return GS_ERR_CUDA;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -108,10 +117,10 @@ extern "C" gs_status gs_bin_noalloc(const gs_proj *proj, const gs_camera *cams, 
     if (base >= ((uint64_t)1 << 31)) return GS_ERR_INVALID_ARG;
     vb.total_tiles = (uint32_t)base;
 
-    unsigned char *s = nullptr;
-    gs_status r = scratch_on_current_device(&s);
-    if (r != GS_OK) return r;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char *s = nullptr;
+    gs_status r = scratch_on_current_device(st, &s);
+    if (r != GS_OK) return r;
     auto *offsets = reinterpret_cast<uint32_t *>(s + OFF_OFFSETS);
     auto *rect = reinterpret_cast<uint2 *>(s + OFF_RECT);
     auto *area = reinterpret_cast<uint32_t *>(s + OFF_AREA);

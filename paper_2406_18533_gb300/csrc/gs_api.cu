@@ -16,6 +16,9 @@ using namespace gs;
 namespace gs {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+// Allocation-failure injection (gs_debug_fail_alloc): -1 off; n >= 0: that
+// many more device allocations succeed, the next one fails with GS_ERR_OOM.
+static std::atomic<long long> g_fail_alloc_after{-1};
 }  // namespace gs
 
 namespace {
@@ -70,6 +73,33 @@ gs_status cuda_check(gs_ctx *c, const char *where)
     return GS_OK;
 }
 
+// True when the allocation-failure injection says this allocation fails.
+bool injected_alloc_failure()
+{
+    long long n = g_fail_alloc_after.load();
+    while (n >= 0) {
+        if (n == 0) {
+            g_fail_alloc_after.store(-1);   // one failure, then off again
+            return true;
+        }
+        if (g_fail_alloc_after.compare_exchange_weak(n, n - 1)) return false;
+    }
+    return false;
+}
+
+// cudaMalloc through the injection point; out-of-memory and injected failures
+// give GS_ERR_OOM, other CUDA errors GS_ERR_CUDA.
+gs_status device_alloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (injected_alloc_failure()) return GS_ERR_OOM;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) return GS_OK;
+    cudaGetLastError();
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
+}
+
 gs_status ensure(gs_ctx *c, DBuf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
@@ -78,11 +108,8 @@ gs_status ensure(gs_ctx *c, DBuf &b, size_t bytes)
     b.p = nullptr;
     b.cap = 0;
     const size_t nb = ((bytes + bytes / 8) + 255) & ~(size_t)255;
-    if (cudaMalloc(&b.p, nb) != cudaSuccess) {
-        cudaGetLastError();
-        b.p = nullptr;
-        return fail(c, GS_ERR_OOM, "cudaMalloc of %zu bytes failed", nb);
-    }
+    const gs_status r = device_alloc(&b.p, nb);
+    if (r != GS_OK) return fail(c, r, "device allocation of %zu bytes failed", nb);
     b.cap = nb;
     return GS_OK;
 }
@@ -438,18 +465,38 @@ gs_status gs_create(gs_ctx **out, const gs_hparams *hp)
     if (hp) c->hp = *hp; else gs_default_hparams(&c->hp);
     gs_status r = check_hparams(c, &c->hp);
     if (r != GS_OK) { delete c; return r; }
-    if (cudaMalloc(&c->status, sizeof(DevStatus)) != cudaSuccess || cudaMalloc(&c->dstep, 2 * sizeof(long long)) != cudaSuccess ||
-        cudaMallocHost(&c->h_status, sizeof(DevStatus)) != cudaSuccess) {
+    void *st = nullptr, *ds = nullptr;
+    if ((r = device_alloc(&st, sizeof(DevStatus))) == GS_OK) c->status = static_cast<DevStatus *>(st);
+    if (r == GS_OK && (r = device_alloc(&ds, 2 * sizeof(long long))) == GS_OK) c->dstep = static_cast<long long *>(ds);
+    if (r == GS_OK && cudaMallocHost(&c->h_status, sizeof(DevStatus)) != cudaSuccess) {
         cudaGetLastError();
+        c->h_status = nullptr;
+        r = GS_ERR_CUDA;
+    }
+    if (r != GS_OK) {
         if (c->status) cudaFree(c->status);
+        if (c->dstep) cudaFree(c->dstep);
         delete c;
-        return GS_ERR_CUDA;
+        return r;
     }
     cudaMemset(c->status, 0, sizeof(DevStatus));
     cudaMemset(c->dstep, 0, 2 * sizeof(long long));
     memset(c->h_status, 0, sizeof(DevStatus));
     if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); }
     *out = c;
+    return GS_OK;
+}
+
+gs_status gs_debug_set_lookback(uint32_t spin_limit, int32_t withhold_first_tile)
+{
+    set_lookback_debug(spin_limit, withhold_first_tile);
+    return GS_OK;
+}
+
+gs_status gs_debug_fail_alloc(int64_t after)
+{
+    if (after < -1) return GS_ERR_INVALID_ARG;
+    g_fail_alloc_after.store(after);
     return GS_OK;
 }
 
@@ -498,7 +545,7 @@ gs_status gs_get_status(gs_ctx *c, void *stream, int32_t *status, uint64_t *need
     return GS_OK;
 }
 
-gs_status gs_get_counters(gs_ctx *c, void *stream, uint64_t out[5])
+gs_status gs_get_counters(gs_ctx *c, void *stream, uint64_t out[6])
 {
     if (!c || !out) return GS_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
@@ -510,6 +557,7 @@ gs_status gs_get_counters(gs_ctx *c, void *stream, uint64_t out[5])
     out[2] = c->h_status->counters[2];
     out[3] = c->h_status->counters[4];
     out[4] = c->h_status->counters[3];
+    out[5] = c->h_status->counters[5];
     return GS_OK;
 }
 

@@ -93,7 +93,8 @@ struct DevStatus {
     int32_t pad;
     unsigned long long needed;  // fragments requested by the last binning
     // F, forward (pixel, fragment) evaluations, backward blended pairs,
-    // Gaussians culled as non-finite, backward walked (pixel, position) pairs
+    // Gaussians culled as non-finite, backward walked (pixel, position) pairs,
+    // forward sum of n_contrib over the pixels
     unsigned long long counters[6];
 };
 
@@ -237,6 +238,10 @@ int fragment_sort_passes(int tile_bits);
 void launch_sort_fragments(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                            uint64_t capacity, const uint32_t *count, int tile_bits, void *temp, DevStatus *status,
                            cudaStream_t st);
+
+// Test hook (gs_debug_set_lookback): look-back spin limit (0 = default) and
+// whether tile 0 of every sort pass withholds its look-back words.
+void set_lookback_debug(uint32_t spin_limit, int withhold_first);
 
 void launch_tile_ranges(const uint32_t *keys, const uint32_t *count, uint64_t capacity, uint2 *ranges,
                         uint32_t total_tiles, cudaStream_t st);

@@ -279,10 +279,10 @@ class Context:
         return int(code.value), int(needed.value)
 
     def counters(self):
-        out = (ctypes.c_uint64 * 5)()
+        out = (ctypes.c_uint64 * 6)()
         self._c("gs_get_counters", self.h, _stream(), out)
         return dict(F=int(out[0]), evals_fwd=int(out[1]), evals_bwd=int(out[2]), walked_bwd=int(out[3]),
-                    culled_nonfinite=int(out[4]))
+                    culled_nonfinite=int(out[4]), contrib_positions=int(out[5]))
 
 
 class RasterizeGaussians(torch.autograd.Function):

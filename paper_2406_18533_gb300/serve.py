@@ -37,6 +37,7 @@ class Request:
     image: torch.Tensor | None = None
     done: float | None = None
     batch: int = -1
+    rejected: str | None = None   # why the request can never be served (then image is None)
 
     @property
     def pixels(self) -> int:
@@ -88,6 +89,18 @@ class RenderServer:
         torch.cuda.synchronize()
 
     # ---------------------------------------------------------------- dispatch
+    def _never_fits(self, r: Request, total_mem: int) -> str | None:
+        """Why a request can never be admitted, or None.  A request larger than
+        the batch pixel budget, or whose image needs more than the device's
+        whole memory minus the reserve, would wait at the head of the queue
+        forever and hold up every request behind it, so it is rejected when it
+        arrives."""
+        if r.pixels > self.max_pixels:
+            return f"{r.cam.W}x{r.cam.H} exceeds the batch budget of {self.max_pixels} pixels"
+        if 3 * 4 * r.pixels > total_mem - self.hbm_reserve:
+            return f"{r.cam.W}x{r.cam.H} needs more than the device memory minus the reserve"
+        return None
+
     def _admit(self, queue: collections.deque) -> list[Request]:
         free = torch.cuda.mem_get_info()[0] - self.hbm_reserve
         batch, pix = [], 0
@@ -135,11 +148,18 @@ class RenderServer:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         queue: collections.deque = collections.deque()
         finished: list[Request] = []
+        total_mem = torch.cuda.mem_get_info()[1]
         t0 = time.perf_counter()
         while pending or queue or any(s.busy for s in self.slots):
             now = time.perf_counter()
             while pending and pending[0].arrival <= now - t0:
-                queue.append(pending.popleft())
+                r = pending.popleft()
+                r.rejected = self._never_fits(r, total_mem)
+                if r.rejected:
+                    r.done = now - t0
+                    finished.append(r)
+                else:
+                    queue.append(r)
             for s in self.slots:
                 if s.busy and s.event.query():
                     finished += self._finish(s, time.perf_counter(), t0)
@@ -158,11 +178,14 @@ class RenderServer:
 
 
 def latency_report(reqs: list[Request], skip: int = 0) -> dict:
+    """Latency percentiles and throughput of the served requests (rejected
+    ones are counted separately)."""
     import numpy as np
-    rs = sorted(reqs, key=lambda r: r.arrival)[skip:]
+    rejected = sum(1 for r in reqs if r.rejected)
+    rs = sorted((r for r in reqs if not r.rejected), key=lambda r: r.arrival)[skip:]
     lat = np.array([(r.done - r.arrival) * 1e3 for r in rs])
     span = max(r.done for r in rs) - min(r.arrival for r in rs)
     pix = sum(r.pixels for r in rs)
     return {"requests": len(rs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "frames_per_s": len(rs) / span,
-            "mpix_per_s": pix / span / 1e6}
+            "mpix_per_s": pix / span / 1e6, "rejected": rejected}

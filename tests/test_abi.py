@@ -37,7 +37,7 @@ def test_binding_covers_every_entry_point(libgs):
 
 def test_abi_version_and_defaults(libgs):
     from paper_2406_18533_gb300 import binding
-    assert libgs.gs_abi_version() == 1
+    assert libgs.gs_abi_version() == 2
     hp = binding.default_hparams()
     assert hp.tile == 16 and hp.smem_batch == 64 and hp.px_per_thread == 1
     assert abs(hp.alpha_min - 1 / 255) < 1e-9 and abs(hp.alpha_max - 0.99) < 1e-7 and abs(hp.T_min - 1e-4) < 1e-10
@@ -128,3 +128,21 @@ def test_bin_noalloc_rejects_bad_arguments_on_host(libgs):
     assert call(cap=(1 << 20) + 1) == bad               # fragment capacity above the limit
     assert call(W=0) == bad                             # camera sizes checked on the host
     assert libgs.gs_bin_noalloc(None, cams, 1, 16, None, ctypes.byref(needed), None) == bad
+
+
+def test_injected_allocation_failure_gives_oom(libgs):
+    """The allocation-failure hook makes gs_create fail with GS_ERR_OOM before
+    any device call (so this runs without a GPU), returns no context, and
+    fires once."""
+    import ctypes
+    from paper_2406_18533_gb300 import binding as b
+    assert libgs.gs_debug_fail_alloc(-2) == b.GS_ERR_INVALID_ARG
+    assert libgs.gs_debug_fail_alloc(0) == b.GS_OK
+    h = ctypes.c_void_p(1)
+    assert libgs.gs_create(ctypes.byref(h), None) == b.GS_ERR_OOM
+    assert not h.value
+    st = libgs.gs_create(ctypes.byref(h), None)         # injection spent: reaches the device
+    assert st in (b.GS_OK, b.GS_ERR_CUDA)
+    if st == b.GS_OK:
+        libgs.gs_destroy(h)
+    assert libgs.gs_debug_set_lookback(0, 0) == b.GS_OK

@@ -321,7 +321,7 @@ def test_fp32_bounds_hold_for_a_float32_transformation(oracle, which):
     p32c = -0.5 * (cf[:, 0] * dx * dx + cf[:, 2] * dy * dy) - cf[:, 1] * dx * dy
     gx, gy = np.abs(a * dx + b * dy), np.abs(b * dx + c * dy)
     e = err[idx]
-    bound = 0.5 * e[:, 2] * (e[:, 3] * gx + e[:, 4] * gy) ** 2 + np.abs(p64) * e[:, 5]
+    bound = 0.5 * (gx * gx * e[:, 2] + 2 * gx * gy * e[:, 3] + gy * gy * e[:, 4]) + np.abs(p64) * e[:, 5]
     ratios["power"] = (np.abs(p32c - p64) / bound).max()
     print({k_: float(r) for k_, r in ratios.items()})
     for name, r in ratios.items():

@@ -1,7 +1,8 @@
 """The bench's parity gate (host logic) on CPU: a stand-in context whose
 render is the oracle's own whole-view image (rounded to float32) passes; an
-error of 1e-3 planted at an unflagged pixel of the compared window fails it;
-the same error outside the window does not count."""
+error of 1e-3 planted at any pixel of the compared window fails it, an
+ambiguous pixel (one with several admissible results) included; the same
+error outside the window does not count."""
 import os
 import sys
 
@@ -48,16 +49,24 @@ def test_gate_passes_on_the_oracle_image(setup):
     assert r["pixels"] == 256 * 256 and "(32,16)" in r["window"]
 
 
-def test_gate_fails_on_an_error_inside_the_window(setup):
+@pytest.mark.parametrize("ambiguous", [False, True])
+def test_gate_fails_on_an_error_inside_the_window(setup, ambiguous):
     bench, oracle, sc, cam, full = setup
     x0, y0 = 32, 16
-    win = oracle.render_window(sc, cam, (x0, y0, 256, 256))
-    flag, _ = oracle.fp32_flags(win, 256, 256)
-    ys, xs = np.nonzero(~flag)
+    win = oracle.render_window_admissible(sc, cam, (x0, y0, 256, 256))
+    ys, xs = np.nonzero(((win["flags"] & 1) > 0) == ambiguous)
+    assert len(ys) > 0
     img = full["img"].copy()
-    img[1, y0 + ys[len(ys) // 2], x0 + xs[len(xs) // 2]] += 1e-3
+    py, px = ys[len(ys) // 2], xs[len(xs) // 2]
+    p = py * 256 + px
+    alts = win["alt"][win["alt_off"][p]:win["alt_off"][p + 1], 1]
+    # 1e-3 away from the exact result and from every other admissible one
+    step = 1e-3
+    while np.any(np.abs(full["img"][1, y0 + py, x0 + px] + step - alts) < 1e-3):
+        step += 1e-3
+    img[1, y0 + py, x0 + px] += step
     r = bench.parity_gate(_Ctx(img), _Params(sc), [cam])
-    assert not r["pass"] and r["max_abs_err"] >= 1e-3 - 1e-6
+    assert not r["pass"] and r["max_abs_err"] >= 1e-3 - 1e-6 and r["unchecked_px"] == 0
     out = full["img"].copy()
     out[1, 5, 5] += 1e-3                                 # outside the window (x < 32)
     assert bench.parity_gate(_Ctx(out), _Params(sc), [cam])["pass"]

@@ -55,3 +55,37 @@ def test_latency_report():
     span = rs[-1].done - rs[2].arrival
     assert rep["frames_per_s"] == pytest.approx(8 / span)
     assert rep["mpix_per_s"] == pytest.approx(8 * 1000 / span / 1e6)
+
+
+def test_a_request_that_can_never_fit_is_rejected_on_arrival(monkeypatch):
+    """A request above the batch pixel budget (or above the device memory
+    minus the reserve) is rejected when it arrives instead of blocking the
+    queue: the requests behind it are still served."""
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a: (1 << 30, 1 << 30))
+    s = _server(max_batch=4, max_pixels=640 * 360 * 2, reserve=0)
+    launched = []
+
+    class _Slot:
+        busy = []
+
+    s.slots = [_Slot()]
+    s.batches = 0
+
+    def launch(slot, batch):
+        launched.append([r.rid for r in batch])
+        for r in batch:
+            r.done = 0.0
+        s.batches += 1
+
+    s._launch = launch
+    reqs = [_req(0, 0.0, 3840, 2160), _req(1, 0.0, 640, 360), _req(2, 0.0, 640, 360)]
+    done = s.run(reqs)
+    assert [r.rid for r in done if r.rejected] == [0] and "exceeds" in done[0].rejected
+    assert launched == [[1, 2]]
+    big = _server(max_batch=4, max_pixels=1 << 40, reserve=(1 << 30) - 2000)
+    assert big._never_fits(_req(3, 0.0, 640, 360), 1 << 30)
+    assert big._never_fits(_req(4, 0.0, 10, 10), 1 << 30) is None
+    for r in reqs[1:]:
+        r.done = 0.001
+    rep = serve.latency_report(reqs)
+    assert rep["rejected"] == 1 and rep["requests"] == 2

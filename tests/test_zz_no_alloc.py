@@ -31,12 +31,13 @@ def _upload(eng, pjs):
     return eng.Proj(t("xy", np.float32), t("conic_o", np.float32), t("rgb_d", np.float32), t("radius", np.int32))
 
 
-def _noalloc(eng, proj, cams, tile, bins):
+def _noalloc(eng, proj, cams, tile, bins, with_needed=True):
     from paper_2406_18533_gb300 import binding as b
     needed = ctypes.c_uint64(0)
     ps, bs = proj.struct(), bins.struct()
     st = b.lib().gs_bin_noalloc(ctypes.byref(ps), b.camera_array(cams), len(cams), tile, ctypes.byref(bs),
-                                ctypes.byref(needed), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+                                ctypes.byref(needed) if with_needed else None,
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     return st, int(needed.value)
 
 
@@ -76,6 +77,12 @@ def test_noalloc_binning_reports_capacity_and_limits(eng):
     small = eng.Bins.empty(16, eng.total_tiles(cams, tile))
     st, needed = _noalloc(eng, proj, cams, tile, small)
     assert st == b.GS_ERR_CAPACITY and needed == ref.F
+    # without needed_host the overflow is only visible as *count == 0 (documented):
+    # the call returns GS_OK and writes nothing past the capacity
+    small.count.fill_(12345)
+    st, _ = _noalloc(eng, proj, cams, tile, small, with_needed=False)
+    torch.cuda.synchronize()
+    assert st == b.GS_OK and int(small.count.item()) == 0
     # beyond the fixed scratch: rejected on the host before any work
     big = eng.Bins.empty(16, eng.total_tiles(cams, tile))
     big.keys = torch.empty(b.NOALLOC_MAX_FRAGS + 1, dtype=torch.int64, device="cuda")
