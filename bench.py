@@ -334,7 +334,8 @@ def run_ours(args, rank, world, local_rank):
         args.tile, args.batch, args.ppt = best["tile"], best["smem_batch"], best["px_per_thread"]
         tuned = {"chosen": best, "trials_ms": {f"t{t.tile}_b{t.smem_batch}_p{t.px_per_thread}": round(t.ms, 3)
                                                for t in trials}}
-    ctx = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt)
+    ctx = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt,
+                         sparse_adam=int(args.sparse_adam))
     G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
     loss = torch.empty(Bv, dtype=torch.float32, device="cuda")
     cam_arr = binding.camera_array(cams)
@@ -421,7 +422,8 @@ def run_ours(args, rank, world, local_rank):
     # per-view: the same scene stepped one view at a time over the same views
     per_view = None
     if Bv > 1 and not args.no_per_view:
-        ctx1 = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt)
+        ctx1 = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt,
+                              sparse_adam=int(args.sparse_adam))
         P1 = P.clone()
         G1, M1, V1 = P1.zeros_like(), P1.zeros_like(), P1.zeros_like()
         loss1 = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -552,6 +554,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": name, "gaussians": sc.N, "views_per_step": Bv, "resolution": f"{W}x{H}",
                    "tile": args.tile, "smem_batch": args.batch, "px_per_thread": args.ppt, "autotune": tuned,
                    "sh_degree": 3,
+                   "adam": "visible-only" if args.sparse_adam else "dense (every Gaussian, the paper's)",
                    "l2": "no flush: params + grad + Adam moments resident in HBM exceed the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "mpix_per_s": value * H * W / 1e6, "cuda_graph": bool(args.graph),
@@ -675,6 +678,8 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="call gs_train_step directly instead of replaying one captured step (CUDA graph)")
     ap.add_argument("--views", type=int, default=0, help="use only the first K views of the workload (profiling)")
+    ap.add_argument("--sparse-adam", action="store_true",
+                    help="visible-only Adam (Gaussians no view of the batch sees keep p, m, v)")
     args = ap.parse_args()
     # the batched training workloads pick their blending shape with the autotuner
     # unless a shape is given; the single-view and serving workloads use the defaults

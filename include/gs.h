@@ -99,7 +99,9 @@ typedef struct gs_hparams {
     float lambda_dssim;       /* loss = (1-l) L1 + l (1 - SSIM), l = 0.2 */
     int32_t px_per_thread;    /* pixels a blending thread owns: 1 (a warp blends an 8x4 block),
                                  2 (8x8) or 4 (8x16, tile 16 or 32) */
-    int32_t reserved;
+    int32_t sparse_adam;      /* 0: Adam over every Gaussian (the paper's optimizer, default);
+                                 1: gs_train_step updates only the Gaussians some view of the
+                                 batch sees (visible-only Adam, see gs_adam_step_sparse) */
 } gs_hparams;
 
 /*
@@ -319,11 +321,28 @@ gs_status gs_adam_step(gs_ctx *ctx, gs_scene *p, const gs_scene *g, gs_scene *m,
                        int64_t step, int32_t B, void *stream);
 
 /*
+ * Visible-only ("sparse") Adam: the update of gs_adam_step applied only to
+ * the Gaussians with visible[i] != 0; the others keep p, m and v exactly as
+ * they were (their moments do not decay).  The paper observes that the
+ * gradient of a batch is sparse, each view seeing a small part of the scene
+ * (Sec. 4); a Gaussian no view of the batch sees has a zero gradient, and
+ * dense Adam spends its 1652 bytes of traffic per Gaussian on it anyway.
+ * visible: device array of p->N bytes (caller-owned).  The step's bias
+ * correction is the batch count as in gs_adam_step (step == 0: the device
+ * counter); a pending GS_ERR_CAPACITY or GS_ERR_TIMEOUT skips the update.
+ */
+gs_status gs_adam_step_sparse(gs_ctx *ctx, gs_scene *p, const gs_scene *g, gs_scene *m, gs_scene *v,
+                              const uint8_t *visible, int64_t step, int32_t B, void *stream);
+
+/*
  * One whole training iteration over a batch of B views (Fig. 1(a) pipeline,
  * batched as in Sec. 4): transformation, binning, compositing, loss,
  * backward, Adam.  targets: [B][3][H][W] float device; loss_out: [B] float
  * device.  Scratch comes from the context.  g receives the batch gradient.
- * step as in gs_adam_step (0: device counter).  Once the context has sized its
+ * step as in gs_adam_step (0: device counter).  With hp.sparse_adam = 1 the
+ * optimizer is gs_adam_step_sparse with visible = "some view of the batch has
+ * the Gaussian's radius > 0", and g's rows of the unseen Gaussians are left
+ * as they were (not written).  Once the context has sized its
  * scratch (a first call, or gs_reserve), the call allocates nothing and never
  * synchronises, so it can be captured in a CUDA graph; the graph replays the
  * captured cameras.

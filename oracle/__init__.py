@@ -448,32 +448,44 @@ def lane_lr(lr6):
 
 
 def adam(p, g, m, v, step, lr6, beta1=0.9, beta2=0.999, eps=1e-15, batch=1,
-         scale_lr_sqrt_b=True, scale_beta_pow_b=True):
+         scale_lr_sqrt_b=True, scale_beta_pow_b=True, visible=None):
     """One Adam step on [N, 60] arrays (FP64).  lr' = lr sqrt(B) (Eq. 1),
     beta' = beta^B (Eq. 2), bias correction with the betas actually used.
-    Returns (p, m, v) as new arrays."""
+    ``visible`` [N] (optional): visible-only Adam -- rows with visible False
+    keep p, m and v unchanged (no update, no decay of the moments); the
+    others take the step above.  Returns (p, m, v) as new arrays."""
     b1 = beta1 ** batch if scale_beta_pow_b else beta1
     b2 = beta2 ** batch if scale_beta_pow_b else beta2
     lr = lane_lr(lr6) * (math.sqrt(batch) if scale_lr_sqrt_b else 1.0)
-    p = np.asarray(p, np.float64)
+    p0 = np.asarray(p, np.float64)
+    m0 = np.asarray(m, np.float64)
+    v0 = np.asarray(v, np.float64)
     g = np.asarray(g, np.float64)
-    m = b1 * np.asarray(m, np.float64) + (1 - b1) * g
-    v = b2 * np.asarray(v, np.float64) + (1 - b2) * g * g
+    m = b1 * m0 + (1 - b1) * g
+    v = b2 * v0 + (1 - b2) * g * g
     mh = m / (1 - b1 ** step)
     vh = v / (1 - b2 ** step)
-    return p - lr * mh / (np.sqrt(vh) + eps), m, v
+    p = p0 - lr * mh / (np.sqrt(vh) + eps)
+    if visible is not None:
+        keep = ~np.asarray(visible, bool)
+        p[keep], m[keep], v[keep] = p0[keep], m0[keep], v0[keep]
+    return p, m, v
 
 
-def train_step(scene, cams, targets, m, v, step, lr6, tile=16, **adam_kw):
+def train_step(scene, cams, targets, m, v, step, lr6, tile=16, sparse=False, **adam_kw):
     """One batched training step: per view render + loss + backward, mean of
-    the per-view parameter gradients over the batch, Adam.  Returns
-    (new_flat_params [N,60], m, v, losses[B], grad [N,60])."""
+    the per-view parameter gradients over the batch, Adam.  sparse=True:
+    visible-only Adam, a Gaussian being visible when some view of the batch
+    gives it a tile rectangle (radius > 0).  Returns (new_flat_params
+    [N,60], m, v, losses[B], grad [N,60])."""
     B = len(cams)
     N = scene.N
     grad = np.zeros((N, 60))
     losses = []
+    visible = np.zeros(N, bool)
     for b, cam in enumerate(cams):
         fw = render(scene, cam, tile)
+        visible |= fw["proj"]["vis"] > 0
         L, dimg, _, _ = ssim_loss(fw["img"], targets[b])
         losses.append(L)
         pr = fw["proj"]
@@ -481,5 +493,5 @@ def train_step(scene, cams, targets, m, v, step, lr6, tile=16, **adam_kw):
         grad += preprocess_bwd(scene, cam, g2d, tile)
     grad /= B
     p = scene.flat().astype(np.float64)
-    p2, m2, v2 = adam(p, grad, m, v, step, lr6, batch=B, **adam_kw)
+    p2, m2, v2 = adam(p, grad, m, v, step, lr6, batch=B, visible=visible if sparse else None, **adam_kw)
     return p2, m2, v2, np.array(losses), grad

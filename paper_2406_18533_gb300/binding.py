@@ -32,7 +32,7 @@ class gs_hparams(ctypes.Structure):
                 ("bg", ctypes.c_float * 3), ("lr", ctypes.c_float * 6), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("scale_lr_sqrt_b", ctypes.c_int32),
                 ("scale_beta_pow_b", ctypes.c_int32), ("lambda_dssim", ctypes.c_float),
-                ("px_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("px_per_thread", ctypes.c_int32), ("sparse_adam", ctypes.c_int32)]
 
 
 class gs_proj(ctypes.Structure):
@@ -78,6 +78,7 @@ SIGNATURES = {
     "gs_render_bwd": [_vp, P(gs_proj), P(gs_bins), P(gs_camera), _i32, _vp, _vp, _vp, P(gs_proj_grad), _vp],
     "gs_preprocess_bwd": [_vp, P(gs_scene), P(gs_camera), _i32, P(gs_proj), P(gs_proj_grad), P(gs_scene), _vp],
     "gs_loss": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
+    "gs_adam_step_sparse": [_vp, P(gs_scene), P(gs_scene), P(gs_scene), P(gs_scene), _vp, _i64, _i32, _vp],
     "gs_adam_step": [_vp, P(gs_scene), P(gs_scene), P(gs_scene), P(gs_scene), _i64, _i32, _vp],
     "gs_train_step": [_vp, P(gs_scene), P(gs_scene), P(gs_scene), P(gs_scene), _i64, P(gs_camera), _i32, _vp, _vp,
                       _vp],

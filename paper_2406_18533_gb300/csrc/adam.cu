@@ -86,20 +86,28 @@ __global__ void __launch_bounds__(256) k_adam(SceneMut P, SceneView G, SceneMut 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.N; i += 2 * stride) {
         const int64_t i2 = i + stride;
-        const bool two = i2 < P.N;
-        float4 p = pp[i], m = mp[i], v = vp[i];
-        const float4 g = gp[i];
-        float4 p2, m2, v2, g2;
+        // visible-only Adam: an unseen Gaussian's p, m, v are neither read nor written
+        const bool one = !a.vis || a.vis[i];
+        const bool two = i2 < P.N && (!a.vis || a.vis[i2]);
+        float4 p, m, v, g, p2, m2, v2, g2;
+        if (one) {
+            p = pp[i];
+            m = mp[i];
+            v = vp[i];
+            g = gp[i];
+        }
         if (two) {
             p2 = pp[i2];
             m2 = mp[i2];
             v2 = vp[i2];
             g2 = gp[i2];
         }
-        adam4(p, g, m, v, lr, a.b1, a.b2, ibc1, ibc2, a.eps);
-        pp[i] = p;
-        mp[i] = m;
-        vp[i] = v;
+        if (one) {
+            adam4(p, g, m, v, lr, a.b1, a.b2, ibc1, ibc2, a.eps);
+            pp[i] = p;
+            mp[i] = m;
+            vp[i] = v;
+        }
         if (two) {
             adam4(p2, g2, m2, v2, lr, a.b1, a.b2, ibc1, ibc2, a.eps);
             pp[i2] = p2;

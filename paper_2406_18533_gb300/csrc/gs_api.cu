@@ -46,6 +46,7 @@ struct gs_ctx {
     DBuf xy, conic_o, rgb_d, radius, g_proj, keys, vals, ranges, count;
     DBuf img, dimg, T_final, n_contrib, maps, acc;
     DBuf tile_order;               // blending launch order (tiles) + 64 words of counters
+    DBuf vis;                      // visible-only Adam: one byte per Gaussian
     uint64_t frag_cap = 0;
     // tracing: events around the stages of gs_train_step
     int trace_max = 0, trace_step = 0;
@@ -331,6 +332,7 @@ gs_status ensure_train(gs_ctx *c, int64_t N, const ViewBatch &vb)
     const size_t pix = (size_t)vb.B * vb.v[0].W * vb.v[0].H;
     gs_status r;
     if ((r = ensure(c, c->g_proj, 48 * n)) != GS_OK) return r;
+    if (c->hp.sparse_adam && (r = ensure(c, c->vis, (size_t)(N > 0 ? N : 1))) != GS_OK) return r;
     if ((r = ensure(c, c->img, 12 * pix)) || (r = ensure(c, c->dimg, 12 * pix)) || (r = ensure(c, c->maps, 36 * pix)) ||
         (r = ensure(c, c->acc, 16 * (size_t)vb.B + 64)))
         return r;
@@ -354,6 +356,7 @@ AdamArgs adam_args(const gs_hparams &hp, int64_t step, int32_t B, long long *dst
 {
     AdamArgs a;
     a.dstep = step == 0 ? dstep : nullptr;
+    a.vis = nullptr;
     if (step == 0) step = 1;   // placeholders; the kernel computes the corrections
     const double b1 = hp.scale_beta_pow_b ? pow((double)hp.beta1, B) : hp.beta1;
     const double b2 = hp.scale_beta_pow_b ? pow((double)hp.beta2, B) : hp.beta2;
@@ -381,6 +384,7 @@ gs_status check_hparams(gs_ctx *c, const gs_hparams *hp)
     if (ilog2_exact(hp->tile) < 0) return fail(c, GS_ERR_INVALID_ARG, "tile must be 8, 16 or 32");
     if (hp->px_per_thread != 1 && hp->px_per_thread != 2 && hp->px_per_thread != 4)
         return fail(c, GS_ERR_INVALID_ARG, "px_per_thread must be 1, 2 or 4");
+    if (hp->sparse_adam != 0 && hp->sparse_adam != 1) return fail(c, GS_ERR_INVALID_ARG, "sparse_adam must be 0 or 1");
     if (!blend_config_ok(hp->tile, hp->smem_batch, hp->px_per_thread))
         return fail(c, GS_ERR_INVALID_ARG,
                     "unsupported (tile, smem_batch, px_per_thread): smem_batch 32, 64 or 128 (32 or 64 with tile 32 "
@@ -507,7 +511,7 @@ gs_status gs_destroy(gs_ctx *c)
                     &c->pk, &c->pv, &c->pk_alt, &c->pv_alt, &c->rect, &c->kmask, &c->rmask,
                     &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_proj, &c->keys,
                     &c->vals, &c->ranges, &c->count, &c->img, &c->dimg, &c->T_final, &c->n_contrib, &c->maps,
-                    &c->acc, &c->tile_order};
+                    &c->acc, &c->tile_order, &c->vis};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     trace_free(c);
@@ -592,7 +596,8 @@ gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *ca
     const size_t n = (size_t)B * (size_t)N;
     size_t s = n * (8 + 16 + 16 + 4 + 4 + 4 + 16 + 8 + 8 + 16 + 48) + frag_capacity * (8 * 2) +
                sort_temp_bytes((uint64_t)n, frag_capacity) +
-               scan_temp_bytes((int64_t)n) + tiles * (8 + 4) + 256 + pix * (4 + 4 + 12 + 12 + 36) + 4096;
+               scan_temp_bytes((int64_t)n) + tiles * (8 + 4) + 256 + pix * (4 + 4 + 12 + 12 + 36) + 4096 +
+               (h.sparse_adam ? (size_t)N : 0);
     *bytes = s;
     return GS_OK;
 }
@@ -701,7 +706,7 @@ gs_status gs_preprocess_bwd(gs_ctx *c, const gs_scene *scene, const gs_camera *c
     if (r != GS_OK) return r;
     GradView gv{reinterpret_cast<float4 *>(dproj->d_xy_o), reinterpret_cast<float4 *>(dproj->d_conic),
                 reinterpret_cast<float4 *>(dproj->d_rgb)};
-    launch_preprocess_bwd(view_of(scene), vb, proj_of(proj), gv, true, mut_of(grad), S(stream));
+    launch_preprocess_bwd(view_of(scene), vb, proj_of(proj), gv, true, mut_of(grad), nullptr, S(stream));
     return cuda_check(c, "gs_preprocess_bwd");
 }
 
@@ -729,6 +734,21 @@ gs_status gs_adam_step(gs_ctx *c, gs_scene *p, const gs_scene *g, gs_scene *m, g
     if (step < 0 || B < 1) return fail(c, GS_ERR_INVALID_ARG, "step must be >= 0 and B >= 1");
     launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), adam_args(c->hp, step, B, c->dstep), c->status, S(stream));
     return cuda_check(c, "gs_adam_step");
+}
+
+gs_status gs_adam_step_sparse(gs_ctx *c, gs_scene *p, const gs_scene *g, gs_scene *m, gs_scene *v,
+                              const uint8_t *visible, int64_t step, int32_t B, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(p) || !scene_ok(g) || !scene_ok(m) || !scene_ok(v) || g->N != p->N || m->N != p->N ||
+        v->N != p->N)
+        return fail(c, GS_ERR_INVALID_ARG, "bad parameter / moment planes");
+    if (step < 0 || B < 1) return fail(c, GS_ERR_INVALID_ARG, "step must be >= 0 and B >= 1");
+    if (!visible && p->N > 0) return fail(c, GS_ERR_INVALID_ARG, "visible is NULL");
+    AdamArgs a = adam_args(c->hp, step, B, c->dstep);
+    a.vis = visible;
+    launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), a, c->status, S(stream));
+    return cuda_check(c, "gs_adam_step_sparse");
 }
 
 gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_scene *v, int64_t step,
@@ -787,9 +807,12 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
                      gv, c->status, order, st);
     mark(c, st, 9);
-    launch_preprocess_bwd(sv, vb, pv, gv, false, mut_of(g), st);
+    uint8_t *vis = c->hp.sparse_adam ? ptr<uint8_t>(c->vis) : nullptr;
+    launch_preprocess_bwd(sv, vb, pv, gv, false, mut_of(g), vis, st);
     mark(c, st, 10);
-    launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), adam_args(c->hp, step, B, c->dstep), c->status, st);
+    AdamArgs aa = adam_args(c->hp, step, B, c->dstep);
+    aa.vis = vis;
+    launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), aa, c->status, st);
     mark(c, st, 11);
     if (c->trace_on) ++c->trace_step;
     c->trace_on = false;

@@ -107,8 +107,10 @@ void count_launches(int n);
 void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, uint32_t *ntiles,
                            uint2 *rect, DevStatus *status, int strict, cudaStream_t st);
 // g holds the blending backward's moments (GradView) unless grads_ready.
+// vis (optional): vis[g] = 1 if some view has the Gaussian's radius > 0,
+// else 0; with vis the rows of unseen Gaussians are not written.
 void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
-                           bool grads_ready, const SceneMut &out, cudaStream_t st);
+                           bool grads_ready, const SceneMut &out, uint8_t *vis, cudaStream_t st);
 // In place: the moments of n entries -> gradients (moments_to_grads).
 void launch_moments_to_grads(const ProjView &p, int64_t n, const GradView &g, cudaStream_t st);
 
@@ -274,6 +276,7 @@ struct AdamArgs {
     float bc1, bc2;    // 1 - b1^t, 1 - b2^t (host step)
     long long *dstep;  // non-null: [0] step counter on the device, ticked before the update;
                        // [1] holds the float bias corrections the tick computes
+    const uint8_t *vis; // non-null: only Gaussians with vis[i] != 0 are updated (visible-only Adam)
 };
 void launch_adam(const SceneMut &p, const SceneView &g, const SceneMut &m, const SceneMut &v, const AdamArgs &a,
                  const DevStatus *status, cudaStream_t st);

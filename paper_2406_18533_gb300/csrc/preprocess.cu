@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256) k_moments_to_grads(ProjView p, int64_t n,
 // Capped for 3 resident blocks (168 registers; uncapped it takes 181 and
 // fits 2): C3 8.4 -> 6.4 ms.
 __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatch vb, ProjView p, GradView gv,
-                                                        bool grads_ready, SceneMut out)
+                                                        bool grads_ready, SceneMut out, uint8_t *vis)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= s.N) return;
@@ -263,6 +263,10 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatc
     bool any = false;
     for (int v = 0; v < vb.B; ++v) any |= p.radius[(int64_t)v * s.N + g] > 0;
     const float invB = 1.f / (float)vb.B;
+    if (vis) {                                   // visible-only Adam: unseen rows stay unwritten
+        vis[g] = any ? 1 : 0;
+        if (!any) return;
+    }
     if (!any) {
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         out.mo[g] = z4; out.ls[g] = z4; out.q[g] = z4;
@@ -446,12 +450,12 @@ void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjVi
 }
 
 void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
-                           bool grads_ready, const SceneMut &out, cudaStream_t st)
+                           bool grads_ready, const SceneMut &out, uint8_t *vis, cudaStream_t st)
 {
     if (s.N == 0) return;
     const int threads = 128;
     const int64_t blocks = (s.N + threads - 1) / threads;
-    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, g, grads_ready, out);
+    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, g, grads_ready, out, vis);
     count_launches(1);
 }
 

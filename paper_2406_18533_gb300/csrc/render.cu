@@ -420,116 +420,6 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1)) k_blend_
         n += __popc(bal);
         if (n <= CH - 32 && hi - 32 > (int64_t)rg.x) continue;
         __syncwarp();
-#ifdef GS_BWD_LANES
-        if constexpr (PPT <= 2 && CH <= 64) {
-            // Pass 1: each lane marks the staged entries its pixels pass
-            // (bit i of mk[k]), and the warp marks the entries that many lanes
-            // pass (dense).  Pass 2: every lane walks its own marked entries
-            // in order, so lanes whose pixels blend different entries work at
-            // the same time; dense entries are walked by the whole warp
-            // together, in their place in the order, and reduced before
-            // their atomics.
-            uint64_t mk[PPT], dense = 0ull;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) mk[k] = 0ull;
-            for (int i = 0; i < n; ++i) {
-                const float4 xyc = s_xyc[i];
-                const uint32_t rel = __float_as_uint(xyc.w);
-                const float4 q = s_q[i];
-                const DxTerms dt = dx_terms(q, __fsub_rn(ps.fx, xyc.x));
-                bool pass_any = false;
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    if (!(rel < nc[k])) continue;
-                    ++walked;
-                    const float pw = power2(q, dt, __fsub_rn(ps.fy[k], xyc.y));
-                    if (pw >= xyc.z && pw <= 0.f) {
-                        mk[k] |= 1ull << i;
-                        pass_any = true;
-                    }
-                }
-                if (__popc(__ballot_sync(0xffffffffu, pass_any)) > DIRECT_UP_TO) dense |= 1ull << i;
-            }
-            // one entry for this lane's pixels: blend, and return the sums
-            auto blend_entry = [&](int i, float vv[8], float &gbl) -> bool {
-                const float4 xyc = s_xyc[i];
-                const float4 q = s_q[i];
-                const float dx = __fsub_rn(ps.fx, xyc.x);
-                const DxTerms dt = dx_terms(q, dx);
-                bool any = false;
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    if (!((mk[k] >> i) & 1ull)) continue;
-                    const float dy = __fsub_rn(ps.fy[k], xyc.y);
-                    const float pw = power2(q, dt, dy);
-                    const float G = ex2(pw);
-                    const float oG = q.w * G;
-                    const float alpha = fminf(bp.alpha_max, oG);
-                    if (alpha < bp.alpha_min) continue;
-                    any = true;
-                    ++evals;
-                    const float4 rgb = s_rgb[i];
-                    const float Tj = __fdividef(T[k], 1.f - alpha);
-                    const float w = alpha * Tj;
-                    vv[6] += w * dC0[k];
-                    vv[7] += w * dC1[k];
-                    gbl += w * dC2[k];
-                    const float e0 = rgb.x - B0[k], e1 = rgb.y - B1[k], e2 = rgb.z - B2[k];
-                    const float dalpha = Tj * (e0 * dC0[k] + e1 * dC1[k] + e2 * dC2[k]);
-                    B0[k] += alpha * e0;
-                    B1[k] += alpha * e1;
-                    B2[k] += alpha * e2;
-                    T[k] = Tj;
-                    if (oG < bp.alpha_max) {
-                        const float dpow = alpha * dalpha;
-                        const float dpx = dpow * dx, dpy = dpow * dy;
-                        vv[0] += dpow;
-                        vv[1] += dpx;
-                        vv[2] += dpy;
-                        vv[3] = fmaf(dpx, dx, vv[3]);
-                        vv[4] = fmaf(dpx, dy, vv[4]);
-                        vv[5] = fmaf(dpy, dy, vv[5]);
-                    }
-                }
-                return any;
-            };
-            uint64_t mine = mk[0];
-#pragma unroll
-            for (int k = 1; k < PPT; ++k) mine |= mk[k];
-            uint64_t todo = dense;
-            while (true) {
-                const int d = todo ? __ffsll((long long)todo) - 1 : 64;   // warp-uniform
-                const uint64_t below = d == 64 ? ~0ull : ((1ull << d) - 1ull);
-                uint64_t rem = mine & below & ~dense;
-                while (rem) {                                    // this lane's sparse entries before d
-                    const int i = __ffsll((long long)rem) - 1;
-                    rem &= rem - 1ull;
-                    float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                    float gbl = 0.f;
-                    if (blend_entry(i, vv, gbl)) add_sums(gv, vbase + __float_as_uint(s_rgb[i].w), vv, gbl);
-                }
-                if (d == 64) break;
-                __syncwarp();
-                float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                float gbl = 0.f;
-                const bool any = ((mine >> d) & 1ull) && blend_entry(d, vv, gbl);
-                const uint32_t ballot = __ballot_sync(0xffffffffu, any);
-                if (ballot) {
-                    const int64_t idx = vbase + __float_as_uint(s_rgb[d].w);
-                    if (__popc(ballot) <= DIRECT_UP_TO) {
-                        if (any) add_sums(gv, idx, vv, gbl);
-                    } else {
-                        const float cur[9] = {vv[0], vv[1], vv[2], vv[3], vv[4], vv[5], vv[6], vv[7], gbl};
-                        flush_one(gv, idx, cur, lane);
-                    }
-                }
-                todo &= todo - 1ull;
-            }
-            n = 0;
-            __syncwarp();
-            continue;
-        }
-#endif
         for (int i = 0; i < n; ++i) {
             const float4 xyc = s_xyc[i];
             const uint32_t rel = __float_as_uint(xyc.w);

@@ -232,6 +232,14 @@ class Context:
         self._c("gs_adam_step", self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm), ctypes.byref(sv),
                 int(step), int(batch), _stream())
 
+    def adam_step_sparse(self, p: DeviceScene, g: DeviceScene, m: DeviceScene, v: DeviceScene,
+                         visible: torch.Tensor, step: int, batch: int):
+        if visible.dtype != torch.uint8 or not visible.is_cuda or visible.numel() != p.N:
+            raise ValueError("visible must be a CUDA uint8 tensor with one entry per Gaussian")
+        sp, sg, sm, sv = p.struct(), g.struct(), m.struct(), v.struct()
+        self._c("gs_adam_step_sparse", self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm),
+                ctypes.byref(sv), _ptr(visible), int(step), int(batch), _stream())
+
     def train_step(self, p, g, m, v, step, cams, targets, loss_out=None, cam_arr=None, check=False):
         """One gs_train_step.  check=True synchronises, and when the fragment
         buffer overflowed (the library then skipped the update) grows it and

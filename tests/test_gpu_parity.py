@@ -257,6 +257,88 @@ def test_adam_stage(eng, oracle, Bv, step):
     assert rel_l2(dp_gpu, dp_ref) < 1e-3
 
 
+def test_adam_sparse_stage(eng, oracle):
+    """gs_adam_step_sparse: the visible rows take dense Adam's step (against
+    the oracle's visible-only Adam), the others keep p, m, v bit for bit."""
+    N = 6000
+    rng = np.random.default_rng(12)
+    def rs():
+        return synth.Scene(rng.standard_normal((N, 4)).astype(np.float32), rng.standard_normal((N, 4)).astype(np.float32),
+                           rng.standard_normal((N, 4)).astype(np.float32),
+                           rng.standard_normal((12, N, 4)).astype(np.float32))
+    p, g, m, v = rs(), rs(), rs(), rs()
+    for a in (v.mo, v.ls, v.q, v.sh):
+        np.abs(a, out=a)
+    for s_ in (p, g, m, v):
+        s_.ls[:, 3] = 0
+    vis = rng.random(N) < 0.3
+    lr6 = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3, 2.5e-4)
+    ctx = eng.Context(lr=lr6)
+    P, G, M, V = (eng.DeviceScene.from_host(s_) for s_ in (p, g, m, v))
+    P0, M0, V0 = P.flat().clone(), M.flat().clone(), V.flat().clone()
+    ctx.adam_step_sparse(P, G, M, V, torch.from_numpy(vis.astype(np.uint8)).cuda(), 3, 4)
+    rp, rm, rv = oracle.adam(p.flat(), g.flat(), m.flat(), v.flat(), 3, lr6, batch=4, visible=vis)
+    out = [t.flat() for t in (P, M, V)]
+    kv = torch.from_numpy(~vis).cuda()
+    for got, before in zip(out, (P0, M0, V0)):
+        assert torch.equal(got[kv], before[kv])
+    assert rel_l2(out[1].cpu().numpy()[vis], rm[vis]) < 1e-6
+    assert rel_l2(out[2].cpu().numpy()[vis], rv[vis]) < 1e-6
+    dp_gpu = out[0].cpu().numpy().astype(np.float64) - p.flat()
+    assert rel_l2(dp_gpu[vis], (rp - p.flat())[vis]) < 1e-3
+
+
+def test_train_step_visible_only_adam(eng, oracle):
+    """Two training steps with visible-only Adam (gs_train_step, sparse_adam =
+    1) on a scene of two clusters 600 m apart: the first batch of cameras
+    looks at cluster A, the second at cluster B.  After the second step the
+    Gaussians of A (seen in step 1, unseen in step 2) keep step 1's p, m, v bit
+    for bit (dense Adam would decay their moments and move them), and the
+    first moments of B's Gaussians follow the oracle's visible-only step."""
+    a_sc, rng = synth.aerial_scene(20_000, n_clusters=6, seed=13)
+    b_sc, _ = synth.aerial_scene(20_000, n_clusters=6, seed=14)
+    a_sc.mo[:, 0] -= 300.0
+    b_sc.mo[:, 0] += 300.0
+    sc = synth.Scene(np.concatenate([a_sc.mo, b_sc.mo]), np.concatenate([a_sc.ls, b_sc.ls]),
+                     np.concatenate([a_sc.q, b_sc.q]), np.concatenate([a_sc.sh, b_sc.sh], 1))
+    inA = np.arange(sc.N) < a_sc.N
+
+    def batch(cx):
+        cams = []
+        for yaw in (0.3, 2.4):
+            pos = (cx + 40 * np.cos(yaw), 40 * np.sin(yaw), 45.0)
+            cams.append(synth._aim_at(pos, (cx, 0.0, 10.0), 192, 108, 50.0))
+        return cams
+    camsA, camsB = batch(-300.0), batch(300.0)
+    tgA = np.stack([synth.blurred_noise_target(rng, 108, 192) for _ in camsA])
+    tgB = np.stack([synth.blurred_noise_target(rng, 108, 192) for _ in camsB])
+    for cams, other in ((camsA, ~inA), (camsB, inA)):
+        for cam in cams:
+            assert not np.any(oracle.fp32_bounds(sc, cam)["vis_out"][other])   # the far cluster is out of view
+    lr6 = (1.6e-4 * 70, 5e-3, 1e-3, 5e-2, 2.5e-3, 2.5e-4)
+    ctx = eng.Context(lr=lr6, sparse_adam=1)
+    P = eng.DeviceScene.from_host(sc)
+    G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
+    ctx.train_step(P, G, M, V, 1, camsA, torch.from_numpy(tgA).cuda(), check=True)
+    torch.cuda.synchronize()
+    after1 = [t.flat().clone() for t in (P, M, V)]
+    ctx.train_step(P, G, M, V, 2, camsB, torch.from_numpy(tgB).cuda(), check=True)
+    torch.cuda.synchronize()
+    ka = torch.from_numpy(inA).cuda()
+    assert float(after1[1][ka].abs().max()) > 0                 # A has moments to keep
+    for t, a1 in zip((P, M, V), after1):
+        assert torch.equal(t.flat()[ka], a1[ka])
+    # the oracle's two visible-only steps; B is untouched by step 1 on both sides
+    z = np.zeros((sc.N, 60))
+    p1, m1, v1, _, _ = oracle.train_step(sc, camsA, tgA, z, z, 1, lr6, sparse=True)
+    assert np.array_equal(p1[~inA], sc.flat().astype(np.float64)[~inA])
+    sc1 = synth.Scene(p1[:, 0:4].astype(np.float32), p1[:, 4:8].astype(np.float32), p1[:, 8:12].astype(np.float32),
+                      p1[:, 12:60].reshape(sc.N, 12, 4).transpose(1, 0, 2).astype(np.float32).copy())
+    p2, m2, _, _, _ = oracle.train_step(sc1, camsB, tgB, m1, v1, 2, lr6, sparse=True)
+    assert np.all(p2[inA] == sc1.flat().astype(np.float64)[inA]) and np.all(m2[inA] == m1[inA])
+    assert rel_l2(M.flat().cpu().numpy()[~inA], m2[~inA]) < GRAD_TOL
+
+
 # ------------------------------------------------------------------ end to end
 
 def _check_image(ref, gpu_img, label=""):
@@ -579,6 +661,58 @@ def test_c2_full_size_sampled_views(eng, oracle):
         loss, _ = ctx.loss(imgs[b][None].contiguous(), torch.from_numpy(tg[b:b + 1]).cuda())
         L, _, _, _ = oracle.ssim_loss(fw["img"], tg[b])
         assert abs(float(loss[0]) - L) < 1e-4 * abs(L)
+
+
+def test_c2_full_size_batched_gradient(eng, oracle):
+    """A batch of two of the 4M-Gaussian scene's 1080p views through
+    gs_train_step (the batched path: one transformation, one binning and one
+    compositing launch over both views): images on every pixel against the
+    admissible set, the per-view losses, and the batch gradient (the mean of
+    the views' gradients, Sec. 4) group by group against oracle.train_step."""
+    sc, cams, tg = synth.workload_c2()
+    pick = [0, 11]
+    cams2 = [cams[b] for b in pick]
+    tg2 = np.ascontiguousarray(tg[pick])
+    lr6 = (1.6e-4 * 70, 5e-3, 1e-3, 5e-2, 2.5e-3, 2.5e-4)
+    ctx = eng.Context(lr=lr6, px_per_thread=2)
+    P = eng.DeviceScene.from_host(sc)
+    imgs = ctx.render(P, cams2, check=True)
+    G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
+    loss = ctx.train_step(P, G, M, V, 1, cams2, torch.from_numpy(tg2).cuda(), check=True)
+    torch.cuda.synchronize()
+    for b, cam in enumerate(cams2):
+        _check_image(oracle.render_admissible(sc, cam), imgs[b].cpu().numpy(), f"C2 batch view {pick[b]}")
+    _, _, _, ref_losses, ref_grad = oracle.train_step(sc, cams2, tg2, np.zeros((sc.N, 60)), np.zeros((sc.N, 60)),
+                                                      1, lr6)
+    for b in range(2):
+        assert abs(float(loss[b]) - ref_losses[b]) < 1e-4 * abs(ref_losses[b])
+    grad = G.flat().cpu().numpy()
+    groups = dict(mean=slice(0, 3), opacity=slice(3, 4), scale=slice(4, 7), quat=slice(8, 12),
+                  sh_dc=slice(12, 15), sh_rest=slice(15, 60))
+    for name, s_ in groups.items():
+        err = rel_l2(grad[:, s_], ref_grad[:, s_])
+        print(f"C2 batch of 2 {name} rel-L2 {err:.2e}")
+        assert err < GRAD_TOL, name
+
+
+def test_c3_full_size_sampled_window(eng, oracle):
+    """The 40M-Gaussian 4K workload: one 3840x2160 view rendered by gs_render
+    (the forward of the batched training step), a 512x512 tile-aligned window
+    checked on every pixel against the oracle's admissible set (the oracle
+    transforms all 40M Gaussians with the view's camera and composites the
+    window)."""
+    sc, cams, _ = synth.workload_c3()
+    cam = cams[0]
+    ctx = eng.Context(px_per_thread=4, smem_batch=32)
+    P = eng.DeviceScene.from_host(sc)
+    img = ctx.render(P, [cam], check=True)[0].cpu().numpy()
+    del P
+    torch.cuda.empty_cache()
+    w = h = 512
+    x0, y0 = (cam.W - w) // 2 // 16 * 16, (cam.H - h) // 2 // 16 * 16
+    ref = oracle.render_window_admissible(sc, cam, (x0, y0, w, h))
+    assert len(ref["index"]) > 10000
+    _check_image(ref, img[:, y0:y0 + h, x0:x0 + w], "C3 window")
 
 
 # ------------------------------------------------------------------ autotuner

@@ -236,3 +236,53 @@ def test_train_step_gradient_is_mean_over_views(oracle):
         assert L == pytest.approx(losses[b], abs=1e-15)
         per.append(oracle.grad_view(sc, cams[b], dimg)[0])
     assert np.allclose(grad, (per[0] + per[1]) / 2, rtol=1e-12, atol=1e-18)
+
+
+# ---------------------------------------------------------------- visible-only Adam
+
+def test_visible_only_adam_rows(oracle):
+    """Visible-only Adam takes dense Adam's step (pinned above to Eq. 1-2) on
+    the visible rows and leaves p, m and v of the others exactly as they were;
+    with every row visible it is dense Adam."""
+    lr6 = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3, 2.5e-4)
+    rng = np.random.default_rng(3)
+    N = 50
+    p, g = rng.standard_normal((N, 60)), rng.standard_normal((N, 60))
+    m, v = rng.standard_normal((N, 60)) * 0.1, rng.random((N, 60)) * 0.1
+    vis = rng.random(N) < 0.4
+    g[~vis] = 0.0                                  # an unseen Gaussian has no gradient
+    for B, step in ((1, 1), (16, 7)):
+        dp, dm, dv = oracle.adam(p, g, m, v, step, lr6, batch=B)
+        sp, sm, sv = oracle.adam(p, g, m, v, step, lr6, batch=B, visible=vis)
+        assert np.array_equal(sp[vis], dp[vis]) and np.array_equal(sm[vis], dm[vis]) and np.array_equal(sv[vis], dv[vis])
+        assert np.array_equal(sp[~vis], p[~vis]) and np.array_equal(sm[~vis], m[~vis]) and np.array_equal(sv[~vis], v[~vis])
+        # dense Adam moves the unseen rows (stale moments), visible-only does not
+        assert np.abs(dp[~vis] - p[~vis]).max() > 0
+        ap, am, av = oracle.adam(p, g, m, v, step, lr6, batch=B, visible=np.ones(N, bool))
+        assert np.array_equal(ap, dp) and np.array_equal(am, dm) and np.array_equal(av, dv)
+
+
+def test_train_step_visible_only_skips_unseen_gaussians(oracle):
+    """In a training step, visible means some view of the batch gives the
+    Gaussian a tile rectangle; Gaussians behind both cameras keep p, m, v,
+    the others take the dense step."""
+    sc = synth.tiny_scene(40, seed=6, spread=0.5)
+    sc.mo[:8, 2] = -2.0                            # behind both cameras
+    cams = [synth.test_camera(W=32, H=24), synth.camera_look_at((0.2, 0.1, -0.3), (0, 0, 3), (0, -1, 0), 32, 24, 60)]
+    rng = np.random.default_rng(1)
+    tg = rng.random((2, 3, 24, 32))
+    N = sc.N
+    m, v = rng.standard_normal((N, 60)) * 1e-3, rng.random((N, 60)) * 1e-6
+    lr6 = (1e-3,) * 6
+    dp, dm, dv, _, grad = oracle.train_step(sc, cams, tg, m, v, 2, lr6)
+    sp, sm, sv, _, grad2 = oracle.train_step(sc, cams, tg, m, v, 2, lr6, sparse=True)
+    seen = np.zeros(N, bool)
+    for cam in cams:
+        seen |= oracle.project(sc, cam)["radius"] > 0
+    assert not seen[:8].any() and seen[8:].sum() > 10
+    # (the oracle's backward adds with OpenMP atomics: equal up to summation order)
+    assert np.allclose(grad, grad2, rtol=1e-10, atol=1e-18) and np.all(grad[~seen] == 0)
+    p0 = sc.flat().astype(np.float64)
+    assert np.array_equal(sp[~seen], p0[~seen]) and np.array_equal(sm[~seen], m[~seen]) and np.array_equal(sv[~seen], v[~seen])
+    assert np.allclose(sp[seen], dp[seen], rtol=1e-10, atol=1e-15) and np.allclose(sm[seen], dm[seen], rtol=1e-8, atol=1e-18)
+    assert np.abs(dp[~seen] - p0[~seen]).max() > 0
