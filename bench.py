@@ -252,11 +252,13 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------ our arm
 
 # DRAM bytes (read + write) of one k_blend_bwd launch per walked (pixel, list
-# position) pair, from an ncu capture of the blending kernels on C1 (tile 16,
-# 64 entries, 2 pixels per thread; summary under profiles/); the kernel's gathers and
-# atomics grow with the walked pairs, so the traffic of a bench launch is
-# taken as this times its walked count.
-BLEND_BWD_DRAM_BYTES_PER_WALKED = 1.047
+# position) pair, from an ncu capture of the kernel on a C2-shaped case (4M
+# Gaussians in Morton storage order, 2 of the 16 views at 1080p, tile 16, 64
+# entries, 2 pixels per thread; summary under profiles/): 1.757 GB over
+# 836.96M walked pairs.  Per-view records, per-view gradient accumulators and
+# walked pairs all grow with the views, so a launch's traffic is taken as
+# this times its walked count.
+BLEND_BWD_DRAM_BYTES_PER_WALKED = 2.10
 
 
 def stage_traffic(stage, counters):
@@ -312,6 +314,18 @@ def stage_roofline(stage, ms, counters, N, Bv, pixels, passes, peaks, clock_mhz,
     return dict(bound="hbm", achieved=byt / sec / 1e9, peak=hbm, unit="GB/s", work_desc=f"{byt:.3e} bytes")
 
 
+def spatial_order(engine, P):
+    """Stores the Gaussians in Morton order of their positions (gs_spatial_order
+    + gs_permute, once at load, outside every timed region): a tile's list
+    entries then gather nearby records instead of random ones."""
+    import torch
+    c = engine.Context()
+    Q = c.permute(P, c.spatial_order(P))
+    torch.cuda.synchronize()
+    c.close()
+    return Q
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2406_18533_gb300 import binding, engine
@@ -326,6 +340,8 @@ def run_ours(args, rank, world, local_rank):
     Bv = len(cams)
     H, W = cams[0].H, cams[0].W
     P = engine.DeviceScene.from_host(sc)
+    if args.storage_order == "morton":
+        P = spatial_order(engine, P)
     targets = torch.from_numpy(tg).cuda()
     tuned = None
     if args.autotune:
@@ -335,7 +351,7 @@ def run_ours(args, rank, world, local_rank):
         tuned = {"chosen": best, "trials_ms": {f"t{t.tile}_b{t.smem_batch}_p{t.px_per_thread}": round(t.ms, 3)
                                                for t in trials}}
     ctx = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt,
-                         sparse_adam=int(args.sparse_adam))
+                         sparse_adam=int(args.sparse_adam), schedule=int(args.schedule == "alg1"))
     G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
     loss = torch.empty(Bv, dtype=torch.float32, device="cuda")
     cam_arr = binding.camera_array(cams)
@@ -423,7 +439,7 @@ def run_ours(args, rank, world, local_rank):
     per_view = None
     if Bv > 1 and not args.no_per_view:
         ctx1 = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt,
-                              sparse_adam=int(args.sparse_adam))
+                              sparse_adam=int(args.sparse_adam), schedule=int(args.schedule == "alg1"))
         P1 = P.clone()
         G1, M1, V1 = P1.zeros_like(), P1.zeros_like(), P1.zeros_like()
         loss1 = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -505,8 +521,9 @@ def run_ours(args, rank, world, local_rank):
                 "unit": rf["unit"], "frac": rf["achieved"] / rf["peak"],
                 "frac_survey_unit": rf["survey"] / rf["peak"] if "survey" in rf else None,
                 "traffic": stage_traffic(dom, counters),
-                "traffic_unit": "bytes per launch (ncu dram bytes per walked pair, scaled by this "
-                                "launch's walked pairs)" if dom == "blend_bwd" else None,
+                "traffic_unit": "bytes per launch (ncu dram bytes per walked pair on a 2-view C2-shaped launch "
+                                "in Morton storage order, scaled by this launch's walked pairs)"
+                                if dom == "blend_bwd" else None,
                 "peak_source": (f"{peak_kind} HBM copy; FP32 derived: {n_sm} SMs (device) x "
                                 f"{FP32_LANES_PER_SM} lanes x 2 flop x {float(peaks.get('sm_max_mhz', 2070.0)):.0f} MHz"),
                 "sm_count": n_sm, "work": rf["work_desc"],
@@ -555,6 +572,10 @@ def run_ours(args, rank, world, local_rank):
                    "tile": args.tile, "smem_batch": args.batch, "px_per_thread": args.ppt, "autotune": tuned,
                    "sh_degree": 3,
                    "adam": "visible-only" if args.sparse_adam else "dense (every Gaussian, the paper's)",
+                   "schedule": ("Algorithm 1 ranges over the previous step's measured tile costs, persistent CTAs"
+                                if args.schedule == "alg1" else "one CTA per tile (longest lists first where it pays)"),
+                   "storage_order": ("Morton order of the positions (gs_spatial_order + gs_permute once at load)"
+                                     if args.storage_order == "morton" else "as generated"),
                    "l2": "no flush: params + grad + Adam moments resident in HBM exceed the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "mpix_per_s": value * H * W / 1e6, "cuda_graph": bool(args.graph),
@@ -616,6 +637,8 @@ def serve_trace(args, local_rank, n_requests):
     torch.cuda.set_device(local_rank)
     sc, rng = synth.large_scene(10_000_000, seed=0)
     scene = engine.DeviceScene.from_host(sc)
+    if args.storage_order == "morton":
+        scene = spatial_order(engine, scene)
     reqs = [serve.Request(i, t, cam) for i, (t, cam) in enumerate(synth.serve_requests(rng, n_requests))]
     server = serve.RenderServer(scene, n_slots=3, max_batch=8, tile=args.tile, smem_batch=args.batch,
                                 px_per_thread=args.ppt)
@@ -678,6 +701,10 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="call gs_train_step directly instead of replaying one captured step (CUDA graph)")
     ap.add_argument("--views", type=int, default=0, help="use only the first K views of the workload (profiling)")
+    ap.add_argument("--storage-order", default="morton", choices=["morton", "given"],
+                    help="store the Gaussians in Morton order of their positions at load (default) or as generated")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "alg1"],
+                    help="blending schedule: one CTA per tile (auto) or Algorithm 1 ranges of measured cost")
     ap.add_argument("--sparse-adam", action="store_true",
                     help="visible-only Adam (Gaussians no view of the batch sees keep p, m, v)")
     args = ap.parse_args()

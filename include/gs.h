@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 2
+#define GS_ABI_VERSION 3
 #define GS_MAX_VIEWS 32   /* views per call (training batch or render batch) */
 #define GS_MAX_FRAGMENTS 1073741823ull  /* 2^30 - 1: largest fragment capacity of one call */
 
@@ -102,6 +102,11 @@ typedef struct gs_hparams {
     int32_t sparse_adam;      /* 0: Adam over every Gaussian (the paper's optimizer, default);
                                  1: gs_train_step updates only the Gaussians some view of the
                                  batch sees (visible-only Adam, see gs_adam_step_sparse) */
+    int32_t schedule;         /* blending schedule of gs_train_step: 0 (default) one CTA per tile,
+                                 longest lists first where that pays; 1 Algorithm 1: the tiles are
+                                 split into contiguous ranges of equal cost, measured per tile in
+                                 the previous step (list lengths before the first), one range per
+                                 resident persistent CTA (see gs_division_points) */
 } gs_hparams;
 
 /*
@@ -350,6 +355,95 @@ gs_status gs_adam_step_sparse(gs_ctx *ctx, gs_scene *p, const gs_scene *g, gs_sc
 gs_status gs_train_step(gs_ctx *ctx, gs_scene *p, gs_scene *g, gs_scene *m, gs_scene *v, int64_t step,
                         const gs_camera *cams, int32_t B, const float *targets, float *loss_out,
                         void *stream);
+
+/*
+ * Densification (App. A.1: Gaussians whose projected position keeps moving
+ * across training steps are cloned or split, by whether their scale exceeds a
+ * threshold; Gaussians of low opacity are pruned; opacity is reset now and
+ * then).  The paper states the rule in words and defers its details to 3DGS;
+ * the readings below fix them.
+ *
+ * gs_set_densify_stats: when grad_acc / grad_cnt (caller-owned device arrays
+ * of N float / uint32) are set, every gs_train_step adds, for each view of its
+ * batch in which a Gaussian is visible (radius > 0), the length of that
+ * view's position gradient |dL_v/d(u, v)| (pixels; the view's own loss, before
+ * the batch mean) to grad_acc and 1 to grad_cnt (a step that overflows its
+ * fragment buffer or whose sort gives up adds nothing).  NULL pointers stop
+ * it.  Steps on a scene of another N add nothing.  The arrays must hold the
+ * scene's N; the caller zeroes them after densifying.
+ *
+ * gs_densify: one densification of N Gaussians (p, m, v) into p_out, m_out,
+ * v_out (caller-owned, capacity Gaussians each; their N field must equal
+ * capacity).  Per Gaussian g, with mean gradient decided in float32 as
+ * grad_acc[g] >= grad_threshold * (float)grad_cnt[g] (and grad_cnt[g] > 0):
+ *   - prune when its opacity logit < logit(min_opacity) (float32 compare);
+ *   - else clone when the gradient test passes and its largest log-scale
+ *     <= log(scale_threshold): the Gaussian and an exact copy (the copy's
+ *     Adam moments zero);
+ *   - else split when the gradient test passes: two children replace it,
+ *     child k at mean + Rq diag(s) xi_k (xi_k = normals[6g + 3k .. +2],
+ *     caller-drawn standard normals), log-scale = log-scale - ln(split_div),
+ *     same rotation, opacity and SH, moments zero;
+ *   - else keep it with its moments.
+ * Outputs keep the input order, each Gaussian's results together (the
+ * original or first child, then the copy or second child).  The new count
+ * goes to *n_out (the call synchronises the stream); if it exceeds capacity
+ * nothing is written and the call returns GS_ERR_CAPACITY with *n_out set.
+ * normals: device float[6 N].
+ *
+ * gs_reset_opacity: every opacity becomes min(opacity, max_opacity) (on the
+ * logit), and the opacity lane of both Adam moments is zeroed.
+ */
+typedef struct gs_densify_params {
+    float grad_threshold;   /* mean |dL/d(u, v)| per visible view, pixels (3DGS-like: 0.2 px order) */
+    float scale_threshold;  /* world units: clone at or below, split above */
+    float min_opacity;      /* prune below (0.005) */
+    float split_div;        /* child scale = parent scale / split_div (1.6) */
+} gs_densify_params;
+
+gs_status gs_set_densify_stats(gs_ctx *ctx, float *grad_acc, uint32_t *grad_cnt, int64_t N);
+gs_status gs_densify(gs_ctx *ctx, const gs_scene *p, const gs_scene *m, const gs_scene *v, const float *grad_acc,
+                     const uint32_t *grad_cnt, const float *normals, const gs_densify_params *dp, gs_scene *p_out,
+                     gs_scene *m_out, gs_scene *v_out, int64_t capacity, int64_t *n_out, void *stream);
+gs_status gs_reset_opacity(gs_ctx *ctx, gs_scene *p, gs_scene *m, gs_scene *v, float max_opacity, void *stream);
+
+/*
+ * Algorithm 1 ("Calculation of Division Points", Sec. 3.3): the paper splits
+ * an image's sequence of pixel blocks among G GPUs by the blocks' runtimes
+ * measured in the previous iteration: CT = cumsum(ET), ET_gpu = CT[B-1] / G,
+ * DP = searchsorted(CT, arange(0, G) * ET_gpu).  Here the blocks are the
+ * batch's tiles and the GPUs are persistent CTAs (hp.schedule = 1).
+ * gs_division_points computes DP for T costs (device uint32, caller-owned,
+ * read only) and P ranges: div[k] (device uint32[P]) is the first tile of
+ * range k, i.e. the first i with CT[i] >= k CT[T-1] / P, compared exactly as
+ * P CT[i] >= k CT[T-1] in 64-bit integers; range k is [div[k], div[k+1]) and
+ * the last ends at T.  Each cost is first capped at (2^32 - 1) / T (so the
+ * 32-bit prefix sums cannot wrap).  T >= 1, 1 <= P <= 2^20.
+ */
+gs_status gs_division_points(gs_ctx *ctx, const uint32_t *cost, int64_t T, int32_t P, uint32_t *div,
+                             void *stream);
+
+/*
+ * Storage order of the Gaussians (a data-layout step, no paper counterpart as
+ * an algorithm: the paper's Gaussian-wise distribution decides which GPU
+ * holds a Gaussian, Sec. 3.1 and App. B.2; this decides where in one GPU's
+ * memory it lives).  Every (view, Gaussian) record the compositing kernels
+ * gather is indexed by Gaussian, so Gaussians that meet the same screen
+ * tiles should sit next to each other in memory.  gs_spatial_order writes
+ * perm[N]: the Gaussian indices sorted stably by the Morton (Z-order) code of
+ * their positions, each axis quantised to 10 bits over the bounding box of
+ * the finite positions as floor((x - lo) * (1024 / (hi - lo))) with each
+ * float32 operation rounded separately, clamped to 1023 (a non-finite
+ * position, or a flat axis, gives cell 0).  gs_permute then writes
+ * dst[i] = src[perm[i]] for all 60 floats (out of place: no plane of dst may
+ * be a plane of src); apply it to the parameters and, in training, to the
+ * Adam moments.  Renders do not depend on the order (ties of equal depth go
+ * to the lower index).  Both calls are asynchronous; perm is caller-owned
+ * device memory of N uint32 (N < 2^31).  gs_spatial_order grows the
+ * context's scratch (12 bytes per Gaussian plus the sort's).
+ */
+gs_status gs_spatial_order(gs_ctx *ctx, const gs_scene *scene, uint32_t *perm, void *stream);
+gs_status gs_permute(gs_ctx *ctx, const gs_scene *src, const uint32_t *perm, gs_scene *dst, void *stream);
 
 /*
  * Forward-only render of B novel views of possibly different sizes (serving):

@@ -377,6 +377,152 @@ def grad_view(scene, cam, dimg, tile=16, **kw):
 
 
 # ----------------------------------------------------------------------------
+# Algorithm 1: division points of a sequence of blocks by their costs
+# ----------------------------------------------------------------------------
+
+def division_points(cost, P):
+    """Algorithm 1 ("Calculation of Division Points") for integer block costs
+    and P parts: CT = cumsum(cost), ET = CT[-1] / P, thresholds arange(0, P)
+    * ET, DP = searchsorted(CT, thresholds) (first index reaching each
+    threshold), with the comparison CT[i] >= k CT[-1] / P taken exactly as
+    P CT[i] >= k CT[-1].  Part k covers [DP[k], DP[k + 1]), the last ends at
+    len(cost)."""
+    CT = np.cumsum(np.asarray(cost, np.int64))
+    thr = np.arange(P, dtype=np.int64) * CT[-1]
+    return np.searchsorted(CT * P, thr, side="left").astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
+# Densification (App. A.1): clone / split by the mean position-gradient length
+# and the scale, prune by opacity, opacity reset
+# ----------------------------------------------------------------------------
+
+def _f32_log(x):
+    """log of a float32 value, in double, rounded once to float32."""
+    return np.float32(math.log(float(np.float32(x))))
+
+
+def densify_thresholds(grad_threshold, scale_threshold, min_opacity, split_div):
+    """The float32 thresholds the decisions compare against: (grad, log scale,
+    opacity logit, log split divisor)."""
+    mo = float(np.float32(min_opacity))
+    return (np.float32(grad_threshold), _f32_log(scale_threshold), np.float32(math.log(mo / (1.0 - mo))),
+            _f32_log(split_div))
+
+
+def densify_actions(p, acc, cnt, grad_threshold, scale_threshold, min_opacity=0.005, split_div=1.6):
+    """Action per Gaussian of the flat parameters p [N, 60] (float32 values):
+    0 prune (opacity logit below logit(min_opacity)), 1 keep, 2 clone (the
+    mean gradient test acc >= thr * cnt passes, float32, and the largest
+    log-scale <= log(scale_threshold)), 3 split (the test passes, larger)."""
+    g, lst, lmin, _ = densify_thresholds(grad_threshold, scale_threshold, min_opacity, split_div)
+    p = np.asarray(p, np.float32)
+    acc = np.asarray(acc, np.float32)
+    cnt = np.asarray(cnt, np.int64)
+    prune = ~(p[:, 3] >= lmin)
+    grow = (cnt > 0) & (acc >= (g * cnt.astype(np.float32)).astype(np.float32))
+    smax = np.fmax(p[:, 4], np.fmax(p[:, 5], p[:, 6]))
+    act = np.where(grow, np.where(smax <= lst, 2, 3), 1)
+    return np.where(prune, 0, act)
+
+
+def densify(p, m, v, acc, cnt, normals, grad_threshold, scale_threshold, min_opacity=0.005, split_div=1.6):
+    """One densification of flat [N, 60] parameters and moments.  Outputs keep
+    the input order, each Gaussian's rows together: keep -> the row with its
+    moments; clone -> the row with its moments, then a copy with zero moments;
+    split -> two children at mean + R(q) diag(exp(log s)) xi_k (xi =
+    normals[g, k], FP64), log-scale - log(split_div) (float32), the rest
+    copied, zero moments; prune -> nothing.  Returns (p, m, v, src, kind):
+    src the source index of each output row, kind its action (1, 2, 3, and
+    4 for a clone's copy)."""
+    p = np.asarray(p, np.float32)
+    m = np.asarray(m, np.float32)
+    v = np.asarray(v, np.float32)
+    normals = np.asarray(normals, np.float64).reshape(-1, 2, 3)
+    act = densify_actions(p, acc, cnt, grad_threshold, scale_threshold, min_opacity, split_div)
+    _, _, _, ldiv = densify_thresholds(grad_threshold, scale_threshold, min_opacity, split_div)
+    rows_p, rows_m, rows_v, src, kind = [], [], [], [], []
+    zero = np.zeros(60)
+    R = np.zeros((len(p), 9))
+    lib().or_quat_rot(_i64(len(p)), _p(np.ascontiguousarray(p[:, 8:12], np.float64)), _p(R))
+    for g in range(len(p)):
+        a = int(act[g])
+        if a == 0:
+            continue
+        if a in (1, 2):
+            rows_p.append(p[g].astype(np.float64)); rows_m.append(m[g].astype(np.float64))
+            rows_v.append(v[g].astype(np.float64)); src.append(g); kind.append(a)
+            if a == 2:
+                rows_p.append(p[g].astype(np.float64)); rows_m.append(zero); rows_v.append(zero)
+                src.append(g); kind.append(4)
+            continue
+        s = np.exp(p[g, 4:7].astype(np.float64))
+        for k in range(2):
+            child = p[g].astype(np.float64).copy()
+            child[0:3] = p[g, 0:3].astype(np.float64) + R[g].reshape(3, 3) @ (s * normals[g, k])
+            child[4:7] = (p[g, 4:7] - ldiv).astype(np.float32)
+            child[7] = 0.0
+            rows_p.append(child); rows_m.append(zero); rows_v.append(zero); src.append(g); kind.append(3)
+    shape = (len(rows_p), 60)
+    mk = lambda rows: np.array(rows).reshape(shape) if rows else np.zeros((0, 60))
+    return mk(rows_p), mk(rows_m), mk(rows_v), np.array(src, np.int64), np.array(kind, np.int64)
+
+
+def reset_opacity(p, m, v, max_opacity=0.01):
+    """Opacity reset: logit = min(logit, logit(max_opacity)) (float32), and
+    the opacity lane of both moments set to 0.  Returns new arrays."""
+    mx = float(np.float32(max_opacity))
+    lmax = np.float32(math.log(mx / (1.0 - mx)))
+    p, m, v = (np.array(a, np.float32) for a in (p, m, v))
+    p[:, 3] = np.minimum(p[:, 3], lmax)
+    m[:, 3] = 0.0
+    v[:, 3] = 0.0
+    return p, m, v
+
+
+# ----------------------------------------------------------------------------
+# Storage order of the Gaussians (Morton code of the position)
+# ----------------------------------------------------------------------------
+
+def morton_cells(xyz):
+    """10-bit cell per axis of float32 positions [N, 3]: floor((x - lo) *
+    (1024 / (hi - lo))) with each float32 operation rounded separately
+    (numpy float32 arithmetic), clamped to [0, 1023]; lo / hi over the rows
+    whose three coordinates are finite; a non-finite row or a flat axis gives 0."""
+    x = np.asarray(xyz, np.float32)
+    ok = np.all(np.isfinite(x), axis=1)
+    cells = np.zeros(x.shape, np.int64)
+    if not ok.any():
+        return cells
+    lo, hi = x[ok].min(0), x[ok].max(0)
+    for a in range(3):
+        if not hi[a] > lo[a]:
+            continue
+        scale = np.float32(1024.0) / np.float32(hi[a] - lo[a])
+        with np.errstate(invalid="ignore"):
+            q = np.floor((x[:, a] - lo[a]).astype(np.float32) * scale)
+        q = np.where(ok, q, 0)
+        cells[:, a] = np.clip(q, 0, 1023).astype(np.int64)
+    return cells
+
+
+def morton_code(cells):
+    """Interleave three 10-bit cells into a 30-bit code: bit b of x to bit 3b,
+    of y to 3b + 1, of z to 3b + 2."""
+    c = np.asarray(cells, np.int64)
+    code = np.zeros(c.shape[0], np.int64)
+    for b in range(10):
+        for a in range(3):
+            code |= ((c[:, a] >> b) & 1) << (3 * b + a)
+    return code
+
+
+def morton_order(scene):
+    """The storage permutation: Gaussian indices sorted stably by Morton code."""
+    return np.argsort(morton_code(morton_cells(scene.mo[:, :3])), kind="stable").astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
 # Sec. 2.1 step 3: L1 + SSIM loss
 # ----------------------------------------------------------------------------
 
@@ -472,12 +618,14 @@ def adam(p, g, m, v, step, lr6, beta1=0.9, beta2=0.999, eps=1e-15, batch=1,
     return p, m, v
 
 
-def train_step(scene, cams, targets, m, v, step, lr6, tile=16, sparse=False, **adam_kw):
+def train_step(scene, cams, targets, m, v, step, lr6, tile=16, sparse=False, stats=None, **adam_kw):
     """One batched training step: per view render + loss + backward, mean of
     the per-view parameter gradients over the batch, Adam.  sparse=True:
     visible-only Adam, a Gaussian being visible when some view of the batch
-    gives it a tile rectangle (radius > 0).  Returns (new_flat_params
-    [N,60], m, v, losses[B], grad [N,60])."""
+    gives it a tile rectangle (radius > 0).  stats (a dict with arrays "acc"
+    [N] and "cnt" [N]): densification statistics, |dL_v/d(u, v)| of each view
+    in which the Gaussian is visible added to acc, 1 to cnt.  Returns
+    (new_flat_params [N,60], m, v, losses[B], grad [N,60])."""
     B = len(cams)
     N = scene.N
     grad = np.zeros((N, 60))
@@ -491,6 +639,10 @@ def train_step(scene, cams, targets, m, v, step, lr6, tile=16, sparse=False, **a
         pr = fw["proj"]
         g2d = render_bwd(cam.W, cam.H, tile, fw["toff"], fw["gidx"], pr["xy"], pr["conic_o"], pr["rgb"], dimg)
         grad += preprocess_bwd(scene, cam, g2d, tile)
+        if stats is not None:
+            seen = pr["vis"] > 0
+            stats["acc"][seen] += np.hypot(g2d[seen, 0], g2d[seen, 1])
+            stats["cnt"][seen] += 1
     grad /= B
     p = scene.flat().astype(np.float64)
     p2, m2, v2 = adam(p, grad, m, v, step, lr6, batch=B, visible=visible if sparse else None, **adam_kw)

@@ -32,7 +32,8 @@ class gs_hparams(ctypes.Structure):
                 ("bg", ctypes.c_float * 3), ("lr", ctypes.c_float * 6), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("scale_lr_sqrt_b", ctypes.c_int32),
                 ("scale_beta_pow_b", ctypes.c_int32), ("lambda_dssim", ctypes.c_float),
-                ("px_per_thread", ctypes.c_int32), ("sparse_adam", ctypes.c_int32)]
+                ("px_per_thread", ctypes.c_int32), ("sparse_adam", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
 
 
 class gs_proj(ctypes.Structure):
@@ -48,6 +49,11 @@ class gs_proj_grad(ctypes.Structure):
 class gs_bins(ctypes.Structure):
     _fields_ = [("keys", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
                 ("count", ctypes.c_void_p), ("capacity", ctypes.c_uint64)]
+
+
+class gs_densify_params(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("scale_threshold", ctypes.c_float),
+                ("min_opacity", ctypes.c_float), ("split_div", ctypes.c_float)]
 
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NONFINITE, GS_ERR_OOM = range(7)
@@ -78,6 +84,13 @@ SIGNATURES = {
     "gs_render_bwd": [_vp, P(gs_proj), P(gs_bins), P(gs_camera), _i32, _vp, _vp, _vp, P(gs_proj_grad), _vp],
     "gs_preprocess_bwd": [_vp, P(gs_scene), P(gs_camera), _i32, P(gs_proj), P(gs_proj_grad), P(gs_scene), _vp],
     "gs_loss": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
+    "gs_spatial_order": [_vp, P(gs_scene), _vp, _vp],
+    "gs_division_points": [_vp, _vp, _i64, _i32, _vp, _vp],
+    "gs_set_densify_stats": [_vp, _vp, _vp, _i64],
+    "gs_densify": [_vp, P(gs_scene), P(gs_scene), P(gs_scene), _vp, _vp, _vp, P(gs_densify_params), P(gs_scene),
+                   P(gs_scene), P(gs_scene), _i64, P(_i64), _vp],
+    "gs_reset_opacity": [_vp, P(gs_scene), P(gs_scene), P(gs_scene), ctypes.c_float, _vp],
+    "gs_permute": [_vp, P(gs_scene), _vp, P(gs_scene), _vp],
     "gs_adam_step_sparse": [_vp, P(gs_scene), P(gs_scene), P(gs_scene), P(gs_scene), _vp, _i64, _i32, _vp],
     "gs_adam_step": [_vp, P(gs_scene), P(gs_scene), P(gs_scene), P(gs_scene), _i64, _i32, _vp],
     "gs_train_step": [_vp, P(gs_scene), P(gs_scene), P(gs_scene), P(gs_scene), _i64, P(gs_camera), _i32, _vp, _vp,

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgs.so")
-SOURCES = ["gs_api.cu", "preprocess.cu", "bin.cu", "bin_noalloc.cu", "render.cu", "loss.cu", "adam.cu"]
+SOURCES = ["gs_api.cu", "preprocess.cu", "bin.cu", "bin_noalloc.cu", "render.cu", "loss.cu", "adam.cu",
+           "densify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -778,6 +778,103 @@ __global__ void __launch_bounds__(256) k_compose_keys(ViewBatch vb, int64_t N, c
     }
 }
 
+// ---------------------------------------------------------------- storage order (Morton code)
+
+// Order-preserving unsigned image of a float (for atomicMin / atomicMax).
+__device__ __forceinline__ uint32_t float_order_bits(float f)
+{
+    const uint32_t b = __float_as_uint(f + 0.f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float float_from_order_bits(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Bounding box of the finite positions: bb[0..2] = min x, y, z, bb[3..5] = max
+// (order bits; bb starts at {~0 x3, 0 x3}).
+// bb[0..5] = empty box, bb[6] = the key count for the sort.
+__global__ void k_bbox_init(uint32_t *bb, uint32_t n)
+{
+    if (threadIdx.x < 6) bb[threadIdx.x] = threadIdx.x < 3 ? 0xffffffffu : 0u;
+    if (threadIdx.x == 6) bb[6] = n;
+}
+
+__global__ void __launch_bounds__(256) k_bbox(const float4 *mo, int64_t N, uint32_t *bb)
+{
+    __shared__ uint32_t s[6];
+    if (threadIdx.x < 6) s[threadIdx.x] = threadIdx.x < 3 ? 0xffffffffu : 0u;
+    __syncthreads();
+    uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 m = mo[i];
+        if (!(isfinite(m.x) && isfinite(m.y) && isfinite(m.z))) continue;
+        const uint32_t k[3] = {float_order_bits(m.x), float_order_bits(m.y), float_order_bits(m.z)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = min(lo[a], k[a]);
+            hi[a] = max(hi[a], k[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        atomicMin(&s[a], lo[a]);
+        atomicMax(&s[3 + a], hi[a]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) atomicMin(&bb[threadIdx.x], s[threadIdx.x]);
+    else if (threadIdx.x < 6) atomicMax(&bb[threadIdx.x], s[threadIdx.x]);
+}
+
+// 10-bit cell of coordinate x in [lo, hi]: floor((x - lo) * (1024 / (hi - lo)))
+// with each float operation explicitly rounded, clamped to 1023 (a flat axis
+// or a non-finite x gives 0).
+__device__ __forceinline__ uint32_t morton_cell(float x, float lo, float hi)
+{
+    if (!(hi > lo) || !isfinite(x)) return 0u;
+    const float scale = __fdiv_rn(1024.f, __fsub_rn(hi, lo));
+    const float q = floorf(__fmul_rn(__fsub_rn(x, lo), scale));
+    return q >= 1023.f ? 1023u : (q <= 0.f ? 0u : (uint32_t)q);
+}
+
+// Bits of v spread to every third position (bit b -> bit 3b).
+__device__ __forceinline__ uint32_t spread3(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_morton(const float4 *mo, int64_t N, const uint32_t *bb, uint32_t *keys,
+                                                uint32_t *vals)
+{
+    const float lx = float_from_order_bits(bb[0]), ly = float_from_order_bits(bb[1]), lz = float_from_order_bits(bb[2]);
+    const float hx = float_from_order_bits(bb[3]), hy = float_from_order_bits(bb[4]), hz = float_from_order_bits(bb[5]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 m = mo[i];
+        const bool ok = isfinite(m.x) && isfinite(m.y) && isfinite(m.z);
+        const uint32_t cx = ok ? morton_cell(m.x, lx, hx) : 0u, cy = ok ? morton_cell(m.y, ly, hy) : 0u,
+                       cz = ok ? morton_cell(m.z, lz, hz) : 0u;
+        keys[i] = spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+        vals[i] = (uint32_t)i;
+    }
+}
+
+// dst plane k, entry i = src plane k, entry perm[i] (15 float4 planes).
+__global__ void __launch_bounds__(256) k_permute(SceneView src, const uint32_t *perm, SceneMut dst)
+{
+    const int pl = blockIdx.y;
+    const float4 *sp = pl == 0 ? src.mo : pl == 1 ? src.ls : pl == 2 ? src.q : src.sh + (int64_t)(pl - 3) * src.N;
+    float4 *dp = pl == 0 ? dst.mo : pl == 1 ? dst.ls : pl == 2 ? dst.q : dst.sh + (int64_t)(pl - 3) * dst.N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < src.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = perm[i];
+        dp[i] = (int64_t)j < src.N ? sp[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 }  // namespace
 
 void set_lookback_debug(uint32_t spin_limit, int withhold_first)
@@ -966,5 +1063,38 @@ void launch_compose_keys(const ViewBatch &vb, int64_t N, const uint32_t *tiles, 
     k_compose_keys<<<stride_blocks(capacity), 256, 0, st>>>(vb, N, tiles, vals, count, rgb_d, keys);
     count_launches(1);
 }
+
+size_t spatial_order_temp_bytes(int64_t N)
+{
+    const uint64_t n = (uint64_t)(N > 0 ? N : 1);
+    return 3 * 4 * n + 256 + sort_temp_bytes(n, 0);
+}
+
+void launch_spatial_order(const float4 *mo, int64_t N, uint32_t *perm, void *temp, DevStatus *status,
+                          cudaStream_t st)
+{
+    if (N <= 0) return;
+    const uint64_t n = (uint64_t)N;
+    char *t = reinterpret_cast<char *>(temp);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(t);
+    uint32_t *keys_alt = keys + n, *vals_alt = keys + 2 * n;
+    uint32_t *bb = reinterpret_cast<uint32_t *>(t + 12 * n);
+    void *sort_tmp = t + 12 * n + 256;
+    k_bbox_init<<<1, 32, 0, st>>>(bb, (uint32_t)n);
+    k_bbox<<<stride_blocks(n), 256, 0, st>>>(mo, N, bb);
+    k_morton<<<stride_blocks(n), 256, 0, st>>>(mo, N, bb, keys, perm);
+    count_launches(3);
+    // 30-bit codes: four stable passes of 8-bit digits, so the result is back in keys / perm
+    radix_sort<8>(keys, perm, keys_alt, vals_alt, n, bb + 6, 4, sort_tmp, status, st);
+}
+
+void launch_permute(const SceneView &src, const uint32_t *perm, const SceneMut &dst, cudaStream_t st)
+{
+    if (src.N <= 0) return;
+    const unsigned bx = stride_blocks((uint64_t)src.N);
+    k_permute<<<dim3(bx, 15), 256, 0, st>>>(src, perm, dst);
+    count_launches(1);
+}
+
 
 }  // namespace gs

@@ -47,6 +47,14 @@ struct gs_ctx {
     DBuf img, dimg, T_final, n_contrib, maps, acc;
     DBuf tile_order;               // blending launch order (tiles) + 64 words of counters
     DBuf vis;                      // visible-only Adam: one byte per Gaussian
+    DBuf order_tmp;                // gs_spatial_order: Morton keys, sort buffers
+    DBuf dens_cnt, dens_off;       // gs_densify: output counts and their offsets
+    DBuf tile_cost, tile_excl;     // Algorithm 1 schedule: measured cost per tile, its prefix sums
+    DBuf div_f, div_b, div_tot;    // division points of the forward / backward ranges, a total
+    uint32_t cost_tiles = 0;       // tiles the cost buffer describes (0: nothing measured yet)
+    float *dacc = nullptr;         // densification statistics (caller-owned), see gs_set_densify_stats
+    uint32_t *dcnt = nullptr;
+    int64_t dN = 0;
     uint64_t frag_cap = 0;
     // tracing: events around the stages of gs_train_step
     int trace_max = 0, trace_step = 0;
@@ -312,6 +320,18 @@ gs_status ensure_iter(gs_ctx *c, int64_t N, const ViewBatch &vb, uint64_t cap)
         (r = ensure(c, c->tile_order, 4 * ((size_t)vb.total_tiles + 64))))
         return r;
     if ((r = ensure(c, c->T_final, 4 * pix)) || (r = ensure(c, c->n_contrib, 4 * pix))) return r;
+    if (c->hp.schedule == 1) {
+        const size_t T = (size_t)vb.total_tiles + 1;
+        const size_t P = (size_t)blend_resident_ctas(c->hp.tile, c->hp.smem_batch, c->hp.px_per_thread, true) +
+                         blend_resident_ctas(c->hp.tile, c->hp.smem_batch, c->hp.px_per_thread, false) + 1;
+        const void *had = c->tile_cost.p;
+        if ((r = ensure(c, c->tile_cost, 4 * T)) != GS_OK) return r;
+        if (c->tile_cost.p != had) c->cost_tiles = 0;   // a new buffer holds no measurements
+        if ((r = ensure(c, c->tile_excl, 4 * T)) ||
+            (r = ensure(c, c->div_f, 4 * P)) || (r = ensure(c, c->div_b, 4 * P)) || (r = ensure(c, c->div_tot, 64)) ||
+            (r = ensure(c, c->scan_tmp, scan_temp_bytes((int64_t)T))))
+            return r;
+    }
     return GS_OK;
 }
 
@@ -385,6 +405,7 @@ gs_status check_hparams(gs_ctx *c, const gs_hparams *hp)
     if (hp->px_per_thread != 1 && hp->px_per_thread != 2 && hp->px_per_thread != 4)
         return fail(c, GS_ERR_INVALID_ARG, "px_per_thread must be 1, 2 or 4");
     if (hp->sparse_adam != 0 && hp->sparse_adam != 1) return fail(c, GS_ERR_INVALID_ARG, "sparse_adam must be 0 or 1");
+    if (hp->schedule != 0 && hp->schedule != 1) return fail(c, GS_ERR_INVALID_ARG, "schedule must be 0 or 1");
     if (!blend_config_ok(hp->tile, hp->smem_batch, hp->px_per_thread))
         return fail(c, GS_ERR_INVALID_ARG,
                     "unsupported (tile, smem_batch, px_per_thread): smem_batch 32, 64 or 128 (32 or 64 with tile 32 "
@@ -511,7 +532,8 @@ gs_status gs_destroy(gs_ctx *c)
                     &c->pk, &c->pv, &c->pk_alt, &c->pv_alt, &c->rect, &c->kmask, &c->rmask,
                     &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_proj, &c->keys,
                     &c->vals, &c->ranges, &c->count, &c->img, &c->dimg, &c->T_final, &c->n_contrib, &c->maps,
-                    &c->acc, &c->tile_order, &c->vis};
+                    &c->acc, &c->tile_order, &c->vis, &c->order_tmp, &c->dens_cnt, &c->dens_off,
+                    &c->tile_cost, &c->tile_excl, &c->div_f, &c->div_b, &c->div_tot};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     trace_free(c);
@@ -720,7 +742,7 @@ gs_status gs_loss(gs_ctx *c, const float *img, const float *target, int32_t B, i
     gs_status r;
     if ((r = ensure(c, c->maps, 36 * pix)) || (r = ensure(c, c->acc, 16 * (size_t)B + 64))) return r;
     launch_loss(img, target, B, W, H, c->hp.lambda_dssim, loss_out, d_img, ptr<float>(c->maps), ptr<double>(c->acc),
-                S(stream));
+                c->status, S(stream));
     return cuda_check(c, "gs_loss");
 }
 
@@ -749,6 +771,110 @@ gs_status gs_adam_step_sparse(gs_ctx *c, gs_scene *p, const gs_scene *g, gs_scen
     a.vis = visible;
     launch_adam(mut_of(p), view_of(g), mut_of(m), mut_of(v), a, c->status, S(stream));
     return cuda_check(c, "gs_adam_step_sparse");
+}
+
+gs_status gs_set_densify_stats(gs_ctx *c, float *grad_acc, uint32_t *grad_cnt, int64_t N)
+{
+    if (!c || N < 0 || (!grad_acc) != (!grad_cnt)) return GS_ERR_INVALID_ARG;
+    c->dacc = grad_acc;
+    c->dcnt = grad_cnt;
+    c->dN = grad_acc ? N : 0;
+    return GS_OK;
+}
+
+gs_status gs_densify(gs_ctx *c, const gs_scene *p, const gs_scene *m, const gs_scene *v, const float *grad_acc,
+                     const uint32_t *grad_cnt, const float *normals, const gs_densify_params *dp, gs_scene *p_out,
+                     gs_scene *m_out, gs_scene *v_out, int64_t capacity, int64_t *n_out, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(p) || !scene_ok(m) || !scene_ok(v) || m->N != p->N || v->N != p->N)
+        return fail(c, GS_ERR_INVALID_ARG, "bad parameter / moment planes");
+    if (!scene_ok(p_out) || !scene_ok(m_out) || !scene_ok(v_out) || capacity < 0 || p_out->N != capacity ||
+        m_out->N != capacity || v_out->N != capacity)
+        return fail(c, GS_ERR_INVALID_ARG, "output planes must hold capacity Gaussians (their N = capacity)");
+    if (!dp || !n_out || (p->N > 0 && (!grad_acc || !grad_cnt || !normals)))
+        return fail(c, GS_ERR_INVALID_ARG, "null statistics, normals, params or n_out");
+    if (!(dp->scale_threshold > 0.f) || !(dp->min_opacity > 0.f && dp->min_opacity < 1.f) ||
+        !(dp->split_div > 0.f) || !(dp->grad_threshold >= 0.f))
+        return fail(c, GS_ERR_INVALID_ARG, "densify params out of range");
+    if (p->N >= ((int64_t)1 << 31) || capacity >= ((int64_t)1 << 32))
+        return fail(c, GS_ERR_INVALID_ARG, "N must be below 2^31 and capacity below 2^32");
+    const int64_t N = p->N;
+    gs_status r;
+    if ((r = ensure(c, c->dens_cnt, 4 * (size_t)(N > 0 ? N : 1))) || (r = ensure(c, c->dens_off, 4 * (size_t)(N > 0 ? N : 1))) ||
+        (r = ensure(c, c->scan_tmp, scan_temp_bytes(N))) || (r = ensure(c, c->total, 64)))
+        return r;
+    cudaStream_t st = S(stream);
+    DensifyArgs d;
+    d.grad_thr = dp->grad_threshold;
+    // thresholds rounded once from double, so a float32 reimplementation can match them bit for bit
+    d.log_scale_thr = (float)log((double)dp->scale_threshold);
+    d.logit_min = (float)log((double)dp->min_opacity / (1.0 - (double)dp->min_opacity));
+    d.log_div = (float)log((double)dp->split_div);
+    launch_densify_count(view_of(p), grad_acc, grad_cnt, d, ptr<uint32_t>(c->dens_cnt), st);
+    launch_exclusive_scan(ptr<uint32_t>(c->dens_cnt), ptr<uint32_t>(c->dens_off), N,
+                          ptr<unsigned long long>(c->total), c->scan_tmp.p, st);
+    launch_densify_emit(view_of(p), view_of(m), view_of(v), grad_acc, grad_cnt, normals, d,
+                        ptr<uint32_t>(c->dens_off), ptr<unsigned long long>(c->total), mut_of(p_out),
+                        mut_of(m_out), mut_of(v_out), st);
+    if ((r = cuda_check(c, "gs_densify")) != GS_OK) return r;
+    uint64_t total = 0;
+    if ((r = read_total(c, st, &total)) != GS_OK) return r;
+    *n_out = (int64_t)total;
+    if ((int64_t)total > capacity) return fail(c, GS_ERR_CAPACITY, "densify needs %llu Gaussians, capacity %lld",
+                                               (unsigned long long)total, (long long)capacity);
+    return GS_OK;
+}
+
+gs_status gs_reset_opacity(gs_ctx *c, gs_scene *p, gs_scene *m, gs_scene *v, float max_opacity, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(p) || !scene_ok(m) || !scene_ok(v) || m->N != p->N || v->N != p->N)
+        return fail(c, GS_ERR_INVALID_ARG, "bad parameter / moment planes");
+    if (!(max_opacity > 0.f && max_opacity < 1.f)) return fail(c, GS_ERR_INVALID_ARG, "max_opacity outside (0, 1)");
+    const float logit_max = (float)log((double)max_opacity / (1.0 - (double)max_opacity));
+    launch_reset_opacity(mut_of(p), mut_of(m), mut_of(v), logit_max, S(stream));
+    return cuda_check(c, "gs_reset_opacity");
+}
+
+gs_status gs_division_points(gs_ctx *c, const uint32_t *cost, int64_t T, int32_t P, uint32_t *div, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!cost || !div || T < 1 || T >= ((int64_t)1 << 31) || P < 1 || P > (1 << 20))
+        return fail(c, GS_ERR_INVALID_ARG, "bad cost / div / T / P");
+    gs_status r;
+    if ((r = ensure(c, c->tile_cost, 4 * (size_t)T)) || (r = ensure(c, c->tile_excl, 4 * (size_t)T)) ||
+        (r = ensure(c, c->scan_tmp, scan_temp_bytes(T))) || (r = ensure(c, c->div_tot, 64)))
+        return r;
+    c->cost_tiles = 0;                              // the schedule's measured costs are overwritten
+    cudaStream_t st = S(stream);
+    cudaMemcpyAsync(c->tile_cost.p, cost, 4 * (size_t)T, cudaMemcpyDeviceToDevice, st);
+    launch_division_points(ptr<uint32_t>(c->tile_cost), (uint32_t)T, (uint32_t)P, ptr<uint32_t>(c->tile_excl),
+                           c->scan_tmp.p, ptr<unsigned long long>(c->div_tot), div, st);
+    return cuda_check(c, "gs_division_points");
+}
+
+gs_status gs_spatial_order(gs_ctx *c, const gs_scene *scene, uint32_t *perm, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(scene) || (scene->N > 0 && !perm)) return fail(c, GS_ERR_INVALID_ARG, "bad scene / perm");
+    if (scene->N >= ((int64_t)1 << 31)) return fail(c, GS_ERR_INVALID_ARG, "N must be below 2^31");
+    gs_status r;
+    if ((r = ensure(c, c->order_tmp, spatial_order_temp_bytes(scene->N))) != GS_OK) return r;
+    launch_spatial_order(reinterpret_cast<const float4 *>(scene->mo), scene->N, perm, c->order_tmp.p, c->status,
+                         S(stream));
+    return cuda_check(c, "gs_spatial_order");
+}
+
+gs_status gs_permute(gs_ctx *c, const gs_scene *src, const uint32_t *perm, gs_scene *dst, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_ok(src) || !scene_ok(dst) || dst->N != src->N || (src->N > 0 && !perm))
+        return fail(c, GS_ERR_INVALID_ARG, "bad planes / perm");
+    if (src->mo == dst->mo || src->ls == dst->ls || src->q == dst->q || src->sh == dst->sh)
+        return fail(c, GS_ERR_INVALID_ARG, "gs_permute works out of place");
+    launch_permute(view_of(src), perm, mut_of(dst), S(stream));
+    return cuda_check(c, "gs_permute");
 }
 
 gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_scene *v, int64_t step,
@@ -792,12 +918,33 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     if (r != GS_OK) return r;
     set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
     const BlendParams bp = blend_of(c->hp);
-    const uint32_t *order = tile_order_for(c, vb, ptr<uint2>(c->ranges), st);   // shared by both passes
+    const uint32_t *order = nullptr, *div_f = nullptr, *div_b = nullptr;
+    uint32_t *cost = nullptr;
+    if (c->hp.schedule == 1 && vb.total_tiles > 0) {
+        // Algorithm 1 over the previous step's measured tile costs (list lengths before the first)
+        const uint32_t T = vb.total_tiles;
+        cost = ptr<uint32_t>(c->tile_cost);
+        if (c->cost_tiles != T) {
+            launch_list_cost(ptr<uint2>(c->ranges), T, cost, st);
+            c->cost_tiles = T;
+        }
+        const uint32_t Pf = blend_resident_ctas(c->hp.tile, c->hp.smem_batch, c->hp.px_per_thread, false);
+        const uint32_t Pb = blend_resident_ctas(c->hp.tile, c->hp.smem_batch, c->hp.px_per_thread, true);
+        launch_division_points(cost, T, Pf, ptr<uint32_t>(c->tile_excl), c->scan_tmp.p,
+                               ptr<unsigned long long>(c->div_tot), ptr<uint32_t>(c->div_f), st);
+        launch_division_points(cost, T, Pb, ptr<uint32_t>(c->tile_excl), c->scan_tmp.p,
+                               ptr<unsigned long long>(c->div_tot), ptr<uint32_t>(c->div_b), st);
+        cudaMemsetAsync(cost, 0, 4 * (size_t)T, st);    // this step measures afresh
+        div_f = ptr<uint32_t>(c->div_f);
+        div_b = ptr<uint32_t>(c->div_b);
+    } else {
+        order = tile_order_for(c, vb, ptr<uint2>(c->ranges), st);   // shared by both passes
+    }
     launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
-                     c->status, order, st);
+                     c->status, order, st, div_f, cost);
     mark(c, st, 6);
     launch_loss(ptr<float>(c->img), targets, B, vb.v[0].W, vb.v[0].H, c->hp.lambda_dssim, loss_out,
-                ptr<float>(c->dimg), ptr<float>(c->maps), ptr<double>(c->acc), st);
+                ptr<float>(c->dimg), ptr<float>(c->maps), ptr<double>(c->acc), c->status, st);
     mark(c, st, 7);
     // three gradient planes of n float4 each, in one buffer: (u, v, opacity), conic, rgb
     if (n) cudaMemsetAsync(c->g_proj.p, 0, 48 * (size_t)n, st);
@@ -805,10 +952,12 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     float4 *gp = ptr<float4>(c->g_proj);
     const GradView gv{gp, gp + n, gp + 2 * n};
     launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
-                     gv, c->status, order, st);
+                     gv, c->status, order, st, div_b, cost);
     mark(c, st, 9);
     uint8_t *vis = c->hp.sparse_adam ? ptr<uint8_t>(c->vis) : nullptr;
-    launch_preprocess_bwd(sv, vb, pv, gv, false, mut_of(g), vis, st);
+    const bool stats = c->dacc && c->dN == N;
+    launch_preprocess_bwd(sv, vb, pv, gv, false, mut_of(g), vis, st, stats ? c->dacc : nullptr,
+                          stats ? c->dcnt : nullptr, c->status);
     mark(c, st, 10);
     AdamArgs aa = adam_args(c->hp, step, B, c->dstep);
     aa.vis = vis;

@@ -109,8 +109,13 @@ void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjVi
 // g holds the blending backward's moments (GradView) unless grads_ready.
 // vis (optional): vis[g] = 1 if some view has the Gaussian's radius > 0,
 // else 0; with vis the rows of unseen Gaussians are not written.
+// dacc / dcnt (optional, densification statistics): for each view in which
+// the Gaussian is visible, |dL_v/d(u, v)| is added to dacc[g] and 1 to dcnt[g],
+// unless status holds GS_ERR_CAPACITY or GS_ERR_TIMEOUT (status is read only
+// with dacc).
 void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
-                           bool grads_ready, const SceneMut &out, uint8_t *vis, cudaStream_t st);
+                           bool grads_ready, const SceneMut &out, uint8_t *vis, cudaStream_t st,
+                           float *dacc = nullptr, uint32_t *dcnt = nullptr, const DevStatus *status = nullptr);
 // In place: the moments of n entries -> gradients (moments_to_grads).
 void launch_moments_to_grads(const ProjView &p, int64_t n, const GradView &g, cudaStream_t st);
 
@@ -241,6 +246,32 @@ void launch_sort_fragments(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, u
                            uint64_t capacity, const uint32_t *count, int tile_bits, void *temp, DevStatus *status,
                            cudaStream_t st);
 
+// Storage order: perm = the Gaussians sorted stably by the Morton code of
+// their positions (10 bits per axis over the finite positions' bounding box);
+// temp holds spatial_order_temp_bytes(N).  launch_permute: dst[i] = src[perm[i]]
+// for all 15 planes.
+size_t spatial_order_temp_bytes(int64_t N);
+void launch_spatial_order(const float4 *mo, int64_t N, uint32_t *perm, void *temp, DevStatus *status,
+                          cudaStream_t st);
+void launch_permute(const SceneView &src, const uint32_t *perm, const SceneMut &dst, cudaStream_t st);
+
+// Densification (densify.cu).  Thresholds in the float32 domain the kernels
+// compare in: grad_thr (pixels), log_scale_thr = log(scale threshold),
+// logit_min = logit(min opacity), log_div = log(split divisor).
+struct DensifyArgs {
+    float grad_thr, log_scale_thr, logit_min, log_div;
+};
+// counts[g] = 0 (prune), 1 (keep) or 2 (clone or split).
+void launch_densify_count(const SceneView &p, const float *acc, const uint32_t *cnt, const DensifyArgs &d,
+                          uint32_t *counts, cudaStream_t st);
+// Writes every output row at offsets[g] (the exclusive scan of counts),
+// nothing when *total exceeds the outputs' N (their capacity).
+void launch_densify_emit(const SceneView &p, const SceneView &m, const SceneView &v, const float *acc,
+                         const uint32_t *cnt, const float *normals, const DensifyArgs &d, const uint32_t *offsets,
+                         const unsigned long long *total, const SceneMut &po, const SceneMut &mo,
+                         const SceneMut &vo, cudaStream_t st);
+void launch_reset_opacity(const SceneMut &p, const SceneMut &m, const SceneMut &v, float logit_max, cudaStream_t st);
+
 // Test hook (gs_debug_set_lookback): look-back spin limit (0 = default) and
 // whether tile 0 of every sort pass withholds its look-back words.
 void set_lookback_debug(uint32_t spin_limit, int withhold_first);
@@ -255,20 +286,34 @@ void launch_compose_keys(const ViewBatch &vb, int64_t N, const uint32_t *tiles, 
 // chunk: list entries a warp gathers and filters per shared-memory refill;
 // ppt: pixels per thread (blend_config_ok says which combinations are built).
 bool blend_config_ok(int tile, int chunk, int ppt);
+// div (optional): Algorithm 1's range starts for blend_resident_ctas(...)
+// persistent CTAs (launch_division_points), used instead of one CTA per
+// tile; cost (optional): each tile's measured cost is added there.
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                       const BlendParams &bp, int chunk, int ppt, DevStatus *status, const uint32_t *order,
-                      cudaStream_t st);
+                      cudaStream_t st, const uint32_t *div = nullptr, uint32_t *cost = nullptr);
 void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                       const BlendParams &bp, int chunk, int ppt, const GradView &g, DevStatus *status,
-                      const uint32_t *order, cudaStream_t st);
+                      const uint32_t *order, cudaStream_t st, const uint32_t *div = nullptr,
+                      uint32_t *cost = nullptr);
+uint32_t blend_resident_ctas(int tile, int chunk, int ppt, bool bwd);
+int sm_count();
+// Algorithm 1 over T tile costs for P ranges: div[k] = the first tile of
+// range k (costs are first clamped to (2^32 - 1) / T in place; excl: T words
+// of scratch; scan_tmp: scan_temp_bytes(T); total: one word).
+void launch_division_points(uint32_t *cost, uint32_t T, uint32_t P, uint32_t *excl, void *scan_tmp,
+                            unsigned long long *total, uint32_t *div, cudaStream_t st);
+// cost[t] = list length of tile t + 1.
+void launch_list_cost(const uint2 *ranges, uint32_t T, uint32_t *cost, cudaStream_t st);
 // Tile launch order for the blending kernels (order: launch slot -> tile;
 // null = index order): heaviest list first, worth it only for a few waves of
 // CTAs (tile_order_pays).  buckets: 64 words of scratch.
 bool tile_order_pays(uint32_t total_tiles);
 void launch_tile_order(const uint2 *ranges, uint32_t n, uint32_t *order, uint32_t *buckets, cudaStream_t st);
 
+// status: a staging wait that runs out records GS_ERR_TIMEOUT there.
 void launch_loss(const float *img, const float *target, int B, int W, int H, float lambda, float *loss_out,
-                 float *d_img, float *maps, double *acc, cudaStream_t st);
+                 float *d_img, float *maps, double *acc, DevStatus *status, cudaStream_t st);
 
 struct AdamArgs {
     float lr[15][4];   // per plane, per lane (already times sqrt(B) when asked)

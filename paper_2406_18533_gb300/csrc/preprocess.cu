@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(256) k_moments_to_grads(ProjView p, int64_t n,
 // Capped for 3 resident blocks (168 registers; uncapped it takes 181 and
 // fits 2): C3 8.4 -> 6.4 ms.
 __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatch vb, ProjView p, GradView gv,
-                                                        bool grads_ready, SceneMut out, uint8_t *vis)
+                                                        bool grads_ready, SceneMut out, uint8_t *vis,
+                                                        float *dacc, uint32_t *dcnt, const DevStatus *status)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= s.N) return;
@@ -284,6 +285,8 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatc
     float dX[3] = {0.f, 0.f, 0.f};
     float dlogit = 0.f;
     float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // dL/dSigma (symmetric), summed over views
+    float dnorm = 0.f;
+    uint32_t dviews = 0u;
 
     for (int v = 0; v < vb.B; ++v) {
         const int64_t idx = (int64_t)v * s.N + g;
@@ -293,6 +296,10 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatc
         float4 gxo = gv.d_xy_o[idx], gco = gv.d_conic[idx];
         const float4 grg = gv.d_rgb[idx];
         if (!grads_ready) moments_to_grads(co, float4(gxo), float4(gco), gxo, gco);
+        if (dacc) {                              // densification statistics of this view
+            dnorm += sqrtf(gxo.x * gxo.x + gxo.y * gxo.y);
+            ++dviews;
+        }
         dlogit += gxo.z * G.o * (1.f - G.o);
         // ---- colour -> SH and viewing direction
         float ddx = G.x - c.C[0], ddy = G.y - c.C[1], ddz = G.z - c.C[2];
@@ -427,6 +434,12 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatc
     dq[3] = 2.f * (-2.f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.f * z * d[4] + y * d[5] + x * d[6] + y * d[7]);
     const float pr = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
     const float iq = 1.f / G.qnorm;
+    // a step whose binning overflowed or whose sort gave up is run again or
+    // dropped: its statistics are not added
+    if (dacc && status->code != GS_ERR_CAPACITY && status->code != GS_ERR_TIMEOUT) {
+        dacc[g] += dnorm;
+        dcnt[g] += dviews;
+    }
     out.mo[g] = make_float4(dX[0] * invB, dX[1] * invB, dX[2] * invB, dlogit * invB);
     out.ls[g] = make_float4(dls[0] * invB, dls[1] * invB, dls[2] * invB, 0.f);
     out.q[g] = make_float4((dq[0] - w * pr) * iq * invB, (dq[1] - x * pr) * iq * invB,
@@ -450,12 +463,13 @@ void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjVi
 }
 
 void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
-                           bool grads_ready, const SceneMut &out, uint8_t *vis, cudaStream_t st)
+                           bool grads_ready, const SceneMut &out, uint8_t *vis, cudaStream_t st, float *dacc,
+                           uint32_t *dcnt, const DevStatus *status)
 {
     if (s.N == 0) return;
     const int threads = 128;
     const int64_t blocks = (s.N + threads - 1) / threads;
-    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, g, grads_ready, out, vis);
+    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, g, grads_ready, out, vis, dacc, dcnt, status);
     count_launches(1);
 }
 

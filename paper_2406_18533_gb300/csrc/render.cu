@@ -196,10 +196,19 @@ constexpr size_t smem_bytes()
     return (size_t)(TILE * TILE / (32 * PPT)) * CH * 3 * sizeof(float4);
 }
 
+// Measured cost of one warp's part of a tile (for the Algorithm 1 schedule):
+// elapsed SM cycles / 1024, plus 1 so that an empty tile still counts.
+__device__ __forceinline__ void add_cost(uint32_t *cost, uint32_t tile_id, long long t0, int lane)
+{
+    if (cost && lane == 0) atomicAdd(&cost[tile_id], (uint32_t)((clock64() - t0) >> 10) + 1u);
+}
+
+// The forward of one tile (tile_id, global over the batch's views) by this
+// CTA; each warp works alone, so a CTA can go on to another tile warp by warp.
 template <int TILE, int CH, int PPT>
-__global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, ProjView p, const uint32_t *vals,
-                                                                const uint2 *ranges, BlendParams bp,
-                                                                DevStatus *status, const uint32_t *order)
+__device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch &vb, const ProjView &p,
+                                               const uint32_t *vals, const uint2 *ranges, const BlendParams &bp,
+                                               DevStatus *status, uint32_t *cost)
 {
     constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
@@ -207,8 +216,8 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, Pr
     float4 *s_xyc = smem + warp * CH;              // u, v, exponent cut, list position + 1 (bits)
     float4 *s_q = smem + (NW + warp) * CH;         // A, B, C, opacity
     float4 *s_rgb = smem + (2 * NW + warp) * CH;
+    const long long t0 = cost ? clock64() : 0ll;
 
-    const uint32_t tile_id = order ? order[blockIdx.x] : blockIdx.x;   // launch order (launch_tile_order)
     const int v = find_view(vb, tile_id);
     const ViewCam &c = vb.v[v];
     const PixelSite<PPT> ps = pixel_site<TILE, PPT>(c, tile_id - c.tile_base, warp, lane);
@@ -344,15 +353,41 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, Pr
     }
     if (lane == 0 && evals) atomicAdd(&status->counters[1], (unsigned long long)evals);
     if (lane == 0 && contrib) atomicAdd(&status->counters[5], (unsigned long long)contrib);
+    add_cost(cost, tile_id, t0, lane);
+}
+
+// One CTA per tile, in launch order `order` (null: index order).
+template <int TILE, int CH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, ProjView p, const uint32_t *vals,
+                                                                const uint2 *ranges, BlendParams bp,
+                                                                DevStatus *status, const uint32_t *order,
+                                                                uint32_t *cost)
+{
+    const uint32_t tile_id = order ? order[blockIdx.x] : blockIdx.x;   // launch order (launch_tile_order)
+    blend_fwd_tile<TILE, CH, PPT>(tile_id, vb, p, vals, ranges, bp, status, cost);
+}
+
+// Algorithm 1 schedule: CTA k blends the tiles [div[k], div[k + 1]) one after
+// another (the last range ends at the last tile), ranges of about equal
+// measured cost.
+template <int TILE, int CH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd_ranges(ViewBatch vb, ProjView p,
+                                                                       const uint32_t *vals, const uint2 *ranges,
+                                                                       BlendParams bp, DevStatus *status,
+                                                                       const uint32_t *div, uint32_t *cost)
+{
+    const uint32_t lo = div[blockIdx.x];
+    const uint32_t hi = blockIdx.x + 1 < gridDim.x ? min(div[blockIdx.x + 1], vb.total_tiles) : vb.total_tiles;
+    for (uint32_t t = lo; t < hi; ++t) blend_fwd_tile<TILE, CH, PPT>(t, vb, p, vals, ranges, bp, status, cost);
 }
 
 // With 2 pixels per thread the backward is held to 64 registers (8 CTAs of
 // 128 threads per SM; 4 bytes of spill): 1% faster on GB300 than at 68
 // registers and 7 CTAs.  Other shapes keep the compiler's choice.
 template <int TILE, int CH, int PPT>
-__global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1)) k_blend_bwd(ViewBatch vb, ProjView p, const uint32_t *vals,
-                                                                const uint2 *ranges, BlendParams bp, GradView gv,
-                                                                DevStatus *status, const uint32_t *order)
+__device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch &vb, const ProjView &p,
+                                               const uint32_t *vals, const uint2 *ranges, const BlendParams &bp,
+                                               const GradView &gv, DevStatus *status, uint32_t *cost)
 {
     constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
@@ -360,8 +395,8 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1)) k_blend_
     float4 *s_xyc = smem + warp * CH;                // u, v, exponent cut, list position (bits)
     float4 *s_q = smem + (NW + warp) * CH;
     float4 *s_rgb = smem + (2 * NW + warp) * CH;    // r, g, b, Gaussian index (bits)
+    const long long t0 = cost ? clock64() : 0ll;
 
-    const uint32_t tile_id = order ? order[blockIdx.x] : blockIdx.x;   // launch order (launch_tile_order)
     const int v = find_view(vb, tile_id);
     const ViewCam &c = vb.v[v];
     const PixelSite<PPT> ps = pixel_site<TILE, PPT>(c, tile_id - c.tile_base, warp, lane);
@@ -504,6 +539,27 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1)) k_blend_
         if (e) atomicAdd(&status->counters[2], e);
         if (wk) atomicAdd(&status->counters[4], wk);
     }
+    add_cost(cost, tile_id, t0, lane);
+}
+
+template <int TILE, int CH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1)) k_blend_bwd(ViewBatch vb, ProjView p, const uint32_t *vals,
+                                                                const uint2 *ranges, BlendParams bp, GradView gv,
+                                                                DevStatus *status, const uint32_t *order,
+                                                                uint32_t *cost)
+{
+    const uint32_t tile_id = order ? order[blockIdx.x] : blockIdx.x;   // launch order (launch_tile_order)
+    blend_bwd_tile<TILE, CH, PPT>(tile_id, vb, p, vals, ranges, bp, gv, status, cost);
+}
+
+template <int TILE, int CH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1))
+    k_blend_bwd_ranges(ViewBatch vb, ProjView p, const uint32_t *vals, const uint2 *ranges, BlendParams bp,
+                       GradView gv, DevStatus *status, const uint32_t *div, uint32_t *cost)
+{
+    const uint32_t lo = div[blockIdx.x];
+    const uint32_t hi = blockIdx.x + 1 < gridDim.x ? min(div[blockIdx.x + 1], vb.total_tiles) : vb.total_tiles;
+    for (uint32_t t = lo; t < hi; ++t) blend_bwd_tile<TILE, CH, PPT>(t, vb, p, vals, ranges, bp, gv, status, cost);
 }
 
 // Launch order of the tiles, heaviest list first.  With few waves of CTAs
@@ -560,25 +616,113 @@ bool smem_opt_in(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 
+// Schedule of a blending launch: one CTA per tile in `order` (null: index
+// order), or, with div, Algorithm 1's ranges for `ctas` persistent CTAs; cost
+// (optional) receives each tile's measured cost.
+struct Sched {
+    const uint32_t *order;
+    const uint32_t *div;
+    uint32_t ctas;
+    uint32_t *cost;
+};
+
 template <int TILE, int CH, int PPT>
 void fwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                const BlendParams &bp, DevStatus *status, const uint32_t *order, cudaStream_t st)
+                const BlendParams &bp, DevStatus *status, const Sched &sc, cudaStream_t st)
 {
     constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
-    static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH, PPT>, sm);
+    static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH, PPT>, sm) && smem_opt_in(k_blend_fwd_ranges<TILE, CH, PPT>, sm);
     (void)ok;
-    k_blend_fwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status, order);
+    if (sc.div)
+        k_blend_fwd_ranges<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
+                                                                                sc.div, sc.cost);
+    else
+        k_blend_fwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
+                                                                                 sc.order, sc.cost);
 }
 
 template <int TILE, int CH, int PPT>
 void bwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
-                const BlendParams &bp, const GradView &g, DevStatus *status, const uint32_t *order,
-                cudaStream_t st)
+                const BlendParams &bp, const GradView &g, DevStatus *status, const Sched &sc, cudaStream_t st)
 {
     constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
-    static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH, PPT>, sm);
+    static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH, PPT>, sm) && smem_opt_in(k_blend_bwd_ranges<TILE, CH, PPT>, sm);
     (void)ok;
-    k_blend_bwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status, order);
+    if (sc.div)
+        k_blend_bwd_ranges<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status,
+                                                                                sc.div, sc.cost);
+    else
+        k_blend_bwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status,
+                                                                                 sc.order, sc.cost);
+}
+
+// Resident CTAs of the range kernel on the whole device.
+template <int TILE, int CH, int PPT, bool BWD>
+uint32_t resident_ctas()
+{
+    static uint32_t n = 0;
+    if (!n) {
+        constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
+        int per_sm = 0;
+        cudaError_t e;
+        if (BWD) {
+            smem_opt_in(k_blend_bwd_ranges<TILE, CH, PPT>, sm);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_bwd_ranges<TILE, CH, PPT>,
+                                                              TILE * TILE / PPT, sm);
+        } else {
+            smem_opt_in(k_blend_fwd_ranges<TILE, CH, PPT>, sm);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_fwd_ranges<TILE, CH, PPT>,
+                                                              TILE * TILE / PPT, sm);
+        }
+        if (e != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        n = (uint32_t)per_sm * (uint32_t)sm_count();
+    }
+    return n;
+}
+
+// Algorithm 1 (division points), with the tiles as the pixel blocks and the
+// persistent CTAs as the GPUs: CT = cumsum(cost) (inclusive), ET = CT[T - 1]
+// / P, thresholds k ET for k = 0 .. P - 1, div[k] = searchsorted(CT, k ET)
+// (the first tile whose cumulative cost reaches the threshold) = the first
+// tile of range k; range k is [div[k], div[k + 1]) and the last ends at T.
+// The comparison CT[i] >= k CT[T - 1] / P is evaluated exactly as
+// P CT[i] >= k CT[T - 1] in 64-bit integers.  excl: the exclusive prefix
+// sums (CT = excl + cost).
+__global__ void k_division_points(const uint32_t *excl, const uint32_t *cost, uint32_t T, uint32_t P,
+                                  const unsigned long long *total, uint32_t *div)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const unsigned long long thr = *total * (unsigned long long)k;
+    uint32_t lo = 0, hi = T;                       // first i with P CT[i] >= k total
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const unsigned long long ct = (unsigned long long)excl[mid] + cost[mid];
+        if (ct * P >= thr) hi = mid; else lo = mid + 1;
+    }
+    div[k] = lo;
+}
+
+// cost[t] = min(cost[t], cap): with cap = (2^32 - 1) / T the 32-bit prefix
+// sums cannot wrap, so the division points stay monotone and the ranges
+// cover every tile exactly once.
+__global__ void k_clamp_cost(uint32_t *cost, uint32_t T, uint32_t cap)
+{
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
+        cost[t] = min(cost[t], cap);
+}
+
+// cost[t] = the tile's list length + 1 (the cost model before any step has
+// been measured).
+__global__ void k_list_cost(const uint2 *ranges, uint32_t T, uint32_t *cost)
+{
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        const uint2 r = ranges[t];
+        cost[t] = (r.y > r.x ? r.y - r.x : 0u) + 1u;
+    }
 }
 
 }  // namespace
@@ -604,31 +748,66 @@ bool blend_config_ok(int tile, int chunk, int ppt)
 
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                       const BlendParams &bp, int chunk, int ppt, DevStatus *status, const uint32_t *order,
-                      cudaStream_t st)
+                      cudaStream_t st, const uint32_t *div, uint32_t *cost)
 {
     if (vb.total_tiles == 0) return;
+    Sched sc{order, div, 0u, cost};
     switch (vb.tile * 10000 + chunk * 10 + ppt) {
 #define GS_FWD_CASE(T, C, P) \
-    case T * 10000 + C * 10 + P: fwd_launch<T, C, P>(vb, p, vals, ranges, bp, status, order, st); break;
+    case T * 10000 + C * 10 + P: sc.ctas = div ? resident_ctas<T, C, P, false>() : 0u; \
+        fwd_launch<T, C, P>(vb, p, vals, ranges, bp, status, sc, st); break;
         GS_BLEND_CASES(GS_FWD_CASE)
 #undef GS_FWD_CASE
-    default: fwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, status, order, st); break;
+    default: sc.div = nullptr; fwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, status, sc, st); break;
     }
     count_launches(1);
 }
 
 void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                       const BlendParams &bp, int chunk, int ppt, const GradView &g, DevStatus *status,
-                      const uint32_t *order, cudaStream_t st)
+                      const uint32_t *order, cudaStream_t st, const uint32_t *div, uint32_t *cost)
 {
     if (vb.total_tiles == 0) return;
+    Sched sc{order, div, 0u, cost};
     switch (vb.tile * 10000 + chunk * 10 + ppt) {
 #define GS_BWD_CASE(T, C, P) \
-    case T * 10000 + C * 10 + P: bwd_launch<T, C, P>(vb, p, vals, ranges, bp, g, status, order, st); break;
+    case T * 10000 + C * 10 + P: sc.ctas = div ? resident_ctas<T, C, P, true>() : 0u; \
+        bwd_launch<T, C, P>(vb, p, vals, ranges, bp, g, status, sc, st); break;
         GS_BLEND_CASES(GS_BWD_CASE)
 #undef GS_BWD_CASE
-    default: bwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, g, status, order, st); break;
+    default: sc.div = nullptr; bwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, g, status, sc, st); break;
     }
+    count_launches(1);
+}
+
+uint32_t blend_resident_ctas(int tile, int chunk, int ppt, bool bwd)
+{
+    switch (tile * 10000 + chunk * 10 + ppt) {
+#define GS_RES_CASE(T, C, P) \
+    case T * 10000 + C * 10 + P: return bwd ? resident_ctas<T, C, P, true>() : resident_ctas<T, C, P, false>();
+        GS_BLEND_CASES(GS_RES_CASE)
+#undef GS_RES_CASE
+    default: return 0u;
+    }
+}
+
+void launch_division_points(uint32_t *cost, uint32_t T, uint32_t P, uint32_t *excl, void *scan_tmp,
+                            unsigned long long *total, uint32_t *div, cudaStream_t st)
+{
+    if (T == 0 || P == 0) return;
+    const unsigned blocks = (T + 255) / 256 < 4096u ? (T + 255) / 256 : 4096u;
+    k_clamp_cost<<<blocks, 256, 0, st>>>(cost, T, 0xffffffffu / T);
+    count_launches(1);
+    launch_exclusive_scan(cost, excl, T, total, scan_tmp, st);
+    k_division_points<<<(P + 255) / 256, 256, 0, st>>>(excl, cost, T, P, total, div);
+    count_launches(1);
+}
+
+void launch_list_cost(const uint2 *ranges, uint32_t T, uint32_t *cost, cudaStream_t st)
+{
+    if (T == 0) return;
+    const unsigned blocks = (T + 255) / 256 < 4096u ? (T + 255) / 256 : 4096u;
+    k_list_cost<<<blocks, 256, 0, st>>>(ranges, T, cost);
     count_launches(1);
 }
 

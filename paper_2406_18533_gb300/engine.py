@@ -240,6 +240,60 @@ class Context:
         self._c("gs_adam_step_sparse", self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm),
                 ctypes.byref(sv), _ptr(visible), int(step), int(batch), _stream())
 
+    def set_densify_stats(self, acc: torch.Tensor | None, cnt: torch.Tensor | None):
+        """gs_set_densify_stats: training steps accumulate |dL_v/d(u, v)| per
+        visible (view, Gaussian) into acc (float32 [N]) and count into cnt
+        (int32 [N], uint32 bits); None stops it."""
+        if acc is None:
+            self._c("gs_set_densify_stats", self.h, None, None, 0)
+            self._dstats = None
+            return
+        if acc.dtype != torch.float32 or cnt.dtype != torch.int32 or acc.numel() != cnt.numel():
+            raise ValueError("acc must be float32 and cnt int32, one entry per Gaussian each")
+        self._c("gs_set_densify_stats", self.h, _ptr(acc), _ptr(cnt), int(acc.numel()))
+        self._dstats = (acc, cnt)        # keep them alive while the library holds their addresses
+
+    def densify(self, p: DeviceScene, m: DeviceScene, v: DeviceScene, acc, cnt, normals, grad_threshold,
+                scale_threshold, min_opacity=0.005, split_div=1.6, capacity=None):
+        """gs_densify: returns (p, m, v) of the densified scene (new tensors)."""
+        cap = capacity if capacity is not None else 2 * p.N
+        po, mo, vo = (DeviceScene.zeros(cap, p.mo.device, p.sh_degree) for _ in range(3))
+        dp = B.gs_densify_params(float(grad_threshold), float(scale_threshold), float(min_opacity), float(split_div))
+        n_out = ctypes.c_int64(0)
+        sp, sm, sv, so, smo, svo = p.struct(), m.struct(), v.struct(), po.struct(), mo.struct(), vo.struct()
+        self._c("gs_densify", self.h, ctypes.byref(sp), ctypes.byref(sm), ctypes.byref(sv), _ptr(acc), _ptr(cnt),
+                _ptr(normals), ctypes.byref(dp), ctypes.byref(so), ctypes.byref(smo), ctypes.byref(svo), int(cap),
+                ctypes.byref(n_out), _stream())
+        n = int(n_out.value)
+        cut = lambda s: DeviceScene(s.mo[:n].clone(), s.ls[:n].clone(), s.q[:n].clone(),
+                                    s.sh[:, :n].contiguous(), s.sh_degree)
+        return cut(po), cut(mo), cut(vo)
+
+    def reset_opacity(self, p: DeviceScene, m: DeviceScene, v: DeviceScene, max_opacity=0.01):
+        sp, sm, sv = p.struct(), m.struct(), v.struct()
+        self._c("gs_reset_opacity", self.h, ctypes.byref(sp), ctypes.byref(sm), ctypes.byref(sv),
+                ctypes.c_float(max_opacity), _stream())
+
+    def division_points(self, cost: torch.Tensor, parts: int) -> torch.Tensor:
+        """gs_division_points (Algorithm 1) of int32 (uint32 bits) costs."""
+        div = torch.empty(parts, dtype=torch.int32, device=cost.device)
+        self._c("gs_division_points", self.h, _ptr(cost), int(cost.numel()), int(parts), _ptr(div), _stream())
+        return div
+
+    def spatial_order(self, scene: DeviceScene) -> torch.Tensor:
+        """gs_spatial_order: the Morton-order permutation of the Gaussians (int32 view of uint32)."""
+        perm = torch.empty(max(scene.N, 1), dtype=torch.int32, device=scene.mo.device)
+        s = scene.struct()
+        self._c("gs_spatial_order", self.h, ctypes.byref(s), _ptr(perm), _stream())
+        return perm[:scene.N]
+
+    def permute(self, scene: DeviceScene, perm: torch.Tensor) -> DeviceScene:
+        """gs_permute: a new scene with entry i = scene's entry perm[i]."""
+        out = scene.zeros_like()
+        s, d = scene.struct(), out.struct()
+        self._c("gs_permute", self.h, ctypes.byref(s), _ptr(perm), ctypes.byref(d), _stream())
+        return out
+
     def train_step(self, p, g, m, v, step, cams, targets, loss_out=None, cam_arr=None, check=False):
         """One gs_train_step.  check=True synchronises, and when the fragment
         buffer overflowed (the library then skipped the update) grows it and

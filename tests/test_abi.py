@@ -37,7 +37,7 @@ def test_binding_covers_every_entry_point(libgs):
 
 def test_abi_version_and_defaults(libgs):
     from paper_2406_18533_gb300 import binding
-    assert libgs.gs_abi_version() == 2
+    assert libgs.gs_abi_version() == 3
     hp = binding.default_hparams()
     assert hp.tile == 16 and hp.smem_batch == 64 and hp.px_per_thread == 1
     assert abs(hp.alpha_min - 1 / 255) < 1e-9 and abs(hp.alpha_max - 0.99) < 1e-7 and abs(hp.T_min - 1e-4) < 1e-10
@@ -48,7 +48,7 @@ def test_struct_layout_matches_c(tmp_path):
     """sizeof and every field offset of the ctypes mirrors equal what gcc
     computes from include/gs.h."""
     from paper_2406_18533_gb300 import binding as b
-    structs = [b.gs_camera, b.gs_scene, b.gs_hparams, b.gs_proj, b.gs_proj_grad, b.gs_bins]
+    structs = [b.gs_camera, b.gs_scene, b.gs_hparams, b.gs_proj, b.gs_proj_grad, b.gs_bins, b.gs_densify_params]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs.h"', 'int main(void) {']
     for st in structs:
         n = st.__name__

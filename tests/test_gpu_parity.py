@@ -216,8 +216,11 @@ def test_preprocess_bwd_stage(eng, oracle):
 
 # ------------------------------------------------------------------ loss and Adam
 
-def test_loss_stage(eng, oracle):
-    Bv, H, W = 2, 70, 100
+@pytest.mark.parametrize("W,H", [(100, 70), (97, 61)])
+def test_loss_stage(eng, oracle, W, H):
+    """Widths that are a multiple of 4 floats stage their rows with TMA tiles,
+    the others with element copies; both against the oracle."""
+    Bv = 2
     rng = np.random.default_rng(0)
     img = rng.random((Bv, 3, H, W)).astype(np.float32)
     tgt = rng.random((Bv, 3, H, W)).astype(np.float32)
@@ -713,6 +716,108 @@ def test_c3_full_size_sampled_window(eng, oracle):
     ref = oracle.render_window_admissible(sc, cam, (x0, y0, w, h))
     assert len(ref["index"]) > 10000
     _check_image(ref, img[:, y0:y0 + h, x0:x0 + w], "C3 window")
+
+
+# ------------------------------------------------------------------ Algorithm 1 schedule
+
+@pytest.mark.parametrize("T,P", [(1, 1), (7, 3), (8160, 1216), (130_560, 1216), (5000, 4096)])
+def test_division_points_match_oracle(eng, oracle, T, P):
+    rng = np.random.default_rng(T + P)
+    cost = rng.integers(0, 30_000, T).astype(np.uint32)
+    cost[rng.random(T) < 0.1] = 0
+    ctx = eng.Context()
+    div = ctx.division_points(torch.from_numpy(cost.view(np.int32)).cuda(), P).cpu().numpy().astype(np.int64)
+    assert np.array_equal(div, oracle.division_points(cost.astype(np.int64), P))
+
+
+def test_algorithm1_schedule_gives_the_same_training_steps(eng):
+    """Training with the Algorithm 1 schedule (persistent CTAs over ranges of
+    equal measured cost; the first step uses list lengths, later steps the
+    previous step's measured costs) gives the same first loss bit for bit
+    (the images are computed pixel by pixel the same way), and the same later
+    losses and parameters up to the order of the gradient atomics."""
+    sc, rng = synth.aerial_scene(60_000, n_clusters=8, seed=21)
+    cams = synth.ring_cameras(rng, 3, (25.0, 80.0), W=320, H=180)
+    tg = torch.from_numpy(np.stack([synth.blurred_noise_target(rng, 180, 320) for _ in cams])).cuda()
+    out = []
+    for schedule in (0, 1):
+        ctx = eng.Context(schedule=schedule)
+        P = eng.DeviceScene.from_host(sc)
+        G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
+        losses = [ctx.train_step(P, G, M, V, 0, cams, tg, check=True).clone() for _ in range(3)]
+        torch.cuda.synchronize()
+        out.append((losses, P.flat().cpu().numpy().astype(np.float64), ctx.counters()))
+    assert torch.equal(out[0][0][0], out[1][0][0])              # step 1: the same parameters on both
+    for a, b in zip(out[0][0][1:], out[1][0][1:]):              # later: up to the atomics' order
+        assert torch.allclose(a, b, rtol=1e-5, atol=0)
+    assert rel_l2(out[1][1], out[0][1]) < 1e-5
+
+
+# ------------------------------------------------------------------ storage order
+
+def _tiles_without_depth_ties(oracle, sc, cam, tile=16):
+    """[H, W] mask of the pixels whose tile holds no two Gaussians of equal
+    float32 depth (rectangles from the oracle's transformation, widened by
+    one tile for float32 membership)."""
+    pr = oracle.project(sc, cam, tile)
+    vis = np.nonzero(pr["vis"] > 0)[0]
+    d = pr["depth"][vis].astype(np.float32)
+    order = np.argsort(d, kind="stable")
+    tied = np.zeros(len(vis), bool)
+    eq = d[order][1:] == d[order][:-1]
+    tied[order[1:][eq]] = True
+    tied[order[:-1][eq]] = True
+    TX, TY = -(-cam.W // tile), -(-cam.H // tile)
+    bad = np.zeros((TY, TX), bool)
+    for g in vis[tied]:
+        x0, x1, y0, y1 = pr["rect"][g]
+        bad[max(0, y0 - 1):y1 + 2, max(0, x0 - 1):x1 + 2] = True
+    return ~np.repeat(np.repeat(bad, tile, 0), tile, 1)[:cam.H, :cam.W]
+
+
+def test_spatial_order_and_permute(eng, oracle):
+    """gs_spatial_order equals the oracle's Morton order bit for bit (an
+    integer result decided by float32 arithmetic that both sides round the
+    same way), including equal positions and a non-finite one; gs_permute
+    moves all 60 floats; and the reordered scene renders the same image bit
+    for bit wherever no two Gaussians of equal float32 depth share a tile
+    (ties composite in index order, which relabelling changes), with 2D
+    gradients equal up to the order of the atomic adds once mapped back."""
+    sc, rng = synth.aerial_scene(60_000, n_clusters=16, seed=17)
+    sc.mo[100] = sc.mo[7]                        # equal positions: index order
+    sc.mo[200, 1] = np.nan                       # non-finite: cell 0, culled in renders
+    ctx = eng.Context()
+    P = eng.DeviceScene.from_host(sc)
+    perm = ctx.spatial_order(P)
+    ref = oracle.morton_order(sc)
+    got = perm.cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, ref)
+    Q = ctx.permute(P, perm)
+    assert torch.equal(Q.flat().view(torch.int32), P.flat()[perm.long()].view(torch.int32))   # bits (a NaN row)
+    cams = synth.ring_cameras(rng, 2, (30.0, 90.0), W=320, H=180)
+    a = ctx.render(P, cams, check=True)
+    b = ctx.render(Q, cams, check=True)
+    for k in range(2):
+        # equal float32 depths composite in index order, which relabelling
+        # changes: their shared tiles are left out, every other pixel is equal
+        same = _tiles_without_depth_ties(oracle, sc, cams[k])
+        assert same.mean() > 0.2
+        assert torch.equal(a[k][:, torch.from_numpy(same).cuda()], b[k][:, torch.from_numpy(same).cuda()])
+    pa, pb = ctx.preprocess(P, cams[:1]), ctx.preprocess(Q, cams[:1])
+    ba, bb = ctx.bin(pa, cams[:1]), ctx.bin(pb, cams[:1])
+    outs = []
+    keep = torch.from_numpy(_tiles_without_depth_ties(oracle, sc, cams[0])).cuda()
+    for pr, bn in ((pa, ba), (pb, bb)):
+        img, T, nc = ctx.render_fwd(pr, bn, cams[:1])
+        dimg = torch.ones_like(img) * keep                  # no upstream gradient on tie tiles
+        outs.append((img, ctx.render_bwd(pr, bn, cams[:1], T, nc, dimg.contiguous())))
+    assert torch.equal(outs[0][0][:, :, keep], outs[1][0][:, :, keep])
+    inv = torch.empty_like(perm)
+    inv[perm.long()] = torch.arange(sc.N, dtype=perm.dtype, device=perm.device)
+    for name in ("d_xy_o", "d_conic", "d_rgb"):
+        ga = getattr(outs[0][1], name)[0]
+        gb = getattr(outs[1][1], name)[0][inv.long()]
+        assert rel_l2(gb.cpu().numpy(), ga.cpu().numpy()) < 1e-5, name
 
 
 # ------------------------------------------------------------------ autotuner

@@ -286,3 +286,124 @@ def test_train_step_visible_only_skips_unseen_gaussians(oracle):
     assert np.array_equal(sp[~seen], p0[~seen]) and np.array_equal(sm[~seen], m[~seen]) and np.array_equal(sv[~seen], v[~seen])
     assert np.allclose(sp[seen], dp[seen], rtol=1e-10, atol=1e-15) and np.allclose(sm[seen], dm[seen], rtol=1e-8, atol=1e-18)
     assert np.abs(dp[~seen] - p0[~seen]).max() > 0
+
+
+# ---------------------------------------------------------------- densification (App. A.1)
+
+def _densify_case():
+    """Eight Gaussians, one per case: pruned (opacity below 0.005), kept (no
+    view, low gradient), cloned (gradient test passes exactly at the
+    threshold, small scale), split (large scale), and others."""
+    rng = np.random.default_rng(9)
+    N = 8
+    p = rng.standard_normal((N, 60)).astype(np.float32)
+    p[:, 7] = 0
+    p[:, 3] = 1.0                                           # opacity 0.73
+    p[0, 3] = -6.0                                          # opacity 0.0025: pruned
+    p[:, 4:7] = np.log(0.05)                                # small scales
+    p[3, 4:7] = (np.log(0.05), np.log(0.5), np.log(0.02))   # one axis large: split
+    p[6, 4:7] = np.log(0.3)
+    m = rng.standard_normal((N, 60)).astype(np.float32) * 0.1
+    v = rng.random((N, 60)).astype(np.float32) * 0.1
+    cnt = np.array([5, 0, 4, 4, 3, 2, 7, 4], np.uint32)
+    thr = np.float32(0.25)
+    acc = (thr * cnt.astype(np.float32)).astype(np.float32)  # exactly at the threshold: grows
+    acc[1] = 9.0                                            # no view: kept whatever acc says
+    acc[4] = np.nextafter(acc[4], np.float32(0))            # one ulp below: kept
+    acc[5] *= 3
+    normals = rng.standard_normal((N, 2, 3))
+    return p, m, v, acc, cnt, normals, float(thr)
+
+
+def test_densify_actions_and_rows(oracle):
+    p, m, v, acc, cnt, normals, thr = _densify_case()
+    act = oracle.densify_actions(p, acc, cnt, thr, 0.1)
+    assert list(act) == [0, 1, 2, 3, 1, 2, 3, 2]
+    po, mo, vo, src, kind = oracle.densify(p, m, v, acc, cnt, normals, thr, 0.1)
+    assert len(po) == 7 - 0 + 3 * 1 + 2 * 1 - 2 + 2          # 1 pruned, 2 kept, 3 clones (+3), 2 splits (+2)
+    assert list(src) == [1, 2, 2, 3, 3, 4, 5, 5, 6, 6, 7, 7]
+    assert list(kind) == [1, 2, 4, 3, 3, 1, 2, 4, 3, 3, 2, 4]
+    for r, (g, k) in enumerate(zip(src, kind)):
+        if k in (1, 2, 4):
+            assert np.array_equal(po[r], p[g].astype(np.float64))
+            if k == 4:
+                assert not po[r].any() or (mo[r] == 0).all() and (vo[r] == 0).all()
+            else:
+                assert np.array_equal(mo[r], m[g].astype(np.float64)) and np.array_equal(vo[r], v[g].astype(np.float64))
+        else:
+            # a child: R^T (x_child - x) / s recovers its normal draw exactly
+            q = p[g, 8:12].astype(np.float64)
+            R = np.zeros(9)
+            oracle.lib().or_quat_rot(oracle._i64(1), oracle._p(np.ascontiguousarray(q[None])), oracle._p(R))
+            s = np.exp(p[g, 4:7].astype(np.float64))
+            xi = (R.reshape(3, 3).T @ (po[r, 0:3] - p[g, 0:3])) / s
+            c = r - int(np.nonzero(src == g)[0][0])
+            assert np.allclose(xi, normals[g, c], atol=1e-12)
+            assert np.array_equal(po[r, 4:7].astype(np.float32),
+                                  (p[g, 4:7] - np.float32(math.log(1.6))).astype(np.float32))
+            assert np.array_equal(po[r, 8:60], p[g, 8:60].astype(np.float64)) and po[r, 3] == p[g, 3]
+            assert (mo[r] == 0).all() and (vo[r] == 0).all()
+
+
+def test_split_children_follow_the_gaussian(oracle):
+    """Split children drawn from standard normals lie at N(mean, R S^2 R^T):
+    over 20,000 draws the offsets' covariance matches the Gaussian's (3%)."""
+    rng = np.random.default_rng(2)
+    n = 20000
+    p = np.zeros((n, 60), np.float32)
+    p[:, 3] = 2.0
+    p[:, 4:7] = np.log([0.3, 0.1, 0.05])
+    p[:, 8:12] = [0.9, 0.3, -0.2, 0.25]
+    acc = np.ones(n, np.float32)
+    cnt = np.ones(n, np.uint32)
+    normals = rng.standard_normal((n, 2, 3))
+    po, _, _, src, kind = oracle.densify(p, p * 0, p * 0, acc, cnt, normals, 0.5, 0.01)
+    assert (kind == 3).all() and len(po) == 2 * n
+    d = po[:, 0:3]
+    C = np.cov(d.T)
+    q = p[0, 8:12].astype(np.float64)
+    R = np.zeros(9)
+    oracle.lib().or_quat_rot(oracle._i64(1), oracle._p(np.ascontiguousarray(q[None])), oracle._p(R))
+    R = R.reshape(3, 3)
+    S = np.diag(np.exp(p[0, 4:7].astype(np.float64)) ** 2)
+    ref = R @ S @ R.T
+    assert np.abs(C - ref).max() < 0.03 * np.abs(ref).max()
+
+
+def test_opacity_reset(oracle):
+    rng = np.random.default_rng(4)
+    p = rng.standard_normal((20, 60)).astype(np.float32) * 4
+    m = rng.standard_normal((20, 60)).astype(np.float32)
+    v = rng.random((20, 60)).astype(np.float32)
+    p2, m2, v2 = oracle.reset_opacity(p, m, v, 0.01)
+    o2 = 1 / (1 + np.exp(-p2[:, 3].astype(np.float64)))
+    o = 1 / (1 + np.exp(-p[:, 3].astype(np.float64)))
+    assert np.allclose(o2, np.minimum(o, 0.01), rtol=1e-6)
+    assert (m2[:, 3] == 0).all() and (v2[:, 3] == 0).all()
+    keep = np.ones(60, bool)
+    keep[3] = False
+    assert np.array_equal(p2[:, keep], p[:, keep]) and np.array_equal(m2[:, keep], m[:, keep])
+
+
+def test_densify_statistics_count_visible_views(oracle):
+    """Statistics of one step: each Gaussian's count is the number of views
+    of the batch that see it (a Gaussian behind one camera counts once), and
+    its sum is the sum of the lengths of its per-view position gradients."""
+    sc = synth.tiny_scene(30, seed=5, spread=0.5)
+    cams = [synth.test_camera(W=32, H=24), synth.camera_look_at((0.0, 0.0, 8.0), (0, 0, 3), (0, -1, 0), 32, 24, 60)]
+    sc.mo[0, 2] = 9.0                                # behind the second camera: only the first sees it
+    rng = np.random.default_rng(0)
+    tg = rng.random((2, 3, 24, 32))
+    st = dict(acc=np.zeros(30), cnt=np.zeros(30, np.int64))
+    z = np.zeros((30, 60))
+    oracle.train_step(sc, cams, tg, z, z, 1, (1e-3,) * 6, stats=st)
+    vis = np.stack([oracle.project(sc, c)["vis"] > 0 for c in cams])
+    assert np.array_equal(st["cnt"], vis.sum(0)) and vis[0, 0] and not vis[1, 0]
+    ref = np.zeros(30)
+    for b, cam in enumerate(cams):
+        fw = oracle.render(sc, cam)
+        _, dimg, _, _ = oracle.ssim_loss(fw["img"], tg[b])
+        pr = fw["proj"]
+        g2d = oracle.render_bwd(cam.W, cam.H, 16, fw["toff"], fw["gidx"], pr["xy"], pr["conic_o"], pr["rgb"], dimg)
+        ref += np.where(vis[b], np.sqrt(g2d[:, 0] ** 2 + g2d[:, 1] ** 2), 0.0)
+    assert np.allclose(st["acc"], ref, rtol=1e-9, atol=1e-15)

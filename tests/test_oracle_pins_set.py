@@ -326,3 +326,68 @@ def test_fp32_bounds_hold_for_a_float32_transformation(oracle, which):
     print({k_: float(r) for k_, r in ratios.items()})
     for name, r in ratios.items():
         assert r <= 1.0, (name, r)
+
+
+# ---------------------------------------------------------------- storage order
+
+def test_morton_code_interleaves_bits(oracle):
+    c = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [2, 0, 0], [1023, 1023, 1023], [5, 3, 6]])
+    code = oracle.morton_code(c)
+    assert list(code[:5]) == [1, 2, 4, 8, 2 ** 30 - 1]
+    # 5 = 101b, 3 = 011b, 6 = 110b: bits (x,y,z) per level 0: (1,1,0), 1: (0,1,1), 2: (1,0,1)
+    assert code[5] == (1 | 2) | ((2 | 4) << 3) | ((1 | 4) << 6)
+
+
+def test_morton_order_is_z_order_of_a_grid(oracle):
+    """A shuffled 8 x 8 x 8 lattice of spacing 8 plus one corner point at 64
+    spans a box of edge 64, so the cells are exactly 128 x the lattice
+    coordinates (the corner clamps to 1023).  The order then visits the
+    lattice in Z-order: it equals the brute-force sort of the lattice indices'
+    interleaved bits, and every aligned 2 x 2 x 2 block is contiguous."""
+    g = np.stack(np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(0)
+    g = g[rng.permutation(len(g))]
+    xyz = np.concatenate([g * 8.0, [[64.0, 64.0, 64.0]]]).astype(np.float32)
+    cells = oracle.morton_cells(xyz)
+    assert np.array_equal(cells[:-1], g * 128) and np.array_equal(cells[-1], [1023, 1023, 1023])
+    sc = synth._empty_scene(len(xyz))
+    sc.mo[:, :3] = xyz
+    order = oracle.morton_order(sc)
+    assert order[-1] == len(g)
+    brute = sorted(range(len(g)), key=lambda i: sum(((int(g[i, a]) >> b) & 1) << (3 * b + a)
+                                                    for b in range(3) for a in range(3)))
+    assert list(order[:-1]) == brute
+    blocks = g[order[:-1]] // 2
+    for k in range(0, len(g), 8):
+        assert len({tuple(r) for r in blocks[k:k + 8]}) == 1
+
+
+def test_morton_order_ties_and_nonfinite(oracle):
+    """Equal positions keep index order; non-finite positions take cell 0 and
+    do not widen the box."""
+    sc = synth._empty_scene(6)
+    sc.mo[:, :3] = [[1, 1, 1], [0, 0, 0], [1, 1, 1], [np.nan, 0, 0], [0, 0, 0], [1, 1, 1]]
+    cells = oracle.morton_cells(sc.mo[:, :3])
+    assert np.array_equal(cells[3], [0, 0, 0]) and np.array_equal(cells[0], [1023, 1023, 1023])
+    assert list(oracle.morton_order(sc)) == [1, 3, 4, 0, 2, 5]
+
+
+# ---------------------------------------------------------------- Algorithm 1
+
+def test_division_points_closed_forms(oracle):
+    """Uniform costs: with CT = 1..8 and 4 parts the thresholds are 0, 2, 4, 6
+    and the first blocks reaching them are 0, 1, 3, 5.  One heavy block takes
+    a part of its own.  Against the printed float form
+    searchsorted(CT, arange(P) * CT[-1] / P) wherever CT[-1] / P is exact."""
+    assert list(oracle.division_points([1] * 8, 4)) == [0, 1, 3, 5]
+    assert list(oracle.division_points([1, 1, 100, 1, 1], 3)) == [0, 2, 2]
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        T, P = int(rng.integers(1, 400)), int(rng.integers(1, 40))
+        c = rng.integers(0, 50, T)
+        c[-1] += P - (c.sum() % P)                 # CT[-1] divisible by P: the float form is exact
+        CT = np.cumsum(c)
+        ref = np.searchsorted(CT, np.arange(P) * (CT[-1] // P), side="left")
+        assert np.array_equal(oracle.division_points(c, P), ref)
+    d = oracle.division_points(rng.integers(0, 9, 1000), 37)
+    assert d[0] == 0 and np.all(np.diff(d) >= 0) and d[-1] <= 1000
