@@ -31,6 +31,7 @@ from paper_2406_18533_gb300 import synth  # noqa: E402
 METRIC = "train views/s batched vs per-view at 1e-4 img err; serve p50/p99 ms"
 UNIT = "views/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+SCHEDULES = {"auto": 0, "alg1": 1, "pool": 2}      # gs_hparams.schedule
 FP32_LANES_PER_SM = 128
 
 
@@ -346,12 +347,18 @@ def run_ours(args, rank, world, local_rank):
     tuned = None
     if args.autotune:
         from paper_2406_18533_gb300 import autotune
-        best, trials = autotune.tune(P, cams, targets, lr=lr6, log=lambda m: print(m, file=sys.stderr, flush=True))
+        best, trials = autotune.tune(P, cams, targets, lr=lr6, log=lambda m: print(m, file=sys.stderr, flush=True),
+                                     schedules=autotune.SCHEDULES if args.schedule is None else ())
         args.tile, args.batch, args.ppt = best["tile"], best["smem_batch"], best["px_per_thread"]
-        tuned = {"chosen": best, "trials_ms": {f"t{t.tile}_b{t.smem_batch}_p{t.px_per_thread}": round(t.ms, 3)
-                                               for t in trials}}
+        if args.schedule is None:
+            args.schedule = {v: k for k, v in SCHEDULES.items()}[best["schedule"]]
+        tuned = {"chosen": best,
+                 "trials_ms": {f"t{t.tile}_b{t.smem_batch}_p{t.px_per_thread}_s{t.schedule}": round(t.ms, 3)
+                               for t in trials}}
+    if args.schedule is None:
+        args.schedule = "auto"
     ctx = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt,
-                         sparse_adam=int(args.sparse_adam), schedule=int(args.schedule == "alg1"))
+                         sparse_adam=int(args.sparse_adam), schedule=SCHEDULES[args.schedule])
     G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
     loss = torch.empty(Bv, dtype=torch.float32, device="cuda")
     cam_arr = binding.camera_array(cams)
@@ -439,7 +446,7 @@ def run_ours(args, rank, world, local_rank):
     per_view = None
     if Bv > 1 and not args.no_per_view:
         ctx1 = engine.Context(lr=lr6, tile=args.tile, smem_batch=args.batch, px_per_thread=args.ppt,
-                              sparse_adam=int(args.sparse_adam), schedule=int(args.schedule == "alg1"))
+                              sparse_adam=int(args.sparse_adam), schedule=SCHEDULES[args.schedule])
         P1 = P.clone()
         G1, M1, V1 = P1.zeros_like(), P1.zeros_like(), P1.zeros_like()
         loss1 = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -572,8 +579,11 @@ def run_ours(args, rank, world, local_rank):
                    "tile": args.tile, "smem_batch": args.batch, "px_per_thread": args.ppt, "autotune": tuned,
                    "sh_degree": 3,
                    "adam": "visible-only" if args.sparse_adam else "dense (every Gaussian, the paper's)",
-                   "schedule": ("Algorithm 1 ranges over the previous step's measured tile costs, persistent CTAs"
-                                if args.schedule == "alg1" else "one CTA per tile (longest lists first where it pays)"),
+                   "schedule": {"alg1": "Algorithm 1 ranges over the previous step's measured tile costs, "
+                                        "persistent CTAs",
+                                "pool": "persistent CTAs pulling tiles from a device queue, heaviest measured "
+                                        "cost of the previous step first",
+                                "auto": "one CTA per tile (longest lists first where it pays)"}[args.schedule],
                    "storage_order": ("Morton order of the positions (gs_spatial_order + gs_permute once at load)"
                                      if args.storage_order == "morton" else "as generated"),
                    "l2": "no flush: params + grad + Adam moments resident in HBM exceed the 129 MB L2",
@@ -703,8 +713,10 @@ def main():
     ap.add_argument("--views", type=int, default=0, help="use only the first K views of the workload (profiling)")
     ap.add_argument("--storage-order", default="morton", choices=["morton", "given"],
                     help="store the Gaussians in Morton order of their positions at load (default) or as generated")
-    ap.add_argument("--schedule", default="auto", choices=["auto", "alg1"],
-                    help="blending schedule: one CTA per tile (auto) or Algorithm 1 ranges of measured cost")
+    ap.add_argument("--schedule", default=None, choices=sorted(SCHEDULES),
+                    help="blending schedule: one CTA per tile (auto), Algorithm 1 ranges of measured cost "
+                         "(alg1) or a persistent pool in measured-cost order (pool); by default the autotuner "
+                         "picks it where it runs, else auto")
     ap.add_argument("--sparse-adam", action="store_true",
                     help="visible-only Adam (Gaussians no view of the batch sees keep p, m, v)")
     args = ap.parse_args()

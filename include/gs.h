@@ -106,7 +106,9 @@ typedef struct gs_hparams {
                                  longest lists first where that pays; 1 Algorithm 1: the tiles are
                                  split into contiguous ranges of equal cost, measured per tile in
                                  the previous step (list lengths before the first), one range per
-                                 resident persistent CTA (see gs_division_points) */
+                                 resident persistent CTA (see gs_division_points); 2 a persistent
+                                 pool: one CTA per resident slot pulls tiles from a device queue
+                                 counter, heaviest cost of the previous step first */
 } gs_hparams;
 
 /*

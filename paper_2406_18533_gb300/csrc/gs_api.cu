@@ -51,6 +51,7 @@ struct gs_ctx {
     DBuf dens_cnt, dens_off;       // gs_densify: output counts and their offsets
     DBuf tile_cost, tile_excl;     // Algorithm 1 schedule: measured cost per tile, its prefix sums
     DBuf div_f, div_b, div_tot;    // division points of the forward / backward ranges, a total
+    DBuf pool_q;                   // persistent pool schedule: queue counters (forward, backward)
     uint32_t cost_tiles = 0;       // tiles the cost buffer describes (0: nothing measured yet)
     float *dacc = nullptr;         // densification statistics (caller-owned), see gs_set_densify_stats
     uint32_t *dcnt = nullptr;
@@ -320,7 +321,7 @@ gs_status ensure_iter(gs_ctx *c, int64_t N, const ViewBatch &vb, uint64_t cap)
         (r = ensure(c, c->tile_order, 4 * ((size_t)vb.total_tiles + 64))))
         return r;
     if ((r = ensure(c, c->T_final, 4 * pix)) || (r = ensure(c, c->n_contrib, 4 * pix))) return r;
-    if (c->hp.schedule == 1) {
+    if (c->hp.schedule == 1 || c->hp.schedule == 2) {
         const size_t T = (size_t)vb.total_tiles + 1;
         const size_t P = (size_t)blend_resident_ctas(c->hp.tile, c->hp.smem_batch, c->hp.px_per_thread, true) +
                          blend_resident_ctas(c->hp.tile, c->hp.smem_batch, c->hp.px_per_thread, false) + 1;
@@ -329,6 +330,7 @@ gs_status ensure_iter(gs_ctx *c, int64_t N, const ViewBatch &vb, uint64_t cap)
         if (c->tile_cost.p != had) c->cost_tiles = 0;   // a new buffer holds no measurements
         if ((r = ensure(c, c->tile_excl, 4 * T)) ||
             (r = ensure(c, c->div_f, 4 * P)) || (r = ensure(c, c->div_b, 4 * P)) || (r = ensure(c, c->div_tot, 64)) ||
+            (r = ensure(c, c->pool_q, 64)) ||
             (r = ensure(c, c->scan_tmp, scan_temp_bytes((int64_t)T))))
             return r;
     }
@@ -405,7 +407,7 @@ gs_status check_hparams(gs_ctx *c, const gs_hparams *hp)
     if (hp->px_per_thread != 1 && hp->px_per_thread != 2 && hp->px_per_thread != 4)
         return fail(c, GS_ERR_INVALID_ARG, "px_per_thread must be 1, 2 or 4");
     if (hp->sparse_adam != 0 && hp->sparse_adam != 1) return fail(c, GS_ERR_INVALID_ARG, "sparse_adam must be 0 or 1");
-    if (hp->schedule != 0 && hp->schedule != 1) return fail(c, GS_ERR_INVALID_ARG, "schedule must be 0 or 1");
+    if (hp->schedule < 0 || hp->schedule > 2) return fail(c, GS_ERR_INVALID_ARG, "schedule must be 0, 1 or 2");
     if (!blend_config_ok(hp->tile, hp->smem_batch, hp->px_per_thread))
         return fail(c, GS_ERR_INVALID_ARG,
                     "unsupported (tile, smem_batch, px_per_thread): smem_batch 32, 64 or 128 (32 or 64 with tile 32 "
@@ -533,7 +535,7 @@ gs_status gs_destroy(gs_ctx *c)
                     &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_proj, &c->keys,
                     &c->vals, &c->ranges, &c->count, &c->img, &c->dimg, &c->T_final, &c->n_contrib, &c->maps,
                     &c->acc, &c->tile_order, &c->vis, &c->order_tmp, &c->dens_cnt, &c->dens_off,
-                    &c->tile_cost, &c->tile_excl, &c->div_f, &c->div_b, &c->div_tot};
+                    &c->tile_cost, &c->tile_excl, &c->div_f, &c->div_b, &c->div_tot, &c->pool_q};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     trace_free(c);
@@ -919,7 +921,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
     const BlendParams bp = blend_of(c->hp);
     const uint32_t *order = nullptr, *div_f = nullptr, *div_b = nullptr;
-    uint32_t *cost = nullptr;
+    uint32_t *cost = nullptr, *queue = nullptr;
     if (c->hp.schedule == 1 && vb.total_tiles > 0) {
         // Algorithm 1 over the previous step's measured tile costs (list lengths before the first)
         const uint32_t T = vb.total_tiles;
@@ -937,11 +939,25 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
         cudaMemsetAsync(cost, 0, 4 * (size_t)T, st);    // this step measures afresh
         div_f = ptr<uint32_t>(c->div_f);
         div_b = ptr<uint32_t>(c->div_b);
+    } else if (c->hp.schedule == 2 && vb.total_tiles > 0) {
+        // persistent pool over the previous step's measured costs, heaviest first
+        const uint32_t T = vb.total_tiles;
+        cost = ptr<uint32_t>(c->tile_cost);
+        if (c->cost_tiles != T) {
+            launch_list_cost(ptr<uint2>(c->ranges), T, cost, st);
+            c->cost_tiles = T;
+        }
+        order = ptr<uint32_t>(c->tile_order);
+        launch_tile_order(ptr<uint2>(c->ranges), T, ptr<uint32_t>(c->tile_order), ptr<uint32_t>(c->tile_order) + T,
+                          st, cost);
+        cudaMemsetAsync(cost, 0, 4 * (size_t)T, st);
+        queue = ptr<uint32_t>(c->pool_q);               // two counters (forward, backward), zero at launch
+        cudaMemsetAsync(queue, 0, 8, st);
     } else {
         order = tile_order_for(c, vb, ptr<uint2>(c->ranges), st);   // shared by both passes
     }
     launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
-                     c->status, order, st, div_f, cost);
+                     c->status, order, st, div_f, cost, queue);
     mark(c, st, 6);
     launch_loss(ptr<float>(c->img), targets, B, vb.v[0].W, vb.v[0].H, c->hp.lambda_dssim, loss_out,
                 ptr<float>(c->dimg), ptr<float>(c->maps), ptr<double>(c->acc), c->status, st);
@@ -952,7 +968,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     float4 *gp = ptr<float4>(c->g_proj);
     const GradView gv{gp, gp + n, gp + 2 * n};
     launch_blend_bwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), bp, c->hp.smem_batch, c->hp.px_per_thread,
-                     gv, c->status, order, st, div_b, cost);
+                     gv, c->status, order, st, div_b, cost, queue ? queue + 1 : nullptr);
     mark(c, st, 9);
     uint8_t *vis = c->hp.sparse_adam ? ptr<uint8_t>(c->vis) : nullptr;
     const bool stats = c->dacc && c->dN == N;

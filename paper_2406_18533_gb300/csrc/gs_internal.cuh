@@ -288,14 +288,17 @@ void launch_compose_keys(const ViewBatch &vb, int64_t N, const uint32_t *tiles, 
 bool blend_config_ok(int tile, int chunk, int ppt);
 // div (optional): Algorithm 1's range starts for blend_resident_ctas(...)
 // persistent CTAs (launch_division_points), used instead of one CTA per
-// tile; cost (optional): each tile's measured cost is added there.
+// tile; queue (optional, wins over div): a zeroed counter from which
+// persistent CTAs, one per resident slot, pull the tiles of `order` (null:
+// index order); cost (optional): each tile's measured cost is added there.
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                       const BlendParams &bp, int chunk, int ppt, DevStatus *status, const uint32_t *order,
-                      cudaStream_t st, const uint32_t *div = nullptr, uint32_t *cost = nullptr);
+                      cudaStream_t st, const uint32_t *div = nullptr, uint32_t *cost = nullptr,
+                      uint32_t *queue = nullptr);
 void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                       const BlendParams &bp, int chunk, int ppt, const GradView &g, DevStatus *status,
                       const uint32_t *order, cudaStream_t st, const uint32_t *div = nullptr,
-                      uint32_t *cost = nullptr);
+                      uint32_t *cost = nullptr, uint32_t *queue = nullptr);
 uint32_t blend_resident_ctas(int tile, int chunk, int ppt, bool bwd);
 int sm_count();
 // Algorithm 1 over T tile costs for P ranges: div[k] = the first tile of
@@ -307,9 +310,11 @@ void launch_division_points(uint32_t *cost, uint32_t T, uint32_t P, uint32_t *ex
 void launch_list_cost(const uint2 *ranges, uint32_t T, uint32_t *cost, cudaStream_t st);
 // Tile launch order for the blending kernels (order: launch slot -> tile;
 // null = index order): heaviest list first, worth it only for a few waves of
-// CTAs (tile_order_pays).  buckets: 64 words of scratch.
+// CTAs (tile_order_pays).  With cost, heaviest measured cost first instead.
+// buckets: 64 words of scratch.
 bool tile_order_pays(uint32_t total_tiles);
-void launch_tile_order(const uint2 *ranges, uint32_t n, uint32_t *order, uint32_t *buckets, cudaStream_t st);
+void launch_tile_order(const uint2 *ranges, uint32_t n, uint32_t *order, uint32_t *buckets, cudaStream_t st,
+                       const uint32_t *cost = nullptr);
 
 // status: a staging wait that runs out records GS_ERR_TIMEOUT there.
 void launch_loss(const float *img, const float *target, int B, int W, int H, float lambda, float *loss_out,

@@ -20,8 +20,9 @@
 // recovers the transmittance before each contributor by division from
 // T_final (no per-fragment state is stored), accumulates per Gaussian the
 // moments of dpow = alpha dL/dalpha (M, Mx, My, Mxx, Mxy, Myy; the mean,
-// conic and opacity gradients are linear in them) and the colour gradient,
-// and adds these nine values to the Gaussian as three float4 atomics: from
+// conic and opacity gradients are linear in them; a lane's pixels share one
+// column, so it sums only M, My, Myy and scales by dx once per entry) and the
+// colour gradient, and adds these nine values to the Gaussian as three float4 atomics: from
 // each contributing lane directly when few lanes contribute, after a
 // reduce-scatter over the warp (17 shuffles) or a fold of the upper half-warp
 // when many do (add_sums, flush_one).  The moments become gradients once per
@@ -381,6 +382,33 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd_ranges(ViewBatch
     for (uint32_t t = lo; t < hi; ++t) blend_fwd_tile<TILE, CH, PPT>(t, vb, p, vals, ranges, bp, status, cost);
 }
 
+// Next position of a persistent CTA's work queue: thread 0 takes it from
+// the global counter, every thread reads it, and no thread leaves the read
+// before thread 0 may overwrite the slot for the next tile.
+__device__ __forceinline__ uint32_t pool_next(uint32_t *queue)
+{
+    __shared__ uint32_t s_next;
+    if (threadIdx.x == 0) s_next = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t t = s_next;
+    __syncthreads();
+    return t;
+}
+
+// Persistent pool: a CTA per resident slot pulls the next tile of `order`
+// (the previous step's measured costs, heaviest first; null: index order)
+// from the queue counter until every tile is taken.
+template <int TILE, int CH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd_pool(ViewBatch vb, ProjView p,
+                                                                     const uint32_t *vals, const uint2 *ranges,
+                                                                     BlendParams bp, DevStatus *status,
+                                                                     const uint32_t *order, uint32_t *queue,
+                                                                     uint32_t *cost)
+{
+    for (uint32_t t = pool_next(queue); t < vb.total_tiles; t = pool_next(queue))
+        blend_fwd_tile<TILE, CH, PPT>(order ? order[t] : t, vb, p, vals, ranges, bp, status, cost);
+}
+
 // With 2 pixels per thread the backward is held to 64 registers (8 CTAs of
 // 128 threads per SM; 4 bytes of spill): 1% faster on GB300 than at 68
 // registers and 7 CTAs.  Other shapes keep the compiler's choice.
@@ -405,16 +433,18 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
     const uint32_t lt = (1u << lane) - 1u;
     const int64_t hw = (int64_t)c.W * c.H;
 
-    float T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], B0[PPT], B1[PPT], B2[PPT];
+    // Per pixel: T, dL/dC, and S = B . dL/dC, where B is the colour behind
+    // the current entry (normalised by the transmittance in front of it).
+    // dL/dalpha_i = T_i (c_i - B_i) . dL/dC = T_i (c_i . dL/dC - S_i), and
+    // B_{i-1} = alpha_i c_i + (1 - alpha_i) B_i, so S obeys the same
+    // recursion: one scalar instead of the three channels of B.
+    float T[PPT], dC0[PPT], dC1[PPT], dC2[PPT], S[PPT];
     uint32_t nc[PPT], wnc = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         T[k] = 1.f;
         dC0[k] = dC1[k] = dC2[k] = 0.f;
         nc[k] = 0u;
-        B0[k] = bp.bg[0];                            // colour behind (normalised)
-        B1[k] = bp.bg[1];
-        B2[k] = bp.bg[2];
         if (ps.inside[k]) {
             const int64_t pix = (int64_t)ps.py[k] * c.W + ps.px;
             T[k] = c.T_final[pix];
@@ -423,6 +453,7 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
             dC1[k] = c.d_img[hw + pix];
             dC2[k] = c.d_img[2 * hw + pix];
         }
+        S[k] = bp.bg[0] * dC0[k] + bp.bg[1] * dC1[k] + bp.bg[2] * dC2[k];
         wnc = max(wnc, nc[k]);
     }
     // this warp walks back to front from its own largest n_contrib, never past the list
@@ -461,10 +492,11 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
             const float4 q = s_q[i];
             const float dx = __fsub_rn(ps.fx, xyc.x);
             const DxTerms dt = dx_terms(q, dx);
-            // this lane's sums over its pixels (GradView): M, Mx, My, Mxx, Mxy,
-            // Myy, r, g in vv, b in gbl
-            float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float gbl = 0.f;
+            // this lane's sums over its pixels: M = sum dpow, My = sum dpow dy,
+            // Myy = sum dpow dy^2 (the lane's pixels share one column, so the
+            // dx moments follow from these: Mx = dx M, Mxx = dx^2 M, Mxy =
+            // dx My) and the colour sums r, g, b
+            float M = 0.f, My = 0.f, Myy = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
             bool any = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -482,24 +514,18 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
                 const float4 rgb = s_rgb[i];
                 const float Tj = __fdividef(T[k], 1.f - alpha);
                 const float w = alpha * Tj;
-                vv[6] += w * dC0[k];
-                vv[7] += w * dC1[k];
-                gbl += w * dC2[k];
-                const float e0 = rgb.x - B0[k], e1 = rgb.y - B1[k], e2 = rgb.z - B2[k];
-                const float dalpha = Tj * (e0 * dC0[k] + e1 * dC1[k] + e2 * dC2[k]);
-                B0[k] += alpha * e0;
-                B1[k] += alpha * e1;
-                B2[k] += alpha * e2;
+                cr = fmaf(w, dC0[k], cr);
+                cg = fmaf(w, dC1[k], cg);
+                cb = fmaf(w, dC2[k], cb);
+                const float e = fmaf(rgb.x, dC0[k], fmaf(rgb.y, dC1[k], fmaf(rgb.z, dC2[k], -S[k])));
+                S[k] = fmaf(alpha, e, S[k]);
                 T[k] = Tj;
                 if (oG < bp.alpha_max) {                // alpha not clamped: geometry and opacity terms
-                    const float dpow = alpha * dalpha;
-                    const float dpx = dpow * dx, dpy = dpow * dy;
-                    vv[0] += dpow;
-                    vv[1] += dpx;
-                    vv[2] += dpy;
-                    vv[3] = fmaf(dpx, dx, vv[3]);
-                    vv[4] = fmaf(dpx, dy, vv[4]);
-                    vv[5] = fmaf(dpy, dy, vv[5]);
+                    const float dpow = w * e;           // alpha dL/dalpha
+                    const float dpy = dpow * dy;
+                    M += dpow;
+                    My += dpy;
+                    Myy = fmaf(dpy, dy, Myy);
                 }
             }
             const uint32_t ballot = __ballot_sync(0xffffffffu, any);
@@ -507,22 +533,31 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
             const int64_t idx = vbase + __float_as_uint(s_rgb[i].w);
             const int contributing = __popc(ballot);
             if constexpr (PPT == 4) {
-                // fold the upper half-warp onto the lower one when it pays,
-                // then every contributing lane adds its own sums
+                // fold the upper half-warp onto the lower one when it pays
+                // (lanes l and l + 16 share a column, so the compact sums
+                // add), then every contributing lane adds its own sums
                 if (contributing > FOLD_ABOVE) {
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) vv[m] += __shfl_down_sync(0xffffffffu, vv[m], 16);
-                    gbl += __shfl_down_sync(0xffffffffu, gbl, 16);
+                    M += __shfl_down_sync(0xffffffffu, M, 16);
+                    My += __shfl_down_sync(0xffffffffu, My, 16);
+                    Myy += __shfl_down_sync(0xffffffffu, Myy, 16);
+                    cr += __shfl_down_sync(0xffffffffu, cr, 16);
+                    cg += __shfl_down_sync(0xffffffffu, cg, 16);
+                    cb += __shfl_down_sync(0xffffffffu, cb, 16);
                     any = lane < 16 && ((ballot >> lane) & 0x10001u) != 0u;
                 }
-                if (any) add_sums(gv, idx, vv, gbl);
+                if (any) {
+                    const float Mx = dx * M;
+                    const float vv[8] = {M, Mx, My, dx * Mx, dx * My, Myy, cr, cg};
+                    add_sums(gv, idx, vv, cb);
+                }
             } else {
+                const float Mx = dx * M;
+                const float vv[9] = {M, Mx, My, dx * Mx, dx * My, Myy, cr, cg, cb};
                 if (contributing <= DIRECT_UP_TO) {
-                    if (any) add_sums(gv, idx, vv, gbl);
+                    if (any) add_sums(gv, idx, vv, cb);
                     continue;
                 }
-                const float cur[9] = {vv[0], vv[1], vv[2], vv[3], vv[4], vv[5], vv[6], vv[7], gbl};
-                flush_one(gv, idx, cur, lane);
+                flush_one(gv, idx, vv, lane);
             }
         }
         n = 0;
@@ -562,6 +597,15 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1))
     for (uint32_t t = lo; t < hi; ++t) blend_bwd_tile<TILE, CH, PPT>(t, vb, p, vals, ranges, bp, gv, status, cost);
 }
 
+template <int TILE, int CH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1))
+    k_blend_bwd_pool(ViewBatch vb, ProjView p, const uint32_t *vals, const uint2 *ranges, BlendParams bp,
+                     GradView gv, DevStatus *status, const uint32_t *order, uint32_t *queue, uint32_t *cost)
+{
+    for (uint32_t t = pool_next(queue); t < vb.total_tiles; t = pool_next(queue))
+        blend_bwd_tile<TILE, CH, PPT>(order ? order[t] : t, vb, p, vals, ranges, bp, gv, status, cost);
+}
+
 // Launch order of the tiles, heaviest list first.  With few waves of CTAs
 // per launch the kernel ends when its slowest tiles do, and in index order the
 // long lists of a dense region can start last.  A counting sort on
@@ -569,19 +613,28 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1))
 // class the order is that of the atomic scatter (results do not depend on the
 // launch order: tiles are independent).  buckets: 64 words, [0, 32) counts
 // of each class, [32, 64) their write cursors.
-__device__ __forceinline__ uint32_t length_class(uint2 r)
+// With `cost` (the measured cost of each tile) the classes are
+// floor(log2(cost)) instead.
+__device__ __forceinline__ uint32_t length_class(const uint2 *ranges, const uint32_t *cost, uint32_t t)
 {
-    const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+    uint32_t len;
+    if (cost) {
+        len = cost[t];
+    } else {
+        const uint2 r = ranges[t];
+        len = r.y > r.x ? r.y - r.x : 0u;
+    }
     return len ? (uint32_t)__clz(len) : 31u;   // 31 - floor(log2 len): the longest lists in class 0
 }
 
-__global__ void __launch_bounds__(256) k_order_count(const uint2 *ranges, uint32_t n, uint32_t *buckets)
+__global__ void __launch_bounds__(256) k_order_count(const uint2 *ranges, const uint32_t *cost, uint32_t n,
+                                                     uint32_t *buckets)
 {
     __shared__ uint32_t h[32];
     if (threadIdx.x < 32) h[threadIdx.x] = 0u;
     __syncthreads();
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
-        atomicAdd(&h[length_class(ranges[t])], 1u);
+        atomicAdd(&h[length_class(ranges, cost, t)], 1u);
     __syncthreads();
     if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&buckets[threadIdx.x], h[threadIdx.x]);
 }
@@ -599,11 +652,11 @@ __global__ void k_order_offsets(uint32_t *buckets)
     buckets[32 + lane] = incl - c;
 }
 
-__global__ void __launch_bounds__(256) k_order_scatter(const uint2 *ranges, uint32_t n, uint32_t *buckets,
-                                                       uint32_t *order)
+__global__ void __launch_bounds__(256) k_order_scatter(const uint2 *ranges, const uint32_t *cost, uint32_t n,
+                                                       uint32_t *buckets, uint32_t *order)
 {
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const uint32_t pos = atomicAdd(&buckets[32 + length_class(ranges[t])], 1u);
+        const uint32_t pos = atomicAdd(&buckets[32 + length_class(ranges, cost, t)], 1u);
         if (pos < n) order[pos] = t;           // the counts add up to n: always true
     }
 }
@@ -617,13 +670,16 @@ bool smem_opt_in(K kernel, size_t bytes)
 }
 
 // Schedule of a blending launch: one CTA per tile in `order` (null: index
-// order), or, with div, Algorithm 1's ranges for `ctas` persistent CTAs; cost
-// (optional) receives each tile's measured cost.
+// order); with div, Algorithm 1's ranges for `ctas` persistent CTAs; with
+// queue, `ctas` persistent CTAs pulling tiles of `order` from the queue
+// counter (zero at launch).  cost (optional) receives each tile's measured
+// cost.
 struct Sched {
     const uint32_t *order;
     const uint32_t *div;
     uint32_t ctas;
     uint32_t *cost;
+    uint32_t *queue;
 };
 
 template <int TILE, int CH, int PPT>
@@ -631,9 +687,14 @@ void fwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, co
                 const BlendParams &bp, DevStatus *status, const Sched &sc, cudaStream_t st)
 {
     constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
-    static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH, PPT>, sm) && smem_opt_in(k_blend_fwd_ranges<TILE, CH, PPT>, sm);
+    static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH, PPT>, sm) &&
+                           smem_opt_in(k_blend_fwd_ranges<TILE, CH, PPT>, sm) &&
+                           smem_opt_in(k_blend_fwd_pool<TILE, CH, PPT>, sm);
     (void)ok;
-    if (sc.div)
+    if (sc.queue)
+        k_blend_fwd_pool<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
+                                                                              sc.order, sc.queue, sc.cost);
+    else if (sc.div)
         k_blend_fwd_ranges<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
                                                                                 sc.div, sc.cost);
     else
@@ -646,9 +707,14 @@ void bwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, co
                 const BlendParams &bp, const GradView &g, DevStatus *status, const Sched &sc, cudaStream_t st)
 {
     constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
-    static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH, PPT>, sm) && smem_opt_in(k_blend_bwd_ranges<TILE, CH, PPT>, sm);
+    static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH, PPT>, sm) &&
+                           smem_opt_in(k_blend_bwd_ranges<TILE, CH, PPT>, sm) &&
+                           smem_opt_in(k_blend_bwd_pool<TILE, CH, PPT>, sm);
     (void)ok;
-    if (sc.div)
+    if (sc.queue)
+        k_blend_bwd_pool<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status,
+                                                                              sc.order, sc.queue, sc.cost);
+    else if (sc.div)
         k_blend_bwd_ranges<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status,
                                                                                 sc.div, sc.cost);
     else
@@ -656,24 +722,30 @@ void bwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, co
                                                                                  sc.order, sc.cost);
 }
 
-// Resident CTAs of the range kernel on the whole device.
-template <int TILE, int CH, int PPT, bool BWD>
+template <class K>
+cudaError_t occupancy(int *per_sm, K kernel, int threads, size_t sm)
+{
+    smem_opt_in(kernel, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, threads, sm);
+}
+
+// Resident CTAs of the range kernel (POOL: of the pool kernel) on the whole
+// device.
+template <int TILE, int CH, int PPT, bool BWD, bool POOL = false>
 uint32_t resident_ctas()
 {
     static uint32_t n = 0;
     if (!n) {
         constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
+        constexpr int threads = TILE * TILE / PPT;
         int per_sm = 0;
         cudaError_t e;
-        if (BWD) {
-            smem_opt_in(k_blend_bwd_ranges<TILE, CH, PPT>, sm);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_bwd_ranges<TILE, CH, PPT>,
-                                                              TILE * TILE / PPT, sm);
-        } else {
-            smem_opt_in(k_blend_fwd_ranges<TILE, CH, PPT>, sm);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_fwd_ranges<TILE, CH, PPT>,
-                                                              TILE * TILE / PPT, sm);
-        }
+        if (BWD)
+            e = POOL ? occupancy(&per_sm, k_blend_bwd_pool<TILE, CH, PPT>, threads, sm)
+                     : occupancy(&per_sm, k_blend_bwd_ranges<TILE, CH, PPT>, threads, sm);
+        else
+            e = POOL ? occupancy(&per_sm, k_blend_fwd_pool<TILE, CH, PPT>, threads, sm)
+                     : occupancy(&per_sm, k_blend_fwd_ranges<TILE, CH, PPT>, threads, sm);
         if (e != cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;
@@ -748,34 +820,36 @@ bool blend_config_ok(int tile, int chunk, int ppt)
 
 void launch_blend_fwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                       const BlendParams &bp, int chunk, int ppt, DevStatus *status, const uint32_t *order,
-                      cudaStream_t st, const uint32_t *div, uint32_t *cost)
+                      cudaStream_t st, const uint32_t *div, uint32_t *cost, uint32_t *queue)
 {
     if (vb.total_tiles == 0) return;
-    Sched sc{order, div, 0u, cost};
+    Sched sc{order, queue ? nullptr : div, 0u, cost, queue};
     switch (vb.tile * 10000 + chunk * 10 + ppt) {
 #define GS_FWD_CASE(T, C, P) \
-    case T * 10000 + C * 10 + P: sc.ctas = div ? resident_ctas<T, C, P, false>() : 0u; \
+    case T * 10000 + C * 10 + P: \
+        sc.ctas = queue ? resident_ctas<T, C, P, false, true>() : div ? resident_ctas<T, C, P, false>() : 0u; \
         fwd_launch<T, C, P>(vb, p, vals, ranges, bp, status, sc, st); break;
         GS_BLEND_CASES(GS_FWD_CASE)
 #undef GS_FWD_CASE
-    default: sc.div = nullptr; fwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, status, sc, st); break;
+    default: sc.div = nullptr; sc.queue = nullptr; fwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, status, sc, st); break;
     }
     count_launches(1);
 }
 
 void launch_blend_bwd(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                       const BlendParams &bp, int chunk, int ppt, const GradView &g, DevStatus *status,
-                      const uint32_t *order, cudaStream_t st, const uint32_t *div, uint32_t *cost)
+                      const uint32_t *order, cudaStream_t st, const uint32_t *div, uint32_t *cost, uint32_t *queue)
 {
     if (vb.total_tiles == 0) return;
-    Sched sc{order, div, 0u, cost};
+    Sched sc{order, queue ? nullptr : div, 0u, cost, queue};
     switch (vb.tile * 10000 + chunk * 10 + ppt) {
 #define GS_BWD_CASE(T, C, P) \
-    case T * 10000 + C * 10 + P: sc.ctas = div ? resident_ctas<T, C, P, true>() : 0u; \
+    case T * 10000 + C * 10 + P: \
+        sc.ctas = queue ? resident_ctas<T, C, P, true, true>() : div ? resident_ctas<T, C, P, true>() : 0u; \
         bwd_launch<T, C, P>(vb, p, vals, ranges, bp, g, status, sc, st); break;
         GS_BLEND_CASES(GS_BWD_CASE)
 #undef GS_BWD_CASE
-    default: sc.div = nullptr; bwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, g, status, sc, st); break;
+    default: sc.div = nullptr; sc.queue = nullptr; bwd_launch<16, 64, 1>(vb, p, vals, ranges, bp, g, status, sc, st); break;
     }
     count_launches(1);
 }
@@ -832,15 +906,16 @@ bool tile_order_pays(uint32_t total_tiles)
     return total_tiles >= 4u * sms && total_tiles <= 112u * sms;
 }
 
-void launch_tile_order(const uint2 *ranges, uint32_t n, uint32_t *order, uint32_t *buckets, cudaStream_t st)
+void launch_tile_order(const uint2 *ranges, uint32_t n, uint32_t *order, uint32_t *buckets, cudaStream_t st,
+                       const uint32_t *cost)
 {
     if (n == 0) return;
     const unsigned blocks = (unsigned)((n + 255) / 256 < 2u * (uint32_t)sm_count() ? (n + 255) / 256
                                                                                    : 2u * (uint32_t)sm_count());
     cudaMemsetAsync(buckets, 0, 32 * sizeof(uint32_t), st);
-    k_order_count<<<blocks, 256, 0, st>>>(ranges, n, buckets);
+    k_order_count<<<blocks, 256, 0, st>>>(ranges, cost, n, buckets);
     k_order_offsets<<<1, 32, 0, st>>>(buckets);
-    k_order_scatter<<<blocks, 256, 0, st>>>(ranges, n, buckets, order);
+    k_order_scatter<<<blocks, 256, 0, st>>>(ranges, cost, n, buckets, order);
     count_launches(3);
 }
 
