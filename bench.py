@@ -310,6 +310,8 @@ def stage_roofline(stage, ms, counters, N, Bv, pixels, passes, peaks, clock_mhz,
     elif stage == "order":
         # depth keys (16 B/pair), histogram + 4 pair-sort passes (68), count gather (12), scan (12)
         byt = Bv * N * 108.0
+    elif stage == "zero_grad":
+        byt = Bv * N * 48.0                  # three float4 gradient planes per (view, Gaussian)
     else:
         byt = Bv * N * 8.0
     return dict(bound="hbm", achieved=byt / sec / 1e9, peak=hbm, unit="GB/s", work_desc=f"{byt:.3e} bytes")

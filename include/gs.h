@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 3
+#define GS_ABI_VERSION 4
 #define GS_MAX_VIEWS 32   /* views per call (training batch or render batch) */
 #define GS_MAX_FRAGMENTS 1073741823ull  /* 2^30 - 1: largest fragment capacity of one call */
 
@@ -162,9 +162,32 @@ int32_t gs_abi_version(void);
  * call allocates (needed before stream capture into a CUDA graph). */
 gs_status gs_reserve(gs_ctx *ctx, int64_t N, const gs_camera *cams, int32_t B, uint64_t frag_capacity);
 
-/* Bytes of scratch gs_train_step would hold for these sizes. */
+/* Bytes of workspace that gs_reserve with these arguments takes from a fresh
+ * caller workspace (gs_set_workspace): the scratch of gs_train_step and
+ * gs_render for these sizes.  Computed on the host (a dry run of gs_reserve
+ * that only adds up the buffers), so it is exact for that call sequence. */
 gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *cams, int32_t B,
                             uint64_t frag_capacity, size_t *bytes);
+
+/* Caller workspace.  After this call the context takes all its scratch from
+ * [ws, ws + bytes) (device memory the caller allocated and owns, 256-byte
+ * aligned) instead of cudaMalloc: buffers are carved in order and never
+ * freed by the library; a buffer that has to grow takes a new region, so
+ * size the workspace with gs_workspace_size and call gs_reserve once with
+ * the same arguments.  A call whose scratch no longer fits returns
+ * GS_ERR_OOM (gs_last_error says how many bytes were missing) and launches
+ * nothing.  The call synchronises `stream` and drops every buffer the
+ * context held (their contents are lost); ws = NULL returns the context to
+ * cudaMalloc.  The workspace must outlive its use by the context. */
+gs_status gs_set_workspace(gs_ctx *ctx, void *ws, size_t bytes, void *stream);
+
+/* The context's device-side Adam step counter (the number of updates made by
+ * calls with step == 0 since creation, or since gs_set_step), for
+ * checkpoint and resume.  Both synchronise `stream` and must not be called
+ * while it is being captured.  gs_set_step: step >= 0, else
+ * GS_ERR_INVALID_ARG; the next step == 0 update then uses step + 1. */
+gs_status gs_get_step(gs_ctx *ctx, int64_t *step, void *stream);
+gs_status gs_set_step(gs_ctx *ctx, int64_t step, void *stream);
 
 /* Synchronise `stream`, then read and clear the device status word.
  * *status gets GS_OK or the first device-side error; *needed (optional) the

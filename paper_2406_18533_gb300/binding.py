@@ -76,6 +76,9 @@ SIGNATURES = {
     "gs_abi_version": [],
     "gs_reserve": [_vp, _i64, P(gs_camera), _i32, ctypes.c_uint64],
     "gs_workspace_size": [P(gs_hparams), _i64, P(gs_camera), _i32, ctypes.c_uint64, P(ctypes.c_size_t)],
+    "gs_set_workspace": [_vp, _vp, ctypes.c_size_t, _vp],
+    "gs_get_step": [_vp, P(_i64), _vp],
+    "gs_set_step": [_vp, _i64, _vp],
     "gs_get_status": [_vp, _vp, P(_i32), P(ctypes.c_uint64)],
     "gs_get_counters": [_vp, _vp, P(ctypes.c_uint64)],
     "gs_preprocess": [_vp, P(gs_scene), P(gs_camera), _i32, P(gs_proj), _vp],

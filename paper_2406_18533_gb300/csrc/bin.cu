@@ -585,8 +585,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_digit_offsets(uint32_t *ghist)
 
 // Ranking: warp w owns the RS_WARP_KEYS consecutive keys t0 + w*RS_WARP_KEYS
 // + [0, RS_WARP_KEYS), item i of lane l being key t0 + w*RS_WARP_KEYS + 32 i
-// + l.  Items are ranked in order with __match_any_sync against per-warp
-// running digit counts, so ranks are stable within the warp; per-digit
+// + l.  Items are ranked in order against per-warp running digit counts
+// (the lanes sharing a digit found with one ballot per digit bit), so ranks
+// are stable within the warp; per-digit
 // prefixes over the warps and over the digits then give every key its
 // position in the tile's output order.
 template <int RB>
@@ -625,7 +626,14 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_onesweep(const uint32_t *kin,
     for (int i = 0; i < RS_ITEMS; ++i) {
         const bool valid = wb + 32 * i + lane < n;
         const uint32_t d = valid ? ((key[i] >> shift) & (uint32_t)(NB - 1)) : (uint32_t)NB;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // the valid lanes holding the same digit: one ballot per digit bit
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t m = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? m : ~m;
+        }
         const uint32_t base = valid ? mycnt[d] : 0u;
         pos[i] = base + __popc(peers & lt);
         __syncwarp();
@@ -1064,10 +1072,14 @@ void launch_compose_keys(const ViewBatch &vb, int64_t N, const uint32_t *tiles, 
     count_launches(1);
 }
 
+// Three arrays of n words, each starting on a 256-byte boundary, then 256
+// bytes of counters and the sort's scratch.
+static uint64_t spatial_stride(uint64_t n) { return (n + 63) / 64 * 64; }
+
 size_t spatial_order_temp_bytes(int64_t N)
 {
     const uint64_t n = (uint64_t)(N > 0 ? N : 1);
-    return 3 * 4 * n + 256 + sort_temp_bytes(n, 0);
+    return 3 * 4 * spatial_stride(n) + 256 + sort_temp_bytes(n, 0);
 }
 
 void launch_spatial_order(const float4 *mo, int64_t N, uint32_t *perm, void *temp, DevStatus *status,
@@ -1076,10 +1088,11 @@ void launch_spatial_order(const float4 *mo, int64_t N, uint32_t *perm, void *tem
     if (N <= 0) return;
     const uint64_t n = (uint64_t)N;
     char *t = reinterpret_cast<char *>(temp);
+    const uint64_t sn = spatial_stride(n);
     uint32_t *keys = reinterpret_cast<uint32_t *>(t);
-    uint32_t *keys_alt = keys + n, *vals_alt = keys + 2 * n;
-    uint32_t *bb = reinterpret_cast<uint32_t *>(t + 12 * n);
-    void *sort_tmp = t + 12 * n + 256;
+    uint32_t *keys_alt = keys + sn, *vals_alt = keys + 2 * sn;
+    uint32_t *bb = reinterpret_cast<uint32_t *>(t + 12 * sn);
+    void *sort_tmp = t + 12 * sn + 256;
     k_bbox_init<<<1, 32, 0, st>>>(bb, (uint32_t)n);
     k_bbox<<<stride_blocks(n), 256, 0, st>>>(mo, N, bb);
     k_morton<<<stride_blocks(n), 256, 0, st>>>(mo, N, bb, keys, perm);

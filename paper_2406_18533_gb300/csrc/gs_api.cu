@@ -26,6 +26,7 @@ namespace {
 struct DBuf {
     void *p = nullptr;
     size_t cap = 0;
+    bool in_ws = false;    // carved from the caller's workspace (not freed by the library)
 };
 
 }  // namespace
@@ -57,6 +58,12 @@ struct gs_ctx {
     uint32_t *dcnt = nullptr;
     int64_t dN = 0;
     uint64_t frag_cap = 0;
+    // caller workspace (gs_set_workspace): scratch is carved from [ws, ws +
+    // ws_bytes) in order, ws_used so far; a dry run only adds up what would be
+    // carved (gs_workspace_size)
+    char *ws = nullptr;
+    size_t ws_bytes = 0, ws_used = 0;
+    bool dry = false;
     // tracing: events around the stages of gs_train_step
     int trace_max = 0, trace_step = 0;
     bool trace_on = false;
@@ -110,14 +117,38 @@ gs_status device_alloc(void **p, size_t bytes)
     return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
 }
 
+void release(DBuf &b)
+{
+    if (b.p && !b.in_ws) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    b.in_ws = false;
+}
+
+// Grows b to hold `bytes` (plus an eighth, rounded to 256 bytes): from
+// cudaMalloc, or carved from the caller's workspace (a grown buffer's old
+// region is not reused), or, in a dry run, only counted.
 gs_status ensure(gs_ctx *c, DBuf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (bytes <= b.cap) return GS_OK;
-    if (b.p) cudaFree(b.p);
-    b.p = nullptr;
-    b.cap = 0;
+    release(b);
     const size_t nb = ((bytes + bytes / 8) + 255) & ~(size_t)255;
+    if (c->dry) {
+        c->ws_used += nb;
+        b.cap = nb;
+        return GS_OK;
+    }
+    if (c->ws) {
+        if (nb > c->ws_bytes - c->ws_used)
+            return fail(c, GS_ERR_OOM, "workspace of %zu bytes too small: %zu more needed", c->ws_bytes,
+                        nb - (c->ws_bytes - c->ws_used));
+        b.p = c->ws + c->ws_used;
+        b.in_ws = true;
+        c->ws_used += nb;
+        b.cap = nb;
+        return GS_OK;
+    }
     const gs_status r = device_alloc(&b.p, nb);
     if (r != GS_OK) return fail(c, r, "device allocation of %zu bytes failed", nb);
     b.cap = nb;
@@ -527,17 +558,60 @@ gs_status gs_debug_fail_alloc(int64_t after)
     return GS_OK;
 }
 
-gs_status gs_destroy(gs_ctx *c)
+// Every scratch buffer of the context.
+void release_all(gs_ctx *c)
 {
-    if (!c) return GS_ERR_INVALID_ARG;
     DBuf *bufs[] = {&c->ntiles, &c->offsets, &c->scan_tmp, &c->total, &c->keys_alt, &c->vals_alt, &c->sort_tmp,
                     &c->pk, &c->pv, &c->pk_alt, &c->pv_alt, &c->rect, &c->kmask, &c->rmask,
                     &c->xy, &c->conic_o, &c->rgb_d, &c->radius, &c->g_proj, &c->keys,
                     &c->vals, &c->ranges, &c->count, &c->img, &c->dimg, &c->T_final, &c->n_contrib, &c->maps,
                     &c->acc, &c->tile_order, &c->vis, &c->order_tmp, &c->dens_cnt, &c->dens_off,
                     &c->tile_cost, &c->tile_excl, &c->div_f, &c->div_b, &c->div_tot, &c->pool_q};
-    for (DBuf *b : bufs)
-        if (b->p) cudaFree(b->p);
+    for (DBuf *b : bufs) release(*b);
+    c->cost_tiles = 0;
+}
+
+gs_status gs_set_workspace(gs_ctx *c, void *ws, size_t bytes, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (ws && (reinterpret_cast<uintptr_t>(ws) & 255u))
+        return fail(c, GS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return cuda_check(c, "gs_set_workspace");
+    release_all(c);
+    c->ws = static_cast<char *>(ws);
+    c->ws_bytes = ws ? bytes : 0;
+    c->ws_used = 0;
+    return GS_OK;
+}
+
+gs_status gs_get_step(gs_ctx *c, int64_t *step, void *stream)
+{
+    if (!c || !step) return GS_ERR_INVALID_ARG;
+    long long h = 0;
+    cudaStream_t st = S(stream);
+    if (cudaMemcpyAsync(&h, c->dstep, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_check(c, "gs_get_step");
+    *step = (int64_t)h;
+    return GS_OK;
+}
+
+gs_status gs_set_step(gs_ctx *c, int64_t step, void *stream)
+{
+    if (!c || step < 0) return GS_ERR_INVALID_ARG;
+    const long long h = (long long)step;
+    cudaStream_t st = S(stream);
+    // the bias corrections next to the counter are recomputed from it by the next step's tick
+    if (cudaMemcpyAsync(c->dstep, &h, sizeof h, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_check(c, "gs_set_step");
+    return GS_OK;
+}
+
+gs_status gs_destroy(gs_ctx *c)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    release_all(c);
     trace_free(c);
     if (c->status) cudaFree(c->status);
     if (c->dstep) cudaFree(c->dstep);
@@ -608,21 +682,16 @@ gs_status gs_workspace_size(const gs_hparams *hp, int64_t N, const gs_camera *ca
                             uint64_t frag_capacity, size_t *bytes)
 {
     if (!bytes || !cams || B < 1 || B > GS_MAX_VIEWS || N < 0) return GS_ERR_INVALID_ARG;
-    gs_hparams h;
-    if (hp) h = *hp; else gs_default_hparams(&h);
-    const int t = h.tile;
-    if (ilog2_exact(t) < 0) return GS_ERR_INVALID_ARG;
-    size_t tiles = 0, pix = 0;
-    for (int v = 0; v < B; ++v) {
-        tiles += (size_t)((cams[v].W + t - 1) / t) * ((cams[v].H + t - 1) / t);
-        pix += (size_t)cams[v].W * cams[v].H;
-    }
-    const size_t n = (size_t)B * (size_t)N;
-    size_t s = n * (8 + 16 + 16 + 4 + 4 + 4 + 16 + 8 + 8 + 16 + 48) + frag_capacity * (8 * 2) +
-               sort_temp_bytes((uint64_t)n, frag_capacity) +
-               scan_temp_bytes((int64_t)n) + tiles * (8 + 4) + 256 + pix * (4 + 4 + 12 + 12 + 36) + 4096 +
-               (h.sparse_adam ? (size_t)N : 0);
-    *bytes = s;
+    // a dry run of gs_reserve on a context that only counts: exactly what a
+    // fresh workspace gives up to gs_reserve with these sizes
+    gs_ctx d;
+    d.err[0] = 0;
+    if (hp) d.hp = *hp; else gs_default_hparams(&d.hp);
+    if (check_hparams(&d, &d.hp) != GS_OK) return GS_ERR_INVALID_ARG;
+    d.dry = true;
+    const gs_status r = gs_reserve(&d, N, cams, B, frag_capacity);
+    if (r != GS_OK) return r;
+    *bytes = d.ws_used;
     return GS_OK;
 }
 

@@ -333,6 +333,34 @@ class Context:
     def reserve(self, N, cams, frag_capacity):
         self._c("gs_reserve", self.h, int(N), B.camera_array(cams), len(cams), int(frag_capacity))
 
+    def get_step(self) -> int:
+        """The device-side Adam step counter (synchronises)."""
+        out = ctypes.c_int64(0)
+        self._c("gs_get_step", self.h, ctypes.byref(out), _stream())
+        return int(out.value)
+
+    def set_step(self, step: int):
+        self._c("gs_set_step", self.h, int(step), _stream())
+
+    def workspace_size(self, N, cams, frag_capacity):
+        """Bytes of caller workspace gs_reserve(N, cams, frag_capacity) takes."""
+        n = ctypes.c_size_t(0)
+        st = B.lib().gs_workspace_size(ctypes.byref(self.hp), int(N), B.camera_array(cams), len(cams),
+                                       int(frag_capacity), ctypes.byref(n))
+        if st != B.GS_OK:
+            raise B.GSError("gs_workspace_size", st, "")
+        return int(n.value)
+
+    def set_workspace(self, ws):
+        """Take all scratch from `ws` (a caller-owned uint8 CUDA tensor, kept
+        alive here) instead of cudaMalloc; None returns to cudaMalloc."""
+        if ws is None:
+            self._c("gs_set_workspace", self.h, None, 0, _stream())
+        else:
+            self._c("gs_set_workspace", self.h, ctypes.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(),
+                    _stream())
+        self._ws = ws
+
     # ---------------------------------------------------------------- status
     def status(self):
         code = ctypes.c_int32(0)

@@ -37,7 +37,7 @@ def test_binding_covers_every_entry_point(libgs):
 
 def test_abi_version_and_defaults(libgs):
     from paper_2406_18533_gb300 import binding
-    assert libgs.gs_abi_version() == 3
+    assert libgs.gs_abi_version() == 4
     hp = binding.default_hparams()
     assert hp.tile == 16 and hp.smem_batch == 64 and hp.px_per_thread == 1
     assert abs(hp.alpha_min - 1 / 255) < 1e-9 and abs(hp.alpha_max - 0.99) < 1e-7 and abs(hp.T_min - 1e-4) < 1e-10
@@ -96,6 +96,31 @@ def test_workspace_size_grows_with_problem(libgs):
     assert libgs.gs_workspace_size(None, 1000, cams, 1, 10000, ctypes.byref(s1)) == 0
     assert libgs.gs_workspace_size(None, 100000, cams, 1, 10000, ctypes.byref(s2)) == 0
     assert s2.value > s1.value > 0
+
+
+def test_workspace_size_counts_every_buffer_of_the_configuration(libgs):
+    """gs_workspace_size is a host-side dry run of gs_reserve: deterministic,
+    a whole number of 256-byte regions, larger by at least the visibility
+    mask with visible-only Adam and by the cost and range arrays with the
+    measured-cost schedules, and it validates the hyperparameters."""
+    from paper_2406_18533_gb300 import binding as b, synth
+    cams = b.camera_array([synth.test_camera(640, 360)] * 3)
+    N, cap = 50000, 400000
+
+    def size(**kw):
+        hp = b.default_hparams(**kw)
+        out = ctypes.c_size_t(0)
+        assert libgs.gs_workspace_size(ctypes.byref(hp), N, cams, 3, cap, ctypes.byref(out)) == 0
+        return out.value
+
+    base = size()
+    assert base == size() and base % 256 == 0
+    assert size(sparse_adam=1) >= base + N
+    assert size(schedule=1) > base and size(schedule=2) > base
+    assert size(tile=8) > base                       # more tiles: longer range and order arrays
+    hp = b.default_hparams(schedule=3)
+    out = ctypes.c_size_t(0)
+    assert libgs.gs_workspace_size(ctypes.byref(hp), N, cams, 3, cap, ctypes.byref(out)) == b.GS_ERR_INVALID_ARG
 
 
 def test_bin_noalloc_rejects_bad_arguments_on_host(libgs):
