@@ -249,9 +249,10 @@ ProjView proj_of(const gs_proj *p)
                     reinterpret_cast<float4 *>(p->rgb_d), p->radius, p->N};
 }
 
-BlendParams blend_of(const gs_hparams &hp)
+BlendParams blend_of(const gs_hparams &hp, uint64_t list_cap)
 {
-    return BlendParams{hp.alpha_min, hp.alpha_max, hp.T_min, {hp.bg[0], hp.bg[1], hp.bg[2]}};
+    return BlendParams{hp.alpha_min, hp.alpha_max, hp.T_min, {hp.bg[0], hp.bg[1], hp.bg[2]},
+                       (uint32_t)(list_cap < 0xffffffffull ? list_cap : 0xffffffffull)};
 }
 
 cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
@@ -751,7 +752,7 @@ gs_status gs_render_fwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, con
     const uint2 *ranges = reinterpret_cast<const uint2 *>(bins->ranges);
     if (tile_order_pays(vb.total_tiles) && (r = ensure(c, c->tile_order, 4 * ((size_t)vb.total_tiles + 64))) != GS_OK)
         return r;
-    launch_blend_fwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c->hp), c->hp.smem_batch, c->hp.px_per_thread,
+    launch_blend_fwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c->hp, bins->capacity), c->hp.smem_batch, c->hp.px_per_thread,
                      c->status, tile_order_for(c, vb, ranges, S(stream)), S(stream));
     return cuda_check(c, "gs_render_fwd");
 }
@@ -781,7 +782,7 @@ gs_status gs_render_bwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, con
     const uint2 *ranges = reinterpret_cast<const uint2 *>(bins->ranges);
     if (tile_order_pays(vb.total_tiles) && (r = ensure(c, c->tile_order, 4 * ((size_t)vb.total_tiles + 64))) != GS_OK)
         return r;
-    launch_blend_bwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c->hp), c->hp.smem_batch, c->hp.px_per_thread, gv,
+    launch_blend_bwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c->hp, bins->capacity), c->hp.smem_batch, c->hp.px_per_thread, gv,
                      c->status, tile_order_for(c, vb, ranges, st), st);
     launch_moments_to_grads(proj_of(proj), (int64_t)B * proj->N, gv, st);
     return cuda_check(c, "gs_render_bwd");
@@ -988,7 +989,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
                     ptr<uint2>(c->ranges), ptr<uint32_t>(c->count), c->frag_cap, st);
     if (r != GS_OK) return r;
     set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
-    const BlendParams bp = blend_of(c->hp);
+    const BlendParams bp = blend_of(c->hp, c->frag_cap);
     const uint32_t *order = nullptr, *div_f = nullptr, *div_b = nullptr;
     uint32_t *cost = nullptr, *queue = nullptr;
     if (c->hp.schedule == 1 && vb.total_tiles > 0) {
@@ -1094,7 +1095,7 @@ gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int
         off += hw;
     }
     const uint32_t *order = tile_order_for(c, vb, ptr<uint2>(c->ranges), st);
-    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), blend_of(c->hp), c->hp.smem_batch,
+    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), blend_of(c->hp, c->frag_cap), c->hp.smem_batch,
                      c->hp.px_per_thread, c->status, order, st);
     return cuda_check(c, "gs_render");
 }

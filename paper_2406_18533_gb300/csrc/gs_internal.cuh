@@ -39,6 +39,7 @@ struct ViewBatch {
 struct BlendParams {
     float alpha_min, alpha_max, T_min;
     float bg[3];
+    uint32_t list_cap;   // entries in the fragment list: a tile range beyond it is refused
 };
 
 struct SceneView {     // read-only parameter planes

@@ -72,6 +72,19 @@ __device__ __forceinline__ float exponent_cut(float o, float alpha_min)
     return o > alpha_min ? __log2f(__fdividef(alpha_min, o)) : 1.f;
 }
 
+// The tile's [start, end) in the fragment list.  A reversed range (the
+// ranges of a sort that failed, which is reported already) or one that ends
+// past the list (only a caller's corrupt ranges) is treated as empty, so no
+// read leaves the list; the second also records GS_ERR_INVALID_ARG.
+__device__ __forceinline__ uint2 checked_range(const uint2 *ranges, uint32_t tile_id, const BlendParams &bp,
+                                               DevStatus *status)
+{
+    const uint2 rg = ranges[tile_id];
+    if (rg.x <= rg.y && rg.y <= bp.list_cap) return rg;
+    if (rg.y > bp.list_cap && threadIdx.x == 0) atomicCAS(&status->code, 0, (int)GS_ERR_INVALID_ARG);
+    return make_uint2(0u, 0u);
+}
+
 __device__ __forceinline__ int find_view(const ViewBatch &vb, uint32_t tile_id)
 {
     int v = 0;
@@ -222,7 +235,7 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
     const int v = find_view(vb, tile_id);
     const ViewCam &c = vb.v[v];
     const PixelSite<PPT> ps = pixel_site<TILE, PPT>(c, tile_id - c.tile_base, warp, lane);
-    const uint2 rg = ranges[tile_id];
+    const uint2 rg = checked_range(ranges, tile_id, bp, status);
     const int64_t vbase = (int64_t)v * p.N;
     const uint32_t lt = (1u << lane) - 1u;
 
@@ -428,7 +441,7 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
     const int v = find_view(vb, tile_id);
     const ViewCam &c = vb.v[v];
     const PixelSite<PPT> ps = pixel_site<TILE, PPT>(c, tile_id - c.tile_base, warp, lane);
-    const uint2 rg = ranges[tile_id];
+    const uint2 rg = checked_range(ranges, tile_id, bp, status);
     const int64_t vbase = (int64_t)v * p.N;
     const uint32_t lt = (1u << lane) - 1u;
     const int64_t hw = (int64_t)c.W * c.H;

@@ -10,6 +10,8 @@
 * Non-finite parameters in strict mode report GS_ERR_NONFINITE.
 * An injected allocation failure returns GS_ERR_OOM and leaves the context
   usable.
+* Corrupt caller tile ranges are refused on the device (GS_ERR_INVALID_ARG),
+  with no read outside the fragment list.
 """
 import numpy as np
 import pytest
@@ -135,3 +137,38 @@ def test_injected_allocation_failure_leaves_the_context_usable(eng):
     G2, M2, V2 = P2.zeros_like(), P2.zeros_like(), P2.zeros_like()
     loss2 = ref.train_step(P2, G2, M2, V2, 1, cams, tg, check=True)
     assert torch.allclose(loss, loss2, rtol=1e-6)
+
+
+def test_corrupt_tile_ranges_are_refused(eng):
+    """Caller-supplied tile ranges that end past the fragment list, or are
+    reversed, make gs_render_fwd and gs_render_bwd blend nothing on those
+    tiles instead of reading outside the list (the first kind also reports
+    GS_ERR_INVALID_ARG; reversed ranges also come from a sort that failed,
+    which is reported already); every other tile renders as before."""
+    from paper_2406_18533_gb300 import binding as b
+    W, H, tile = 160, 96, 16
+    pj = synth.synthetic_proj(4000, W, H, seed=23)
+    cam = synth.test_camera(W, H)
+    proj = _proj(eng, pj)
+    ctx = eng.Context(tile=tile)
+    bins = ctx.bin(proj, [cam])
+    img0, T0, nc0 = ctx.render_fwd(proj, bins, [cam])
+    torch.cuda.synchronize()
+    assert ctx.status()[0] == b.GS_OK
+    cap = bins.capacity
+    assert int(bins.ranges[3, 1] - bins.ranges[3, 0]) > 0 and int(bins.ranges[7, 1] - bins.ranges[7, 0]) > 0
+    bins.ranges[3, 0], bins.ranges[3, 1] = cap - 2, cap + 4096        # ends past the list
+    bins.ranges[7, 0], bins.ranges[7, 1] = 9, 4                       # reversed
+    img, T, nc = ctx.render_fwd(proj, bins, [cam])
+    torch.cuda.synchronize()
+    assert ctx.status()[0] == b.GS_ERR_INVALID_ARG
+    bad = torch.zeros(H, W, dtype=torch.bool, device="cuda")
+    bad[0:16, 48:64] = True                                           # tile 3 of a 10-tile row
+    bad[0:16, 112:128] = True                                         # tile 7
+    assert bool((T[0][bad] == 1).all()) and bool((nc[0][bad] == 0).all())
+    assert torch.equal(img[0][:, ~bad], img0[0][:, ~bad]) and torch.equal(T[0][~bad], T0[0][~bad])
+    dimg = torch.ones_like(img)
+    g = ctx.render_bwd(proj, bins, [cam], T, nc, dimg)
+    torch.cuda.synchronize()
+    assert ctx.status()[0] == b.GS_ERR_INVALID_ARG
+    assert all(bool(torch.isfinite(getattr(g, k)).all()) for k in ("d_xy_o", "d_conic", "d_rgb"))
