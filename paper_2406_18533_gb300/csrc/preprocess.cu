@@ -128,6 +128,74 @@ __device__ __forceinline__ Geom load_geom(const SceneView &s, int64_t g)
     return G;
 }
 
+// Error-free sum of two floats: s = RN(a + b) and a + b = s + e exactly
+// (Knuth's TwoSum; explicitly rounded operations, so nothing is contracted).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Depth of a point in view space, as the fragment order defines it: the sum
+// t2 + R6 x + R7 y + R8 z evaluated left to right in double precision (each
+// product of two floats is exact in double, each of the three additions is
+// rounded to double) and then rounded to float; *above: whether that double
+// sum exceeds `near`.  Double-precision arithmetic runs at a small fraction
+// of the float rate on this GPU, so the sum is first evaluated in float
+// arithmetic without losing the rounding decision:
+//  - each product splits into an exact pair h + l (h = RN(R x), l by fma);
+//  - t2 + h1 + h2 + h3 by error-free TwoSums, their errors and the l's added
+//    in float: s + e is within 20 * 2^-48 M < 2^-43 M of the exact sum
+//    (M = |t2| + |h1| + |h2| + |h3|);
+//  - the double chain is within 3.01 * 2^-53 M < 2^-51 M of the exact sum;
+//  - f = RN(s + e) with s + e = f + r exactly; if |r| + B, B = 2^-41 M (twice
+//    the 2^-42 M of the two bounds together), is below half the gap from f to
+//    its nearer float neighbour, the double sum lies strictly inside f's
+//    rounding interval, so its float rounding is f; and f > near (f < near)
+//    implies the double sum is above (below) near, near being a float.
+// Otherwise (f within B of a rounding boundary, f == near, a tiny, huge or
+// non-finite value: rare) the double chain itself is evaluated, out of line
+// so that it holds no registers on the common path.
+__device__ __noinline__ double depth_chain(float t, float r6, float r7, float r8, float x, float y, float z)
+{
+    double zd = (double)t;
+    zd = __dadd_rn(zd, __dmul_rn((double)r6, (double)x));
+    zd = __dadd_rn(zd, __dmul_rn((double)r7, (double)y));
+    return __dadd_rn(zd, __dmul_rn((double)r8, (double)z));
+}
+
+__device__ __forceinline__ float view_depth(const ViewCam &c, float x, float y, float z, bool *above)
+{
+    const float t = c.t[2];
+    const float h1 = __fmul_rn(c.R[6], x), l1 = __fmaf_rn(c.R[6], x, -h1);
+    const float h2 = __fmul_rn(c.R[7], y), l2 = __fmaf_rn(c.R[7], y, -h2);
+    const float h3 = __fmul_rn(c.R[8], z), l3 = __fmaf_rn(c.R[8], z, -h3);
+    float s, e1, e2, e3;
+    two_sum(t, h1, s, e1);
+    two_sum(s, h2, s, e2);
+    two_sum(s, h3, s, e3);
+    const float e = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, l1)), __fadd_rn(l2, l3));
+    float f, r;
+    two_sum(s, e, f, r);
+    const float M = __fadd_rn(__fadd_rn(fabsf(t), fabsf(h1)), __fadd_rn(fabsf(h2), fabsf(h3)));
+    const float B = __fmul_rn(M, 0x1p-41f);
+    const uint32_t bits = __float_as_uint(fabsf(f)), ex = bits >> 23;
+    bool fast = isfinite(M) && ex >= 25u && ex <= 253u && f != c.near_z;
+    if (fast) {
+        const float ulp = __uint_as_float((ex - 23u) << 23);      // 2^(exponent - 23) of a normal f
+        const float half_gap = (bits & 0x7fffffu) ? 0.5f * ulp : 0.25f * ulp;
+        fast = __fadd_rn(fabsf(r), B) < half_gap;
+    }
+    if (fast) {
+        *above = f > c.near_z;
+        return f;
+    }
+    const double zd = depth_chain(t, c.R[6], c.R[7], c.R[8], x, y, z);
+    *above = zd > (double)c.near_z;
+    return __double2float_rn(zd);
+}
+
 // Register use is capped for 6 resident blocks (a few spills): more warps hide
 // the latency of the scattered per-view stores better (measured: C3 5.0 ->
 // 4.3 ms).
@@ -150,20 +218,14 @@ __global__ void __launch_bounds__(128, 6) k_preprocess_fwd(SceneView s, ViewBatc
         const int64_t idx = (int64_t)v * s.N + g;
         const float px = c.R[0] * G.x + c.R[1] * G.y + c.R[2] * G.z + c.t[0];
         const float py = c.R[3] * G.x + c.R[4] * G.y + c.R[5] * G.z + c.t[1];
-        // The depth that orders the fragments is evaluated in double with
-        // separately rounded operations (t + R20 x + R21 y + R22 z, left to
-        // right) and then rounded to float, so near-equal depths order the
-        // same way as the correctly rounded exact depth.  Three double
-        // operations per (view, Gaussian) cost nothing measurable.
-        double zd = (double)c.t[2];
-        zd = __dadd_rn(zd, __dmul_rn((double)c.R[6], (double)G.x));
-        zd = __dadd_rn(zd, __dmul_rn((double)c.R[7], (double)G.y));
-        zd = __dadd_rn(zd, __dmul_rn((double)c.R[8], (double)G.z));
-        const float pz = __double2float_rn(zd);
+        // the depth that orders the fragments: the double-precision sum
+        // rounded to float, as the oracle defines it (view_depth)
+        bool above_near;
+        const float pz = view_depth(c, G.x, G.y, G.z, &above_near);
         uint32_t area = 0;
         int r_int = 0;
         uint2 rc = pack_rect(1u, 0u, 0u, 0u);     // empty
-        if (G.ok && zd > (double)c.near_z) {
+        if (G.ok && above_near) {
             const float iz = 1.f / pz;
             const float u = c.fx * px * iz + c.cx;
             const float vv = c.fy * py * iz + c.cy;

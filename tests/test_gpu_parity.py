@@ -186,6 +186,57 @@ def test_preprocess_fwd_stage(eng, oracle):
     assert np.abs(rd[:, 3] / pr["depth"][vis] - 1).max() < 1e-6
 
 
+def _double_chain_depth(sc, cam):
+    """t2 + R6 x + R7 y + R8 z in double, left to right, each operation
+    rounded (numpy does not contract), then rounded to float32."""
+    R = cam.R.astype(np.float64)
+    x, y, z = (sc.mo[:, k].astype(np.float64) for k in range(3))
+    d = ((np.float64(cam.t[2]) + R[2, 0] * x) + R[2, 1] * y) + R[2, 2] * z
+    return d, d.astype(np.float32)
+
+
+@pytest.mark.parametrize("posed", [False, True])
+def test_view_depth_is_the_double_sum_rounded_to_float(eng, posed):
+    """The fragment order's depth key equals, bit for bit, the double sum
+    rounded to float, and visibility follows the double sum's comparison
+    with near.  The kernel evaluates the sum in float arithmetic and falls
+    back to double only near a float rounding boundary: the axis-aligned
+    case puts depths exactly on, and within 2^-40 of, the midpoints between
+    floats in [1, 2) (camera at z = -1, so depth = 1 + z), where the
+    fallback must run; the posed case covers random positions."""
+    rng = np.random.default_rng(6)
+    if posed:
+        sc = synth.tiny_scene(60_000, seed=6, spread=2.0, depth=(0.5, 30.0))
+        cam = synth.camera_look_at((0.3, -0.2, -0.4), (0.0, 0.1, 4.0), (0.05, -1.0, 0.0), 320, 240, 80.0)
+    else:
+        n = 6000
+        sc = synth.tiny_scene(n, seed=6)
+        j = rng.integers(0, 1 << 20, n)
+        near_tie = np.arange(n) < n // 3                              # small j: offsets stay exact in float
+        j[near_tie] = rng.integers(0, 64, near_tie.sum())
+        z = (2 * j + 1).astype(np.float64) * 2.0 ** -24              # 1 + z: a midpoint between floats
+        z[near_tie] += rng.choice([2.0 ** -40, -(2.0 ** -40), 2.0 ** -33], near_tie.sum())
+        assert np.array_equal(z.astype(np.float32).astype(np.float64), z)
+        sc.mo[:, 0] = 0.0
+        sc.mo[:, 1] = 0.0
+        sc.mo[:, 2] = z.astype(np.float32)
+        cam = synth.test_camera(64, 48, pos=(0, 0, -1.0), target=(0, 0, 1.0))
+        assert cam.t[2] == 1.0 and cam.R[2, 2] == 1.0
+    ctx = eng.Context()
+    proj = ctx.preprocess(eng.DeviceScene.from_host(sc), [cam])
+    d64, d32 = _double_chain_depth(sc, cam)
+    r = proj.radius[0].cpu().numpy()
+    dg = proj.rgb_d[0].cpu().numpy()[:, 3]
+    vis = r > 0
+    assert vis.sum() > 0.5 * sc.N
+    assert np.array_equal(dg[vis].view(np.uint32), d32[vis].view(np.uint32))
+    assert (d64[vis] > np.float64(cam.near)).all()
+    if not posed:
+        half = np.abs(d64 - d32.astype(np.float64)) * 2.0 ** 24       # distance to the float, in half-ulps of [1, 2)
+        assert (half == 1.0).sum() > 0.5 * sc.N                       # exact ties (round to even)
+        assert ((half > 0.99) & (half < 1.01) & (half != 1.0)).sum() > 0.2 * sc.N   # within 2^-33 of a tie
+
+
 def test_preprocess_bwd_stage(eng, oracle):
     """Same parameters and the same screen-space gradients on both sides; a
     posed camera so every term of the chain is exercised."""
