@@ -375,6 +375,67 @@ class Context:
                     culled_nonfinite=int(out[4]), contrib_positions=int(out[5]))
 
 
+def train_from_host(ctx: Context, p: DeviceScene, g: DeviceScene, m: DeviceScene, v: DeviceScene, cams,
+                    host_targets, steps: int, cam_arr=None, on_loss=None):
+    """`steps` training steps (gs_train_step, step counter on the device) whose
+    targets come from pinned host memory, pipelined: the upload of step k+1's
+    targets runs on a copy stream into the second of two device buffers
+    while step k computes, and step k's losses come back to the host (pinned,
+    on the compute stream) and are handed to on_loss(k, losses) while step
+    k+1 runs.  host_targets: one pinned [B, 3, H, W] float32 tensor used by
+    every step, or a sequence of `steps` of them.  Returns the last step's
+    losses (numpy).  Synchronises at the end."""
+    seq = isinstance(host_targets, (list, tuple))
+    first = host_targets[0] if seq else host_targets
+    if not first.is_pinned():
+        raise ValueError("host targets must be in pinned memory")
+    Bv = len(cams)
+    arr = cam_arr if cam_arr is not None else B.camera_array(cams)
+    dev = p.mo.device
+    main = torch.cuda.current_stream(dev)
+    copy = torch.cuda.Stream(dev)
+    bufs = [torch.empty(first.shape, dtype=torch.float32, device=dev) for _ in range(2)]
+    uploaded = [torch.cuda.Event() for _ in range(2)]
+    released = [torch.cuda.Event() for _ in range(2)]
+    loss_dev = torch.empty(Bv, dtype=torch.float32, device=dev)
+    loss_host = [torch.empty(Bv, dtype=torch.float32).pin_memory() for _ in range(2)]
+    loss_ready = [torch.cuda.Event() for _ in range(2)]
+
+    def upload(k):
+        b = k % 2
+        with torch.cuda.stream(copy):
+            if k >= 2:
+                copy.wait_event(released[b])          # step k - 2 is done with this buffer
+            bufs[b].copy_(host_targets[k] if seq else host_targets, non_blocking=True)
+            uploaded[b].record(copy)
+
+    last = None
+    if steps > 0:
+        upload(0)
+    for k in range(steps):
+        b = k % 2
+        if k + 1 < steps:
+            upload(k + 1)
+        main.wait_event(uploaded[b])
+        ctx.train_step(p, g, m, v, 0, cams, bufs[b], loss_out=loss_dev, cam_arr=arr)
+        released[b].record(main)
+        loss_host[b].copy_(loss_dev, non_blocking=True)
+        loss_ready[b].record(main)
+        if k > 0:                                    # the previous step's losses, one step behind
+            loss_ready[1 - b].synchronize()
+            last = loss_host[1 - b].numpy().copy()
+            if on_loss:
+                on_loss(k - 1, last)
+    if steps > 0:
+        b = (steps - 1) % 2
+        loss_ready[b].synchronize()
+        last = loss_host[b].numpy().copy()
+        if on_loss:
+            on_loss(steps - 1, last)
+    torch.cuda.synchronize(dev)
+    return last
+
+
 class RasterizeGaussians(torch.autograd.Function):
     """image[B,3,H,W] = render(params) with a hand-written backward.
 
