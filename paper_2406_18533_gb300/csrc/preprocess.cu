@@ -314,9 +314,12 @@ __global__ void __launch_bounds__(256) k_moments_to_grads(ProjView p, int64_t n,
 
 // K8: chain rule from dL/d(u, v, conic, opacity, rgb) per view to the 59
 // parameters; views summed in a fixed order (deterministic), times 1/B.
-// Capped for 3 resident blocks (168 registers; uncapped it takes 181 and
-// fits 2): C3 8.4 -> 6.4 ms.
-__global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatch vb, ProjView p, GradView gv,
+// Capped for 4 resident blocks (128 registers, 8 bytes of spill), which the
+// two passes over the views make room for: one pass holding the 48 SH
+// coefficients, the other their 48 gradient sums (in one pass both, 168
+// registers at 3 blocks: C2 2.24 -> 1.98 ms, C3 2.08 -> 1.90 ms).  Caps of
+// 5 and 6 blocks spill 224 and 360 bytes.
+__global__ void __launch_bounds__(128, 4) k_preprocess_bwd(SceneView s, ViewBatch vb, ProjView p, GradView gv,
                                                         bool grads_ready, SceneMut out, uint8_t *vis,
                                                         float *dacc, uint32_t *dcnt, const DevStatus *status)
 {
@@ -341,9 +344,12 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatc
 #pragma unroll
     for (int k = 0; k < 12; ++k) shv[k] = s.sh[(int64_t)k * s.N + g];
     const float *shf = reinterpret_cast<const float *>(shv);
-    float dsh[48];
-#pragma unroll
-    for (int j = 0; j < 48; ++j) dsh[j] = 0.f;
+    // two passes over the views: the first takes every gradient but the SH
+    // coefficients' (it needs the coefficients, for the clamp test and the
+    // direction term), recording per view and channel whether the colour was
+    // clamped; the second sums the coefficients' gradients Y (x) dL/drgb.  The
+    // coefficients and their 48 gradient sums are then never live together.
+    uint32_t clampm[3] = {0u, 0u, 0u};                 // bit v: channel clamped at 0 in view v
     float dX[3] = {0.f, 0.f, 0.f};
     float dlogit = 0.f;
     float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // dL/dSigma (symmetric), summed over views
@@ -377,7 +383,10 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatc
 #pragma unroll
             for (int k = 0; k < 16; ++k)
                 if (k < nk) acc += shf[3 * k + ch] * Y[k];
-            if (acc + 0.5f < 0.f) drgb[ch] = 0.f;
+            if (acc + 0.5f < 0.f) {
+                drgb[ch] = 0.f;
+                clampm[ch] |= 1u << v;
+            }
         }
         float w[16];
 #pragma unroll
@@ -385,10 +394,7 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatc
             w[k] = 0.f;
             if (k < nk) {
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    dsh[3 * k + ch] += Y[k] * drgb[ch];
-                    w[k] += shf[3 * k + ch] * drgb[ch];
-                }
+                for (int ch = 0; ch < 3; ++ch) w[k] += shf[3 * k + ch] * drgb[ch];
             }
         }
         float gx, gy, gz;
@@ -467,6 +473,29 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(SceneView s, ViewBatc
             dX[1] += c.R[1] * dpx + c.R[4] * dpy + c.R[7] * dpz;
             dX[2] += c.R[2] * dpx + c.R[5] * dpy + c.R[8] * dpz;
         }
+    }
+    // ---- second pass: the SH coefficients, dsh = sum over views of Y (x) dL/drgb
+    float dsh[48];
+#pragma unroll
+    for (int j = 0; j < 48; ++j) dsh[j] = 0.f;
+    for (int v = 0; v < vb.B; ++v) {
+        const int64_t idx = (int64_t)v * s.N + g;
+        if (p.radius[idx] <= 0) continue;
+        const ViewCam &c = vb.v[v];
+        const float4 grg = gv.d_rgb[idx];
+        float ddx = G.x - c.C[0], ddy = G.y - c.C[1], ddz = G.z - c.C[2];
+        const float il = 1.f / sqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+        ddx *= il; ddy *= il; ddz *= il;
+        float Y[16];
+        sh_eval(ddx, ddy, ddz, Y);
+        const float drgb[3] = {(clampm[0] >> v) & 1u ? 0.f : grg.x, (clampm[1] >> v) & 1u ? 0.f : grg.y,
+                               (clampm[2] >> v) & 1u ? 0.f : grg.z};
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < nk) {
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] += Y[k] * drgb[ch];
+            }
     }
     // ---- Sigma = M M^T, M = Rq diag(s): dM = 2 dSigma M
     float M[9];
