@@ -448,7 +448,12 @@ def run_ours(args, rank, world, local_rank):
     binding.call("gs_trace_enable", ctx.h, 0, ctx=ctx.h)
     arr = np.frombuffer(buf, dtype=np.float32).reshape(nstep_tr, binding.GS_TRACE_STAGES)[:nst.value]
     stage_ms = {s: float(arr[:, i].mean()) for i, s in enumerate(binding.TRACE_STAGES)}
+    # the backward's work counters (walked and blended pairs) from one more
+    # step with counting on; the timed and traced steps ran without it
+    ctx.count_work(True)
+    train_once()
     counters = ctx.counters()
+    ctx.count_work(False)
 
     # per-view: the same scene stepped one view at a time over the same views
     per_view = None

@@ -81,6 +81,7 @@ SIGNATURES = {
     "gs_set_step": [_vp, _i64, _vp],
     "gs_get_status": [_vp, _vp, P(_i32), P(ctypes.c_uint64)],
     "gs_get_counters": [_vp, _vp, P(ctypes.c_uint64)],
+    "gs_count_work": [_vp, _i32],
     "gs_preprocess": [_vp, P(gs_scene), P(gs_camera), _i32, P(gs_proj), _vp],
     "gs_bin": [_vp, P(gs_proj), P(gs_camera), _i32, P(gs_bins), P(ctypes.c_uint64), _vp],
     "gs_render_fwd": [_vp, P(gs_proj), P(gs_bins), P(gs_camera), _i32, _vp, _vp, _vp, _vp],

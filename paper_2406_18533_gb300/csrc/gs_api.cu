@@ -58,6 +58,7 @@ struct gs_ctx {
     uint32_t *dcnt = nullptr;
     int64_t dN = 0;
     uint64_t frag_cap = 0;
+    bool count_work = false;       // gs_count_work: the backward counts walked and blended pairs
     // caller workspace (gs_set_workspace): scratch is carved from [ws, ws +
     // ws_bytes) in order, ws_used so far; a dry run only adds up what would be
     // carved (gs_workspace_size)
@@ -249,10 +250,11 @@ ProjView proj_of(const gs_proj *p)
                     reinterpret_cast<float4 *>(p->rgb_d), p->radius, p->N};
 }
 
-BlendParams blend_of(const gs_hparams &hp, uint64_t list_cap)
+BlendParams blend_of(const gs_ctx *c, uint64_t list_cap)
 {
+    const gs_hparams &hp = c->hp;
     return BlendParams{hp.alpha_min, hp.alpha_max, hp.T_min, {hp.bg[0], hp.bg[1], hp.bg[2]},
-                       (uint32_t)(list_cap < 0xffffffffull ? list_cap : 0xffffffffull)};
+                       (uint32_t)(list_cap < 0xffffffffull ? list_cap : 0xffffffffull), c->count_work ? 1 : 0};
 }
 
 cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
@@ -664,6 +666,13 @@ gs_status gs_get_counters(gs_ctx *c, void *stream, uint64_t out[6])
     return GS_OK;
 }
 
+gs_status gs_count_work(gs_ctx *c, int32_t on)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    c->count_work = on != 0;
+    return GS_OK;
+}
+
 gs_status gs_reserve(gs_ctx *c, int64_t N, const gs_camera *cams, int32_t B, uint64_t frag_capacity)
 {
     if (!c || N < 0) return GS_ERR_INVALID_ARG;
@@ -752,7 +761,7 @@ gs_status gs_render_fwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, con
     const uint2 *ranges = reinterpret_cast<const uint2 *>(bins->ranges);
     if (tile_order_pays(vb.total_tiles) && (r = ensure(c, c->tile_order, 4 * ((size_t)vb.total_tiles + 64))) != GS_OK)
         return r;
-    launch_blend_fwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c->hp, bins->capacity), c->hp.smem_batch, c->hp.px_per_thread,
+    launch_blend_fwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c, bins->capacity), c->hp.smem_batch, c->hp.px_per_thread,
                      c->status, tile_order_for(c, vb, ranges, S(stream)), S(stream));
     return cuda_check(c, "gs_render_fwd");
 }
@@ -782,7 +791,7 @@ gs_status gs_render_bwd(gs_ctx *c, const gs_proj *proj, const gs_bins *bins, con
     const uint2 *ranges = reinterpret_cast<const uint2 *>(bins->ranges);
     if (tile_order_pays(vb.total_tiles) && (r = ensure(c, c->tile_order, 4 * ((size_t)vb.total_tiles + 64))) != GS_OK)
         return r;
-    launch_blend_bwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c->hp, bins->capacity), c->hp.smem_batch, c->hp.px_per_thread, gv,
+    launch_blend_bwd(vb, proj_of(proj), bins->vals, ranges, blend_of(c, bins->capacity), c->hp.smem_batch, c->hp.px_per_thread, gv,
                      c->status, tile_order_for(c, vb, ranges, st), st);
     launch_moments_to_grads(proj_of(proj), (int64_t)B * proj->N, gv, st);
     return cuda_check(c, "gs_render_bwd");
@@ -989,7 +998,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
                     ptr<uint2>(c->ranges), ptr<uint32_t>(c->count), c->frag_cap, st);
     if (r != GS_OK) return r;
     set_images(vb, ptr<float>(c->img), ptr<float>(c->T_final), ptr<uint32_t>(c->n_contrib), ptr<float>(c->dimg));
-    const BlendParams bp = blend_of(c->hp, c->frag_cap);
+    const BlendParams bp = blend_of(c, c->frag_cap);
     const uint32_t *order = nullptr, *div_f = nullptr, *div_b = nullptr;
     uint32_t *cost = nullptr, *queue = nullptr;
     if (c->hp.schedule == 1 && vb.total_tiles > 0) {
@@ -1095,7 +1104,7 @@ gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int
         off += hw;
     }
     const uint32_t *order = tile_order_for(c, vb, ptr<uint2>(c->ranges), st);
-    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), blend_of(c->hp, c->frag_cap), c->hp.smem_batch,
+    launch_blend_fwd(vb, pv, ptr<uint32_t>(c->vals), ptr<uint2>(c->ranges), blend_of(c, c->frag_cap), c->hp.smem_batch,
                      c->hp.px_per_thread, c->status, order, st);
     return cuda_check(c, "gs_render");
 }

@@ -40,6 +40,7 @@ struct BlendParams {
     float alpha_min, alpha_max, T_min;
     float bg[3];
     uint32_t list_cap;   // entries in the fragment list: a tile range beyond it is refused
+    int32_t count_work;  // nonzero: the backward counts its walked and blended pairs (counters[4], [2])
 };
 
 struct SceneView {     // read-only parameter planes

@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd_pool(ViewBatch v
 // With 2 pixels per thread the backward is held to 64 registers (8 CTAs of
 // 128 threads per SM; 4 bytes of spill): 1% faster on GB300 than at 68
 // registers and 7 CTAs.  Other shapes keep the compiler's choice.
-template <int TILE, int CH, int PPT>
+template <int TILE, int CH, int PPT, bool COUNT>
 __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch &vb, const ProjView &p,
                                                const uint32_t *vals, const uint2 *ranges, const BlendParams &bp,
                                                const GradView &gv, DevStatus *status, uint32_t *cost)
@@ -505,41 +505,50 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
             const float4 q = s_q[i];
             const float dx = __fsub_rn(ps.fx, xyc.x);
             const DxTerms dt = dx_terms(q, dx);
-            // this lane's sums over its pixels: M = sum dpow, My = sum dpow dy,
+            // The exponent of every pixel first, the rest only when some lane
+            // of the warp passes the cut (a warp-uniform branch), then without
+            // branches: a pixel that does not blend takes alpha = 0, which
+            // leaves T, S and every sum unchanged.
+            // This lane's sums over its pixels: M = sum dpow, My = sum dpow dy,
             // Myy = sum dpow dy^2 (the lane's pixels share one column, so the
             // dx moments follow from these: Mx = dx M, Mxx = dx^2 M, Mxy =
-            // dx My) and the colour sums r, g, b
+            // dx My) and the colour sums r, g, b.
+            float dy[PPT], pw[PPT];
+            bool pass[PPT], anyp = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const bool walk = rel < nc[k];
+                if constexpr (COUNT) walked += walk;
+                dy[k] = __fsub_rn(ps.fy[k], xyc.y);
+                pw[k] = power2(q, dt, dy[k]);
+                pass[k] = walk && pw[k] >= xyc.z && pw[k] <= 0.f;
+                anyp = anyp || pass[k];
+            }
+            if (!__any_sync(0xffffffffu, anyp)) continue;
+            const float4 rgb = s_rgb[i];
             float M = 0.f, My = 0.f, Myy = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
             bool any = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (!(rel < nc[k])) continue;
-                ++walked;
-                const float dy = __fsub_rn(ps.fy[k], xyc.y);
-                const float pw = power2(q, dt, dy);
-                if (!(pw >= xyc.z && pw <= 0.f)) continue;
-                const float G = ex2(pw);
-                const float oG = q.w * G;
+                const float oG = q.w * ex2(pw[k]);
                 const float alpha = fminf(bp.alpha_max, oG);
-                if (alpha < bp.alpha_min) continue;
-                any = true;
-                ++evals;
-                const float4 rgb = s_rgb[i];
-                const float Tj = __fdividef(T[k], 1.f - alpha);
-                const float w = alpha * Tj;
+                const bool bl = pass[k] && alpha >= bp.alpha_min;
+                const float a = bl ? alpha : 0.f;
+                const float Tj = __fdividef(T[k], 1.f - a);
+                const float w = a * Tj;
                 cr = fmaf(w, dC0[k], cr);
                 cg = fmaf(w, dC1[k], cg);
                 cb = fmaf(w, dC2[k], cb);
                 const float e = fmaf(rgb.x, dC0[k], fmaf(rgb.y, dC1[k], fmaf(rgb.z, dC2[k], -S[k])));
-                S[k] = fmaf(alpha, e, S[k]);
-                T[k] = Tj;
-                if (oG < bp.alpha_max) {                // alpha not clamped: geometry and opacity terms
-                    const float dpow = w * e;           // alpha dL/dalpha
-                    const float dpy = dpow * dy;
-                    M += dpow;
-                    My += dpy;
-                    Myy = fmaf(dpy, dy, Myy);
-                }
+                S[k] = fmaf(a, e, S[k]);
+                T[k] = bl ? Tj : T[k];
+                const float dpow = (bl && oG < bp.alpha_max) ? w * e : 0.f;   // alpha dL/dalpha (alpha unclamped)
+                const float dpy = dpow * dy[k];
+                M += dpow;
+                My += dpy;
+                Myy = fmaf(dpy, dy[k], Myy);
+                any = any || bl;
+                if constexpr (COUNT) evals += bl;
             }
             const uint32_t ballot = __ballot_sync(0xffffffffu, any);
             if (ballot == 0u) continue;
@@ -577,46 +586,49 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
         __syncwarp();
     }
     // blended (pixel, Gaussian) pairs and walked (pixel, position) pairs
-    unsigned long long e = evals, wk = walked;
+    if constexpr (COUNT) {
+        unsigned long long e = evals, wk = walked;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        e += __shfl_xor_sync(0xffffffffu, e, o);
-        wk += __shfl_xor_sync(0xffffffffu, wk, o);
-    }
-    if (lane == 0) {
-        if (e) atomicAdd(&status->counters[2], e);
-        if (wk) atomicAdd(&status->counters[4], wk);
+        for (int o = 16; o > 0; o >>= 1) {
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+            wk += __shfl_xor_sync(0xffffffffu, wk, o);
+        }
+        if (lane == 0) {
+            if (e) atomicAdd(&status->counters[2], e);
+            if (wk) atomicAdd(&status->counters[4], wk);
+        }
     }
     add_cost(cost, tile_id, t0, lane);
 }
 
-template <int TILE, int CH, int PPT>
+template <int TILE, int CH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1)) k_blend_bwd(ViewBatch vb, ProjView p, const uint32_t *vals,
                                                                 const uint2 *ranges, BlendParams bp, GradView gv,
                                                                 DevStatus *status, const uint32_t *order,
                                                                 uint32_t *cost)
 {
     const uint32_t tile_id = order ? order[blockIdx.x] : blockIdx.x;   // launch order (launch_tile_order)
-    blend_bwd_tile<TILE, CH, PPT>(tile_id, vb, p, vals, ranges, bp, gv, status, cost);
+    blend_bwd_tile<TILE, CH, PPT, COUNT>(tile_id, vb, p, vals, ranges, bp, gv, status, cost);
 }
 
-template <int TILE, int CH, int PPT>
+template <int TILE, int CH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1))
     k_blend_bwd_ranges(ViewBatch vb, ProjView p, const uint32_t *vals, const uint2 *ranges, BlendParams bp,
                        GradView gv, DevStatus *status, const uint32_t *div, uint32_t *cost)
 {
     const uint32_t lo = div[blockIdx.x];
     const uint32_t hi = blockIdx.x + 1 < gridDim.x ? min(div[blockIdx.x + 1], vb.total_tiles) : vb.total_tiles;
-    for (uint32_t t = lo; t < hi; ++t) blend_bwd_tile<TILE, CH, PPT>(t, vb, p, vals, ranges, bp, gv, status, cost);
+    for (uint32_t t = lo; t < hi; ++t)
+        blend_bwd_tile<TILE, CH, PPT, COUNT>(t, vb, p, vals, ranges, bp, gv, status, cost);
 }
 
-template <int TILE, int CH, int PPT>
+template <int TILE, int CH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TILE *TILE / PPT, (PPT == 2 ? 8 : 1))
     k_blend_bwd_pool(ViewBatch vb, ProjView p, const uint32_t *vals, const uint2 *ranges, BlendParams bp,
                      GradView gv, DevStatus *status, const uint32_t *order, uint32_t *queue, uint32_t *cost)
 {
     for (uint32_t t = pool_next(queue); t < vb.total_tiles; t = pool_next(queue))
-        blend_bwd_tile<TILE, CH, PPT>(order ? order[t] : t, vb, p, vals, ranges, bp, gv, status, cost);
+        blend_bwd_tile<TILE, CH, PPT, COUNT>(order ? order[t] : t, vb, p, vals, ranges, bp, gv, status, cost);
 }
 
 // Launch order of the tiles, heaviest list first.  With few waves of CTAs
@@ -715,24 +727,36 @@ void fwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, co
                                                                                  sc.order, sc.cost);
 }
 
+template <int TILE, int CH, int PPT, bool COUNT>
+void bwd_launch_counting(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
+                         const BlendParams &bp, const GradView &g, DevStatus *status, const Sched &sc, cudaStream_t st)
+{
+    constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
+    static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH, PPT, COUNT>, sm) &&
+                           smem_opt_in(k_blend_bwd_ranges<TILE, CH, PPT, COUNT>, sm) &&
+                           smem_opt_in(k_blend_bwd_pool<TILE, CH, PPT, COUNT>, sm);
+    (void)ok;
+    if (sc.queue)
+        k_blend_bwd_pool<TILE, CH, PPT, COUNT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(
+            vb, p, vals, ranges, bp, g, status, sc.order, sc.queue, sc.cost);
+    else if (sc.div)
+        k_blend_bwd_ranges<TILE, CH, PPT, COUNT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(
+            vb, p, vals, ranges, bp, g, status, sc.div, sc.cost);
+    else
+        k_blend_bwd<TILE, CH, PPT, COUNT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(
+            vb, p, vals, ranges, bp, g, status, sc.order, sc.cost);
+}
+
+// The walked and blended pairs are counted only when asked (bp.count_work):
+// the two counts cost about 3% of the backward's issued instructions.
 template <int TILE, int CH, int PPT>
 void bwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                 const BlendParams &bp, const GradView &g, DevStatus *status, const Sched &sc, cudaStream_t st)
 {
-    constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
-    static const bool ok = smem_opt_in(k_blend_bwd<TILE, CH, PPT>, sm) &&
-                           smem_opt_in(k_blend_bwd_ranges<TILE, CH, PPT>, sm) &&
-                           smem_opt_in(k_blend_bwd_pool<TILE, CH, PPT>, sm);
-    (void)ok;
-    if (sc.queue)
-        k_blend_bwd_pool<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status,
-                                                                              sc.order, sc.queue, sc.cost);
-    else if (sc.div)
-        k_blend_bwd_ranges<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status,
-                                                                                sc.div, sc.cost);
+    if (bp.count_work)
+        bwd_launch_counting<TILE, CH, PPT, true>(vb, p, vals, ranges, bp, g, status, sc, st);
     else
-        k_blend_bwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, g, status,
-                                                                                 sc.order, sc.cost);
+        bwd_launch_counting<TILE, CH, PPT, false>(vb, p, vals, ranges, bp, g, status, sc, st);
 }
 
 template <class K>
@@ -754,8 +778,8 @@ uint32_t resident_ctas()
         int per_sm = 0;
         cudaError_t e;
         if (BWD)
-            e = POOL ? occupancy(&per_sm, k_blend_bwd_pool<TILE, CH, PPT>, threads, sm)
-                     : occupancy(&per_sm, k_blend_bwd_ranges<TILE, CH, PPT>, threads, sm);
+            e = POOL ? occupancy(&per_sm, k_blend_bwd_pool<TILE, CH, PPT, false>, threads, sm)
+                     : occupancy(&per_sm, k_blend_bwd_ranges<TILE, CH, PPT, false>, threads, sm);
         else
             e = POOL ? occupancy(&per_sm, k_blend_fwd_pool<TILE, CH, PPT>, threads, sm)
                      : occupancy(&per_sm, k_blend_fwd_ranges<TILE, CH, PPT>, threads, sm);

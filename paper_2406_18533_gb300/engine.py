@@ -368,6 +368,11 @@ class Context:
         self._c("gs_get_status", self.h, _stream(), ctypes.byref(code), ctypes.byref(needed))
         return int(code.value), int(needed.value)
 
+    def count_work(self, on: bool = True):
+        """Counts the backward's walked and blended pairs from the next step on
+        (off by default: counting costs issue slots in the backward)."""
+        self._c("gs_count_work", self.h, int(bool(on)))
+
     def counters(self):
         out = (ctypes.c_uint64 * 6)()
         self._c("gs_get_counters", self.h, _stream(), out)
