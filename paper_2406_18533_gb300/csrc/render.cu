@@ -179,6 +179,12 @@ __device__ __forceinline__ PixelSite<PPT> pixel_site(const ViewCam &c, uint32_t 
     return s;
 }
 
+// Compile-time pixel index (k) for the per-pixel bodies of the backward.
+template <int K>
+struct PixelK {
+    static constexpr int value = K;
+};
+
 // One list entry as gathered by a lane during a refill.
 struct Entry {
     bool ok;
@@ -505,16 +511,19 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
             const float4 q = s_q[i];
             const float dx = __fsub_rn(ps.fx, xyc.x);
             const DxTerms dt = dx_terms(q, dx);
-            // The exponent of every pixel first, the rest only when some lane
-            // of the warp passes the cut (a warp-uniform branch), then without
-            // branches: a pixel that does not blend takes alpha = 0, which
-            // leaves T, S and every sum unchanged.
+            // The exponent of every pixel first; the rest only for the pixel
+            // rows (k) where some lane passes the cut (warp-uniform branches:
+            // an entry that reaches only one of a lane's pixels costs one
+            // pixel's arithmetic), there without branches: a pixel that does
+            // not blend takes alpha = 0, which leaves T, S and every sum
+            // unchanged.
             // This lane's sums over its pixels: M = sum dpow, My = sum dpow dy,
             // Myy = sum dpow dy^2 (the lane's pixels share one column, so the
             // dx moments follow from these: Mx = dx M, Mxx = dx^2 M, Mxy =
             // dx My) and the colour sums r, g, b.
             float dy[PPT], pw[PPT];
-            bool pass[PPT], anyp = false;
+            bool pass[PPT];
+            uint32_t rows = 0u;                           // bit k: some lane passes at pixel k
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const bool walk = rel < nc[k];
@@ -522,14 +531,14 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
                 dy[k] = __fsub_rn(ps.fy[k], xyc.y);
                 pw[k] = power2(q, dt, dy[k]);
                 pass[k] = walk && pw[k] >= xyc.z && pw[k] <= 0.f;
-                anyp = anyp || pass[k];
+                rows |= __any_sync(0xffffffffu, pass[k]) ? 1u << k : 0u;
             }
-            if (!__any_sync(0xffffffffu, anyp)) continue;
+            if (rows == 0u) continue;
             const float4 rgb = s_rgb[i];
             float M = 0.f, My = 0.f, Myy = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
             bool any = false;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
+            auto pixel = [&](auto kc) {
+                constexpr int k = decltype(kc)::value;
                 const float oG = q.w * ex2(pw[k]);
                 const float alpha = fminf(bp.alpha_max, oG);
                 const bool bl = pass[k] && alpha >= bp.alpha_min;
@@ -549,6 +558,23 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
                 Myy = fmaf(dpy, dy[k], Myy);
                 any = any || bl;
                 if constexpr (COUNT) evals += bl;
+            };
+            if constexpr (PPT == 1) {
+                pixel(PixelK<0>{});
+            } else if constexpr (PPT == 2) {
+                if (rows == 3u) {                             // both: the two pixels interleave
+                    pixel(PixelK<0>{});
+                    pixel(PixelK<1>{});
+                } else if (rows == 1u) {
+                    pixel(PixelK<0>{});
+                } else {
+                    pixel(PixelK<1>{});
+                }
+            } else {
+                if (rows & 1u) pixel(PixelK<0>{});
+                if (rows & 2u) pixel(PixelK<1>{});
+                if (rows & 4u) pixel(PixelK<2>{});
+                if (rows & 8u) pixel(PixelK<3>{});
             }
             const uint32_t ballot = __ballot_sync(0xffffffffu, any);
             if (ballot == 0u) continue;
