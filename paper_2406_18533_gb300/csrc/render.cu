@@ -179,7 +179,7 @@ __device__ __forceinline__ PixelSite<PPT> pixel_site(const ViewCam &c, uint32_t 
     return s;
 }
 
-// Compile-time pixel index (k) for the per-pixel bodies of the backward.
+// Compile-time pixel index (k) for the per-pixel bodies of the blending kernels.
 template <int K>
 struct PixelK {
     static constexpr int value = K;
@@ -281,7 +281,8 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
             bool all_done = true;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) all_done = all_done && done[k];
-            if (!all_done) {
+            // (two pixels per thread: the walk votes across the warp, so every lane enters it)
+            if (PPT == 2 ? !__all_sync(0xffffffffu, all_done) : !all_done) {
                 for (int i = 0; i < n; ++i) {
                     const float4 xyc = s_xyc[i];
                     const float4 q = s_q[i];
@@ -306,6 +307,49 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
                         C2[0] += rgb.z * w;
                         T[0] = hit ? Tn : T[0];
                         nc[0] = hit ? pos1 : nc[0];
+                    } else if constexpr (PPT == 2) {
+                        // two pixels: the exponents first, then the blending
+                        // only for the pixel rows where some lane passes
+                        // (warp-uniform branches, no per-pixel ones); the
+                        // lanes leave together once every pixel is done
+                        float pw[PPT];
+                        bool pass[PPT];
+                        uint32_t rows = 0u;
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) {
+                            pw[k] = power2(q, dt, __fsub_rn(ps.fy[k], xyc.y));
+                            pass[k] = !done[k] && pw[k] >= xyc.z && pw[k] <= 0.f;
+                            rows |= __any_sync(0xffffffffu, pass[k]) ? 1u << k : 0u;
+                        }
+                        if (rows == 0u) {
+                            if (__all_sync(0xffffffffu, done[0] && done[1])) break;
+                            continue;
+                        }
+                        const float4 rgb = s_rgb[i];
+                        auto pixel = [&](auto kc) {
+                            constexpr int k = decltype(kc)::value;
+                            const float a0 = fminf(bp.alpha_max, q.w * ex2(pw[k]));
+                            bool hit = pass[k] && a0 >= bp.alpha_min;
+                            const float Tn = T[k] * (1.f - a0);
+                            const bool term = hit && Tn < bp.T_min;     // would saturate: stop before it
+                            done[k] = done[k] || term;
+                            ne[k] = term ? pos1 : ne[k];
+                            hit = hit && !term;
+                            const float w = hit ? a0 * T[k] : 0.f;
+                            C0[k] += rgb.x * w;
+                            C1[k] += rgb.y * w;
+                            C2[k] += rgb.z * w;
+                            T[k] = hit ? Tn : T[k];
+                            nc[k] = hit ? pos1 : nc[k];
+                        };
+                        if (rows == 3u) {
+                            pixel(PixelK<0>{});
+                            pixel(PixelK<1>{});
+                        } else if (rows == 1u) {
+                            pixel(PixelK<0>{});
+                        } else {
+                            pixel(PixelK<1>{});
+                        }
                     } else {
                         float4 rgb_early;
                         if constexpr (PPT == 4) rgb_early = s_rgb[i];    // four pixels: load ahead of the tests
@@ -551,7 +595,7 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
                 const float e = fmaf(rgb.x, dC0[k], fmaf(rgb.y, dC1[k], fmaf(rgb.z, dC2[k], -S[k])));
                 S[k] = fmaf(a, e, S[k]);
                 T[k] = bl ? Tj : T[k];
-                const float dpow = (bl && oG < bp.alpha_max) ? w * e : 0.f;   // alpha dL/dalpha (alpha unclamped)
+                const float dpow = oG < bp.alpha_max ? w * e : 0.f;   // alpha dL/dalpha (alpha unclamped; w = 0 unless blended)
                 const float dpy = dpow * dy[k];
                 M += dpow;
                 My += dpy;
