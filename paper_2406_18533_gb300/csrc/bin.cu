@@ -207,86 +207,88 @@ __global__ void __launch_bounds__(256) k_pair_compact(int64_t n, const float4 *r
     }
 }
 
-// Culls footprint tiles against the alpha >= cull_alpha ellipse, in pair
-// index order (coalesced reads): a warp lays the rectangles (of at most
-// TILE_CULL_MAX_AREA tiles) of its 32 pairs end to end and tests one (pair,
-// tile) slot per lane per round (ellipse_terms once per pair, the box test
-// per slot), so the work is balanced whatever the rectangle sizes; each
-// pair's lane collects its slots' ballot bits.  rm[i] = (rectangle words,
-// kept-tile bits low, high); larger rectangles and pairs not culled keep all
-// bits.  area[i] becomes the kept count (0 drops the pair from the binning).
-// Pairs with area[i] = 0 (not visible) are skipped.
+// Culls footprint tiles against the alpha >= cull_alpha ellipse, one pair
+// per thread, in pair index order (coalesced reads).  With f(d) = a dx^2 +
+// 2 b dx dy + c dy^2 the ellipse is f <= L (L = the widened threshold of
+// ellipse_terms).  Per tile row, the pixel-centre rows of the row give a band
+// dy in [dy0, dy1]; the ellipse meets the band where |dy| <= Y = sqrt(a L /
+// det), and there its x-range is the interval between
+//   xl(dy) = (-b dy - sqrt(a L - det dy^2)) / a  and
+//   xr(dy) = (-b dy + sqrt(a L - det dy^2)) / a.
+// xr is concave in dy with its maximum at dy_r = -b sqrt(L / (c det)) (the
+// ellipse's rightmost point) and xl convex with its minimum at -dy_r, so the
+// band's x-range is [xl(clamp(-dy_r)), xr(clamp(dy_r))], each clamped into the
+// band.  A tile of the row is kept when its pixel-centre columns meet that
+// range.  This is the box test of ellipse_box_hits done once per tile row
+// instead of once per tile; the band limits, the range and Y are widened by
+// 1e-3 relative plus 1e-2 pixel, above the rounding of the square roots and
+// divisions (the threshold L already carries ellipse_terms' margin), so a
+// tile is never dropped where the per-pixel test could blend.
+// rm[i] = (rectangle words, kept-tile bits low, high); larger rectangles and
+// pairs not culled keep all bits.  area[i] becomes the kept count (0 drops
+// the pair from the binning).  Pairs with area[i] = 0 (not visible) are
+// skipped.
+// sqrt(x) for x >= 0 from the approximate reciprocal square root (0 at 0).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    return x > 0.f ? x * rsqrtf(x) : 0.f;
+}
+
+__device__ __forceinline__ uint64_t row_interval_mask(const float4 &co, const float4 &te, float u, float v,
+                                                      uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1, float T)
+{
+    if (!(te.x >= 0.f)) return 0ull;                     // alpha never reaches the cut
+    const uint32_t w = x1 - x0 + 1u;
+    const uint32_t ra = w * (y1 - y0 + 1u);
+    const uint64_t all = ra >= 64u ? ~0ull : ((1ull << ra) - 1ull);
+    if (te.x == INFINITY) return all;                     // not positive definite: keep every tile
+    const float a = co.x, b = co.y, L = te.x, det = te.w;
+    constexpr float REL = 1e-3f, ABS = 1e-2f;
+    const float aL = a * L;
+    const float Y = sqrt_approx(__fdividef(aL, det)) * (1.f + REL) + ABS;   // |dy| reach of the ellipse
+    const float dyr = -b * sqrt_approx(L * te.z / det);                       // dy of the rightmost point (te.z = 1/c)
+    const float ia = te.y;                                                     // 1/a
+    const float iT = 1.f / T;                                                  // exact: T is a power of two
+    uint64_t mask = 0ull;
+    for (uint32_t ty = y0; ty <= y1; ++ty) {
+        const float py0 = (float)ty * T + 0.5f - v;               // the row's pixel-centre dy range
+        const float lo = fmaxf(py0 - ABS, -Y), hi = fminf(py0 + (T - 1.f) + ABS, Y);
+        if (!(lo <= hi)) continue;
+        const float dr = fminf(fmaxf(dyr, lo), hi), dl = fminf(fmaxf(-dyr, lo), hi);
+        const float sr = sqrt_approx(aL - det * dr * dr), sl = sqrt_approx(aL - det * dl * dl);
+        float xr = (sr - b * dr) * ia, xl = -(sl + b * dl) * ia;
+        const float m = (xr - xl) * REL + ABS;
+        xr = u + xr + m;
+        xl = u + xl - m;
+        // tiles whose pixel-centre columns [tx T + 0.5, tx T + T - 0.5] meet [xl, xr]
+        const float fl = ceilf((xl - (T - 0.5f)) * iT), fh = floorf((xr - 0.5f) * iT);
+        const int tl = (int)fmaxf(fl, (float)x0), th = (int)fminf(fh, (float)x1);
+        if (tl > th) continue;
+        const uint32_t s = (ty - y0) * w + ((uint32_t)tl - x0), len = (uint32_t)(th - tl) + 1u;
+        mask |= (~0ull >> (64u - len)) << s;
+    }
+    return mask & all;
+}
+
 __global__ void __launch_bounds__(256) k_cull_tiles(ViewBatch vb, ProjView p, const uint2 *rect, uint32_t *area,
                                                     float cull_alpha, uint4 *rm)
 {
     const int64_t n = (int64_t)vb.B * p.N;
-    const int lane = threadIdx.x & 31;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i - lane >= n) return;                   // uniform over the warp
-    const uint32_t cnt0 = i < n ? area[i] : 0u;  // 0: not visible, nothing to do
-    if (!__any_sync(0xffffffffu, cnt0 > 0u)) return;
-    const uint2 rc = cnt0 ? rect[i] : make_uint2(1u, 0u);
+    if (i >= n) return;
+    const uint32_t cnt0 = area[i];                       // 0: not visible, nothing to do
+    if (!cnt0) return;
+    const uint2 rc = rect[i];
     const uint32_t ra = rect_area(rc);
-    const bool cull = cnt0 > 0u && ra <= TILE_CULL_MAX_AREA;
     uint64_t mask = ~0ull;
-    if (__any_sync(0xffffffffu, cull)) {
-        float4 co = make_float4(0.f, 0.f, 0.f, 0.f), te = make_float4(-1.f, 0.f, 0.f, 0.f);
-        float2 uv = make_float2(0.f, 0.f);
-        if (cull) {
-            co = p.conic_o[i];
-            uv = p.xy[i];
-            te = ellipse_terms(co, cull_alpha);
-            mask = 0ull;
-        }
-        const uint32_t x0 = rc.x & 0xffffu, y0 = rc.y & 0xffffu, w = (rc.x >> 16) - x0 + 1u;
-        const uint32_t sa = cull ? ra : 0u;      // slots of this lane's pair
-        uint32_t incl = sa;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        const uint32_t rel = incl - sa;
-        const uint32_t span = __shfl_sync(0xffffffffu, incl, 31);
-        const float T = (float)vb.tile;
-        for (uint32_t r0 = 0; r0 < span; r0 += 32) {
-            const uint32_t f = r0 + lane;
-            int L = 0;                           // last lane with rel <= f
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const uint32_t q = __shfl_sync(0xffffffffu, rel, L + step);
-                if (q <= f) L += step;
-            }
-            const uint32_t local = f - __shfl_sync(0xffffffffu, rel, L);
-            const uint32_t lw = __shfl_sync(0xffffffffu, w, L);
-            const uint32_t lx0 = __shfl_sync(0xffffffffu, x0, L), ly0 = __shfl_sync(0xffffffffu, y0, L);
-            const float4 lt = make_float4(__shfl_sync(0xffffffffu, te.x, L), __shfl_sync(0xffffffffu, te.y, L),
-                                          __shfl_sync(0xffffffffu, te.z, L), __shfl_sync(0xffffffffu, te.w, L));
-            const float la = __shfl_sync(0xffffffffu, co.x, L), lb = __shfl_sync(0xffffffffu, co.y, L),
-                        lc = __shfl_sync(0xffffffffu, co.z, L);
-            const float lu = __shfl_sync(0xffffffffu, uv.x, L), lv = __shfl_sync(0xffffffffu, uv.y, L);
-            bool hit = false;
-            if (f < span) {
-                const uint32_t dy = local / lw, dx = local - dy * lw;
-                const float bx = __fmaf_rn((float)(lx0 + dx), T, 0.5f), by = __fmaf_rn((float)(ly0 + dy), T, 0.5f);
-                hit = ellipse_terms_box_hits(lt, la, lb, lc, lu, lv, bx, __fadd_rn(bx, T - 1.f), by,
-                                             __fadd_rn(by, T - 1.f));
-            }
-            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-            // this lane's slots [rel, rel + sa) within the round's [r0, r0 + 32)
-            if (sa && rel < r0 + 32u && rel + sa > r0) {
-                const uint32_t lo = rel > r0 ? rel - r0 : 0u;
-                const uint32_t hi = rel + sa < r0 + 32u ? rel + sa - r0 : 32u;
-                const uint32_t width = hi - lo;
-                const uint32_t bits = (bal >> lo) & (width == 32u ? 0xffffffffu : ((1u << width) - 1u));
-                mask |= (uint64_t)bits << (r0 + lo - rel);
-            }
-        }
+    if (ra <= TILE_CULL_MAX_AREA) {
+        const float4 co = p.conic_o[i];
+        const float2 uv = p.xy[i];
+        mask = row_interval_mask(co, ellipse_terms(co, cull_alpha), uv.x, uv.y, rc.x & 0xffffu, rc.x >> 16,
+                                 rc.y & 0xffffu, rc.y >> 16, (float)vb.tile);
+        area[i] = (uint32_t)__popcll(mask);
     }
-    if (cnt0) {                                  // (rm is read for visible pairs only)
-        rm[i] = make_uint4(rc.x, rc.y, (uint32_t)mask, (uint32_t)(mask >> 32));
-        if (cull) area[i] = (uint32_t)__popcll(mask);
-    }
+    rm[i] = make_uint4(rc.x, rc.y, (uint32_t)mask, (uint32_t)(mask >> 32));
 }
 
 // The visible pairs' tile rectangles and tile counts in depth order (the
