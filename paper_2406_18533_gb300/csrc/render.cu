@@ -281,8 +281,8 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
             bool all_done = true;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) all_done = all_done && done[k];
-            // (two pixels per thread: the walk votes across the warp, so every lane enters it)
-            if (PPT == 2 ? !__all_sync(0xffffffffu, all_done) : !all_done) {
+            // (more than one pixel per thread: the walk votes across the warp, so every lane enters it)
+            if (PPT > 1 ? !__all_sync(0xffffffffu, all_done) : !all_done) {
                 for (int i = 0; i < n; ++i) {
                     const float4 xyc = s_xyc[i];
                     const float4 q = s_q[i];
@@ -307,11 +307,11 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
                         C2[0] += rgb.z * w;
                         T[0] = hit ? Tn : T[0];
                         nc[0] = hit ? pos1 : nc[0];
-                    } else if constexpr (PPT == 2) {
-                        // two pixels: the exponents first, then the blending
-                        // only for the pixel rows where some lane passes
-                        // (warp-uniform branches, no per-pixel ones); the
-                        // lanes leave together once every pixel is done
+                    } else {
+                        // two or four pixels: the exponents first, then the
+                        // blending only for the pixel rows where some lane
+                        // passes (warp-uniform branches, no per-pixel ones);
+                        // the lanes leave together once every pixel is done
                         float pw[PPT];
                         bool pass[PPT];
                         uint32_t rows = 0u;
@@ -322,7 +322,10 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
                             rows |= __any_sync(0xffffffffu, pass[k]) ? 1u << k : 0u;
                         }
                         if (rows == 0u) {
-                            if (__all_sync(0xffffffffu, done[0] && done[1])) break;
+                            bool fin = true;
+#pragma unroll
+                            for (int k = 0; k < PPT; ++k) fin = fin && done[k];
+                            if (__all_sync(0xffffffffu, fin)) break;
                             continue;
                         }
                         const float4 rgb = s_rgb[i];
@@ -342,43 +345,21 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
                             T[k] = hit ? Tn : T[k];
                             nc[k] = hit ? pos1 : nc[k];
                         };
-                        if (rows == 3u) {
-                            pixel(PixelK<0>{});
-                            pixel(PixelK<1>{});
-                        } else if (rows == 1u) {
-                            pixel(PixelK<0>{});
-                        } else {
-                            pixel(PixelK<1>{});
-                        }
-                    } else {
-                        float4 rgb_early;
-                        if constexpr (PPT == 4) rgb_early = s_rgb[i];    // four pixels: load ahead of the tests
-                        bool still = false;
-#pragma unroll
-                        for (int k = 0; k < PPT; ++k) {
-                            if (done[k]) continue;
-                            still = true;
-                            const float pw = power2(q, dt, __fsub_rn(ps.fy[k], xyc.y));
-                            if (!(pw >= xyc.z && pw <= 0.f)) continue;  // below the alpha cut, or power > 0
-                            const float alpha = fminf(bp.alpha_max, q.w * ex2(pw));
-                            if (alpha < bp.alpha_min) continue;
-                            const float Tn = T[k] * (1.f - alpha);
-                            if (Tn < bp.T_min) {
-                                done[k] = true;
-                                ne[k] = pos1;
-                                continue;
+                        if constexpr (PPT == 2) {
+                            if (rows == 3u) {                       // both rows: the two pixels interleave
+                                pixel(PixelK<0>{});
+                                pixel(PixelK<1>{});
+                            } else if (rows == 1u) {
+                                pixel(PixelK<0>{});
+                            } else {
+                                pixel(PixelK<1>{});
                             }
-                            float4 rgb;
-                            if constexpr (PPT == 4) rgb = rgb_early;
-                            else rgb = s_rgb[i];
-                            const float w = alpha * T[k];
-                            C0[k] += rgb.x * w;
-                            C1[k] += rgb.y * w;
-                            C2[k] += rgb.z * w;
-                            T[k] = Tn;
-                            nc[k] = pos1;
+                        } else {
+                            if (rows & 1u) pixel(PixelK<0>{});
+                            if (rows & 2u) pixel(PixelK<1>{});
+                            if (rows & 4u) pixel(PixelK<2>{});
+                            if (rows & 8u) pixel(PixelK<3>{});
                         }
-                        if (!still) break;
                     }
                 }
 #pragma unroll
