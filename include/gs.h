@@ -197,18 +197,18 @@ gs_status gs_get_status(gs_ctx *ctx, void *stream, int32_t *status, uint64_t *ne
 /* Counters of the last binning / forward / backward render (synchronises):
  * out[0] = fragments F, out[1] = (pixel, fragment) evaluations in the
  * forward, out[2] = (pixel, Gaussian) pairs blended in the backward,
- * out[3] = (pixel, list position) pairs the backward walked (out[2] and
- * out[3] only while gs_count_work is on), out[4] =
+ * out[3] = (pixel, list position) pairs the backward walked (out[1],
+ * out[2], out[3] and out[5] only while gs_count_work is on), out[4] =
  * Gaussians culled for non-finite parameters (cumulative), out[5] = the sum
  * of n_contrib over the forward's pixels (list positions the backward
  * covers, before any culling).  out holds 6 values (ABI version 2). */
 gs_status gs_get_counters(gs_ctx *ctx, void *stream, uint64_t out[6]);
 
-/* Work counting of the compositing backward (profiling aid, no paper
- * counterpart).  out[2] and out[3] of gs_get_counters are counted only while
- * it is on (on != 0); off (the default) they read 0 after each binning.
- * Counting takes about 3% of the backward's issued instructions, so timed
- * runs leave it off and count in a separate step.  Takes effect at the next
+/* Work counting of the compositing kernels (profiling aid, no paper
+ * counterpart).  out[1], out[2], out[3] and out[5] of gs_get_counters are
+ * counted only while it is on (on != 0); off (the default) they read 0 after
+ * each binning.  Counting takes a few percent of the blending kernels' issued
+ * instructions, so timed runs leave it off and count in a separate step.  Takes effect at the next
  * backward launch; a CUDA graph captured before keeps the setting it was
  * captured with. */
 gs_status gs_count_work(gs_ctx *ctx, int32_t on);

@@ -225,7 +225,7 @@ __device__ __forceinline__ void add_cost(uint32_t *cost, uint32_t tile_id, long 
 
 // The forward of one tile (tile_id, global over the batch's views) by this
 // CTA; each warp works alone, so a CTA can go on to another tile warp by warp.
-template <int TILE, int CH, int PPT>
+template <int TILE, int CH, int PPT, bool COUNT>
 __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch &vb, const ProjView &p,
                                                const uint32_t *vals, const uint2 *ranges, const BlendParams &bp,
                                                DevStatus *status, uint32_t *cost)
@@ -297,7 +297,7 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
                         const float Tn = T[0] * (1.f - a0);
                         if (hit && Tn < bp.T_min) {
                             done[0] = true;
-                            ne[0] = pos1;
+                            if constexpr (COUNT) ne[0] = pos1;
                             hit = false;
                         }
                         const float4 rgb = s_rgb[i];
@@ -336,7 +336,7 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
                             const float Tn = T[k] * (1.f - a0);
                             const bool term = hit && Tn < bp.T_min;     // would saturate: stop before it
                             done[k] = done[k] || term;
-                            ne[k] = term ? pos1 : ne[k];
+                            if constexpr (COUNT) ne[k] = term ? pos1 : ne[k];
                             hit = hit && !term;
                             const float w = hit ? a0 * T[k] : 0.f;
                             C0[k] += rgb.x * w;
@@ -364,7 +364,7 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
                 }
 #pragma unroll
                 for (int k = 0; k < PPT; ++k)
-                    if (!done[k]) ne[k] = min(base + 32, rg.y) - rg.x;
+                    if (COUNT && !done[k]) ne[k] = min(base + 32, rg.y) - rg.x;
             }
             n = 0;
             __syncwarp();
@@ -389,33 +389,35 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
         contrib += nc[k];
     }
     // (pixel, list position) evaluations until termination, and positions
-    // below n_contrib (the backward's share), for the roofline counters; each
-    // warp adds its own (no block barrier: warps finish apart)
+    // below n_contrib (the backward's share), for the roofline counters when
+    // asked; each warp adds its own (no block barrier: warps finish apart)
+    if constexpr (COUNT) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        evals += __shfl_xor_sync(0xffffffffu, evals, o);
-        contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            evals += __shfl_xor_sync(0xffffffffu, evals, o);
+            contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+        }
+        if (lane == 0 && evals) atomicAdd(&status->counters[1], (unsigned long long)evals);
+        if (lane == 0 && contrib) atomicAdd(&status->counters[5], (unsigned long long)contrib);
     }
-    if (lane == 0 && evals) atomicAdd(&status->counters[1], (unsigned long long)evals);
-    if (lane == 0 && contrib) atomicAdd(&status->counters[5], (unsigned long long)contrib);
     add_cost(cost, tile_id, t0, lane);
 }
 
 // One CTA per tile, in launch order `order` (null: index order).
-template <int TILE, int CH, int PPT>
+template <int TILE, int CH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd(ViewBatch vb, ProjView p, const uint32_t *vals,
                                                                 const uint2 *ranges, BlendParams bp,
                                                                 DevStatus *status, const uint32_t *order,
                                                                 uint32_t *cost)
 {
     const uint32_t tile_id = order ? order[blockIdx.x] : blockIdx.x;   // launch order (launch_tile_order)
-    blend_fwd_tile<TILE, CH, PPT>(tile_id, vb, p, vals, ranges, bp, status, cost);
+    blend_fwd_tile<TILE, CH, PPT, COUNT>(tile_id, vb, p, vals, ranges, bp, status, cost);
 }
 
 // Algorithm 1 schedule: CTA k blends the tiles [div[k], div[k + 1]) one after
 // another (the last range ends at the last tile), ranges of about equal
 // measured cost.
-template <int TILE, int CH, int PPT>
+template <int TILE, int CH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd_ranges(ViewBatch vb, ProjView p,
                                                                        const uint32_t *vals, const uint2 *ranges,
                                                                        BlendParams bp, DevStatus *status,
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd_ranges(ViewBatch
 {
     const uint32_t lo = div[blockIdx.x];
     const uint32_t hi = blockIdx.x + 1 < gridDim.x ? min(div[blockIdx.x + 1], vb.total_tiles) : vb.total_tiles;
-    for (uint32_t t = lo; t < hi; ++t) blend_fwd_tile<TILE, CH, PPT>(t, vb, p, vals, ranges, bp, status, cost);
+    for (uint32_t t = lo; t < hi; ++t) blend_fwd_tile<TILE, CH, PPT, COUNT>(t, vb, p, vals, ranges, bp, status, cost);
 }
 
 // Next position of a persistent CTA's work queue: thread 0 takes it from
@@ -442,7 +444,7 @@ __device__ __forceinline__ uint32_t pool_next(uint32_t *queue)
 // Persistent pool: a CTA per resident slot pulls the next tile of `order`
 // (the previous step's measured costs, heaviest first; null: index order)
 // from the queue counter until every tile is taken.
-template <int TILE, int CH, int PPT>
+template <int TILE, int CH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd_pool(ViewBatch vb, ProjView p,
                                                                      const uint32_t *vals, const uint2 *ranges,
                                                                      BlendParams bp, DevStatus *status,
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) k_blend_fwd_pool(ViewBatch v
                                                                      uint32_t *cost)
 {
     for (uint32_t t = pool_next(queue); t < vb.total_tiles; t = pool_next(queue))
-        blend_fwd_tile<TILE, CH, PPT>(order ? order[t] : t, vb, p, vals, ranges, bp, status, cost);
+        blend_fwd_tile<TILE, CH, PPT, COUNT>(order ? order[t] : t, vb, p, vals, ranges, bp, status, cost);
 }
 
 // With 2 pixels per thread the backward is held to 64 registers (8 CTAs of
@@ -758,24 +760,36 @@ struct Sched {
     uint32_t *queue;
 };
 
+template <int TILE, int CH, int PPT, bool COUNT>
+void fwd_launch_counting(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
+                const BlendParams &bp, DevStatus *status, const Sched &sc, cudaStream_t st)
+{
+    constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
+    static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH, PPT, COUNT>, sm) &&
+                           smem_opt_in(k_blend_fwd_ranges<TILE, CH, PPT, COUNT>, sm) &&
+                           smem_opt_in(k_blend_fwd_pool<TILE, CH, PPT, COUNT>, sm);
+    (void)ok;
+    if (sc.queue)
+        k_blend_fwd_pool<TILE, CH, PPT, COUNT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
+                                                                              sc.order, sc.queue, sc.cost);
+    else if (sc.div)
+        k_blend_fwd_ranges<TILE, CH, PPT, COUNT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
+                                                                                sc.div, sc.cost);
+    else
+        k_blend_fwd<TILE, CH, PPT, COUNT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
+                                                                                 sc.order, sc.cost);
+}
+
+// The forward's counts (evaluations until termination, list positions below
+// n_contrib) are taken only when asked (bp.count_work), like the backward's.
 template <int TILE, int CH, int PPT>
 void fwd_launch(const ViewBatch &vb, const ProjView &p, const uint32_t *vals, const uint2 *ranges,
                 const BlendParams &bp, DevStatus *status, const Sched &sc, cudaStream_t st)
 {
-    constexpr size_t sm = smem_bytes<TILE, CH, PPT>();
-    static const bool ok = smem_opt_in(k_blend_fwd<TILE, CH, PPT>, sm) &&
-                           smem_opt_in(k_blend_fwd_ranges<TILE, CH, PPT>, sm) &&
-                           smem_opt_in(k_blend_fwd_pool<TILE, CH, PPT>, sm);
-    (void)ok;
-    if (sc.queue)
-        k_blend_fwd_pool<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
-                                                                              sc.order, sc.queue, sc.cost);
-    else if (sc.div)
-        k_blend_fwd_ranges<TILE, CH, PPT><<<sc.ctas, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
-                                                                                sc.div, sc.cost);
+    if (bp.count_work)
+        fwd_launch_counting<TILE, CH, PPT, true>(vb, p, vals, ranges, bp, status, sc, st);
     else
-        k_blend_fwd<TILE, CH, PPT><<<vb.total_tiles, TILE * TILE / PPT, sm, st>>>(vb, p, vals, ranges, bp, status,
-                                                                                 sc.order, sc.cost);
+        fwd_launch_counting<TILE, CH, PPT, false>(vb, p, vals, ranges, bp, status, sc, st);
 }
 
 template <int TILE, int CH, int PPT, bool COUNT>
@@ -832,8 +846,8 @@ uint32_t resident_ctas()
             e = POOL ? occupancy(&per_sm, k_blend_bwd_pool<TILE, CH, PPT, false>, threads, sm)
                      : occupancy(&per_sm, k_blend_bwd_ranges<TILE, CH, PPT, false>, threads, sm);
         else
-            e = POOL ? occupancy(&per_sm, k_blend_fwd_pool<TILE, CH, PPT>, threads, sm)
-                     : occupancy(&per_sm, k_blend_fwd_ranges<TILE, CH, PPT>, threads, sm);
+            e = POOL ? occupancy(&per_sm, k_blend_fwd_pool<TILE, CH, PPT, false>, threads, sm)
+                     : occupancy(&per_sm, k_blend_fwd_ranges<TILE, CH, PPT, false>, threads, sm);
         if (e != cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;

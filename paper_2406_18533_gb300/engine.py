@@ -369,8 +369,9 @@ class Context:
         return int(code.value), int(needed.value)
 
     def count_work(self, on: bool = True):
-        """Counts the backward's walked and blended pairs from the next step on
-        (off by default: counting costs issue slots in the backward)."""
+        """Counts the blending kernels' work (forward evaluations and
+        contributing positions, backward walked and blended pairs) from the
+        next step on (off by default: counting costs issue slots)."""
         self._c("gs_count_work", self.h, int(bool(on)))
 
     def counters(self):
