@@ -65,11 +65,25 @@ __device__ __forceinline__ float4 stage_q(const float4 &co)
     return make_float4(-0.5f * LOG2E * co.x, -LOG2E * co.y, -0.5f * LOG2E * co.z, co.w);
 }
 
-// Below this exponent o * 2^pw < alpha_min: the exponential need not be taken.
-// Forward and backward use the same cut, so their decisions agree exactly.
+// The exponents worth an exponential lie in [cut, 0] (below cut, o * 2^pw <
+// alpha_min; above 0, the pixel is off the Gaussian's quadratic form).  The
+// staged record keeps the interval's midpoint m = cut / 2 (exact), so that one
+// subtraction and one comparison, |pw - m| <= -m, test both ends.  Forward and
+// backward use the same test, so their decisions agree exactly.
+__device__ __forceinline__ float exponent_mid(float o, float alpha_min);
+__device__ __forceinline__ bool in_cut(float pw, float mid)
+{
+    return fabsf(__fsub_rn(pw, mid)) <= -mid;
+}
+
 __device__ __forceinline__ float exponent_cut(float o, float alpha_min)
 {
     return o > alpha_min ? __log2f(__fdividef(alpha_min, o)) : 1.f;
+}
+
+__device__ __forceinline__ float exponent_mid(float o, float alpha_min)
+{
+    return 0.5f * exponent_cut(o, alpha_min);
 }
 
 // The tile's [start, end) in the fragment list.  A reversed range (the
@@ -233,7 +247,7 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
     constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4 *s_xyc = smem + warp * CH;              // u, v, exponent cut, list position + 1 (bits)
+    float4 *s_xyc = smem + warp * CH;              // u, v, exponent_mid, list position + 1 (bits)
     float4 *s_q = smem + (NW + warp) * CH;         // A, B, C, opacity
     float4 *s_rgb = smem + (2 * NW + warp) * CH;
     const long long t0 = cost ? clock64() : 0ll;
@@ -270,7 +284,7 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
         if (hit) {
             const int slot = n + __popc(bal & lt);
             const float4 q = stage_q(e.co);
-            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_cut(q.w, bp.alpha_min), __uint_as_float(j - rg.x + 1u));
+            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_mid(q.w, bp.alpha_min), __uint_as_float(j - rg.x + 1u));
             s_q[slot] = q;
             s_rgb[slot] = p.rgb_d[vbase + e.g];
         }
@@ -293,7 +307,7 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
                         if (done[0]) break;
                         const float pw = power2(q, dt, __fsub_rn(ps.fy[0], xyc.y));
                         const float a0 = fminf(bp.alpha_max, q.w * ex2(pw));
-                        bool hit = pw >= xyc.z && pw <= 0.f && a0 >= bp.alpha_min;
+                        bool hit = in_cut(pw, xyc.z) && a0 >= bp.alpha_min;
                         const float Tn = T[0] * (1.f - a0);
                         if (hit && Tn < bp.T_min) {
                             done[0] = true;
@@ -318,7 +332,7 @@ __device__ __forceinline__ void blend_fwd_tile(uint32_t tile_id, const ViewBatch
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
                             pw[k] = power2(q, dt, __fsub_rn(ps.fy[k], xyc.y));
-                            pass[k] = !done[k] && pw[k] >= xyc.z && pw[k] <= 0.f;
+                            pass[k] = !done[k] && in_cut(pw[k], xyc.z);
                             rows |= __any_sync(0xffffffffu, pass[k]) ? 1u << k : 0u;
                         }
                         if (rows == 0u) {
@@ -466,7 +480,7 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
     constexpr int NW = TILE * TILE / (32 * PPT);
     extern __shared__ float4 smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4 *s_xyc = smem + warp * CH;                // u, v, exponent cut, list position (bits)
+    float4 *s_xyc = smem + warp * CH;                // u, v, exponent_mid, list position (bits)
     float4 *s_q = smem + (NW + warp) * CH;
     float4 *s_rgb = smem + (2 * NW + warp) * CH;    // r, g, b, Gaussian index (bits)
     const long long t0 = cost ? clock64() : 0ll;
@@ -524,7 +538,7 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
             const int slot = n + __popc(bal & lt);
             const float4 q = stage_q(e.co);
             const float4 rgbd = p.rgb_d[vbase + e.g];
-            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_cut(q.w, bp.alpha_min),
+            s_xyc[slot] = make_float4(e.xy.x, e.xy.y, exponent_mid(q.w, bp.alpha_min),
                                       __uint_as_float((uint32_t)(j - rg.x)));
             s_q[slot] = q;
             s_rgb[slot] = make_float4(rgbd.x, rgbd.y, rgbd.z, __uint_as_float(e.g));
@@ -557,7 +571,7 @@ __device__ __forceinline__ void blend_bwd_tile(uint32_t tile_id, const ViewBatch
                 if constexpr (COUNT) walked += walk;
                 dy[k] = __fsub_rn(ps.fy[k], xyc.y);
                 pw[k] = power2(q, dt, dy[k]);
-                pass[k] = walk && pw[k] >= xyc.z && pw[k] <= 0.f;
+                pass[k] = walk && in_cut(pw[k], xyc.z);
                 rows |= __any_sync(0xffffffffu, pass[k]) ? 1u << k : 0u;
             }
             if (rows == 0u) continue;
