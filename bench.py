@@ -304,7 +304,10 @@ def stage_roofline(stage, ms, counters, N, Bv, pixels, passes, peaks, clock_mhz,
     if stage == "sort":
         byt = passes * F * 24.0
     elif stage == "adam":
-        byt = 59 * 28.0 * N
+        # dense: every Gaussian; visible-only: the rows of the Gaussians some
+        # view sees, plus the one-byte mask of all of them
+        vis = counters.get("visible_gaussians")
+        byt = 59 * 28.0 * N if vis is None else 59 * 28.0 * vis + N
     elif stage == "preprocess":
         byt = N * 240.0 + Bv * N * 52.0
     elif stage == "preprocess_bwd":
@@ -447,13 +450,20 @@ def run_ours(args, rank, world, local_rank):
     binding.call("gs_trace_read", ctx.h, buf, ctypes.byref(nst), ctx=ctx.h)
     binding.call("gs_trace_enable", ctx.h, 0, ctx=ctx.h)
     arr = np.frombuffer(buf, dtype=np.float32).reshape(nstep_tr, binding.GS_TRACE_STAGES)[:nst.value]
-    stage_ms = {s: float(arr[:, i].mean()) for i, s in enumerate(binding.TRACE_STAGES)}
+    # median over the traced steps: a step whose host launches fell behind
+    # the GPU shows the gap in one stage, and the median leaves it out
+    stage_ms = {s: float(np.median(arr[:, i])) for i, s in enumerate(binding.TRACE_STAGES)}
     # the backward's work counters (walked and blended pairs) from one more
     # step with counting on; the timed and traced steps ran without it
     ctx.count_work(True)
     train_once()
     counters = ctx.counters()
     ctx.count_work(False)
+    if args.sparse_adam:
+        # Gaussians some view of the batch sees: the rows visible-only Adam touches
+        pr = ctx.preprocess(P, cams)
+        counters["visible_gaussians"] = int((pr.radius > 0).any(dim=0).sum().item())
+        del pr
 
     # per-view: the same scene stepped one view at a time over the same views
     per_view = None
