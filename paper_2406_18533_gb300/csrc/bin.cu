@@ -207,90 +207,6 @@ __global__ void __launch_bounds__(256) k_pair_compact(int64_t n, const float4 *r
     }
 }
 
-// Culls footprint tiles against the alpha >= cull_alpha ellipse, one pair
-// per thread, in pair index order (coalesced reads).  With f(d) = a dx^2 +
-// 2 b dx dy + c dy^2 the ellipse is f <= L (L = the widened threshold of
-// ellipse_terms).  Per tile row, the pixel-centre rows of the row give a band
-// dy in [dy0, dy1]; the ellipse meets the band where |dy| <= Y = sqrt(a L /
-// det), and there its x-range is the interval between
-//   xl(dy) = (-b dy - sqrt(a L - det dy^2)) / a  and
-//   xr(dy) = (-b dy + sqrt(a L - det dy^2)) / a.
-// xr is concave in dy with its maximum at dy_r = -b sqrt(L / (c det)) (the
-// ellipse's rightmost point) and xl convex with its minimum at -dy_r, so the
-// band's x-range is [xl(clamp(-dy_r)), xr(clamp(dy_r))], each clamped into the
-// band.  A tile of the row is kept when its pixel-centre columns meet that
-// range.  This is the box test of ellipse_box_hits done once per tile row
-// instead of once per tile; the band limits, the range and Y are widened by
-// 1e-3 relative plus 1e-2 pixel, above the rounding of the square roots and
-// divisions (the threshold L already carries ellipse_terms' margin), so a
-// tile is never dropped where the per-pixel test could blend.
-// rm[i] = (rectangle words, kept-tile bits low, high); larger rectangles and
-// pairs not culled keep all bits.  area[i] becomes the kept count (0 drops
-// the pair from the binning).  Pairs with area[i] = 0 (not visible) are
-// skipped.
-// sqrt(x) for x >= 0 from the approximate reciprocal square root (0 at 0).
-__device__ __forceinline__ float sqrt_approx(float x)
-{
-    return x > 0.f ? x * rsqrtf(x) : 0.f;
-}
-
-__device__ __forceinline__ uint64_t row_interval_mask(const float4 &co, const float4 &te, float u, float v,
-                                                      uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1, float T)
-{
-    if (!(te.x >= 0.f)) return 0ull;                     // alpha never reaches the cut
-    const uint32_t w = x1 - x0 + 1u;
-    const uint32_t ra = w * (y1 - y0 + 1u);
-    const uint64_t all = ra >= 64u ? ~0ull : ((1ull << ra) - 1ull);
-    if (te.x == INFINITY) return all;                     // not positive definite: keep every tile
-    const float a = co.x, b = co.y, L = te.x, det = te.w;
-    constexpr float REL = 1e-3f, ABS = 1e-2f;
-    const float aL = a * L;
-    const float Y = sqrt_approx(__fdividef(aL, det)) * (1.f + REL) + ABS;   // |dy| reach of the ellipse
-    const float dyr = -b * sqrt_approx(L * te.z / det);                       // dy of the rightmost point (te.z = 1/c)
-    const float ia = te.y;                                                     // 1/a
-    const float iT = 1.f / T;                                                  // exact: T is a power of two
-    uint64_t mask = 0ull;
-    for (uint32_t ty = y0; ty <= y1; ++ty) {
-        const float py0 = (float)ty * T + 0.5f - v;               // the row's pixel-centre dy range
-        const float lo = fmaxf(py0 - ABS, -Y), hi = fminf(py0 + (T - 1.f) + ABS, Y);
-        if (!(lo <= hi)) continue;
-        const float dr = fminf(fmaxf(dyr, lo), hi), dl = fminf(fmaxf(-dyr, lo), hi);
-        const float sr = sqrt_approx(aL - det * dr * dr), sl = sqrt_approx(aL - det * dl * dl);
-        float xr = (sr - b * dr) * ia, xl = -(sl + b * dl) * ia;
-        const float m = (xr - xl) * REL + ABS;
-        xr = u + xr + m;
-        xl = u + xl - m;
-        // tiles whose pixel-centre columns [tx T + 0.5, tx T + T - 0.5] meet [xl, xr]
-        const float fl = ceilf((xl - (T - 0.5f)) * iT), fh = floorf((xr - 0.5f) * iT);
-        const int tl = (int)fmaxf(fl, (float)x0), th = (int)fminf(fh, (float)x1);
-        if (tl > th) continue;
-        const uint32_t s = (ty - y0) * w + ((uint32_t)tl - x0), len = (uint32_t)(th - tl) + 1u;
-        mask |= (~0ull >> (64u - len)) << s;
-    }
-    return mask & all;
-}
-
-__global__ void __launch_bounds__(256) k_cull_tiles(ViewBatch vb, ProjView p, const uint2 *rect, uint32_t *area,
-                                                    float cull_alpha, uint4 *rm)
-{
-    const int64_t n = (int64_t)vb.B * p.N;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t cnt0 = area[i];                       // 0: not visible, nothing to do
-    if (!cnt0) return;
-    const uint2 rc = rect[i];
-    const uint32_t ra = rect_area(rc);
-    uint64_t mask = ~0ull;
-    if (ra <= TILE_CULL_MAX_AREA) {
-        const float4 co = p.conic_o[i];
-        const float2 uv = p.xy[i];
-        mask = row_interval_mask(co, ellipse_terms(co, cull_alpha), uv.x, uv.y, rc.x & 0xffffu, rc.x >> 16,
-                                 rc.y & 0xffffu, rc.y >> 16, (float)vb.tile);
-        area[i] = (uint32_t)__popcll(mask);
-    }
-    rm[i] = make_uint4(rc.x, rc.y, (uint32_t)mask, (uint32_t)(mask >> 32));
-}
-
 // The visible pairs' tile rectangles and tile counts in depth order (the
 // counts are the input of the offsets scan), so that the emission reads
 // everything in order; with culling (rm non-null) one 16-byte random read per
@@ -957,14 +873,6 @@ uint32_t *launch_depth_order(const ViewBatch &vb, const ProjView &p, bool rect_r
     return order;                                 // four passes: back in the first buffers
 }
 
-void launch_cull_tiles(const ViewBatch &vb, const ProjView &p, const uint2 *rect, uint32_t *area, float cull_alpha,
-                       uint4 *rm, cudaStream_t st)
-{
-    const int64_t n = (int64_t)vb.B * p.N;
-    if (n <= 0) return;
-    k_cull_tiles<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vb, p, rect, area, cull_alpha, rm);
-    count_launches(1);
-}
 
 void launch_gather_counts(const uint32_t *order, const uint2 *rect, const uint32_t *area, const uint4 *rm, int64_t n,
                           const uint32_t *n_vis, uint32_t *counts, uint32_t *rx, uint32_t *ry, uint2 *keep,

@@ -304,11 +304,11 @@ gs_status run_binning(gs_ctx *c, const ViewBatch &vb, const ProjView &p, bool re
     uint32_t *pk = ptr<uint32_t>(c->pk), *pv = ptr<uint32_t>(c->pv), *pk_alt = ptr<uint32_t>(c->pk_alt);
     uint2 *rect = ptr<uint2>(c->rect);
     uint32_t *tk = ptr<uint32_t>(c->keys), *tk_alt = ptr<uint32_t>(c->keys_alt), *v_alt = ptr<uint32_t>(c->vals_alt);
-    // a training step culls footprint tiles against the alpha ellipse; gs_bin keeps whole rectangles
+    // a training step or a render culled footprint tiles against the alpha
+    // ellipse in the transformation kernel (rect_ready); gs_bin keeps whole rectangles
     const float cull_alpha = rect_ready ? c->hp.alpha_min : 0.f;
     uint4 *rm = cull_alpha > 0.f ? ptr<uint4>(c->rmask) : nullptr;
     uint2 *keep = ptr<uint2>(c->kmask);
-    if (rm) launch_cull_tiles(vb, p, rect, ptr<uint32_t>(c->ntiles), cull_alpha, rm, st);
     // (1) the visible (view, Gaussian) pairs in depth order
     uint32_t *order = launch_depth_order(vb, p, rect_ready, rect, ptr<uint32_t>(c->ntiles), pk, pv, pk_alt,
                                          ptr<uint32_t>(c->pv_alt), ptr<uint32_t>(c->offsets), n_vis, total,
@@ -980,7 +980,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
     c->trace_on = c->trace_max > 0 && c->trace_step < c->trace_max;
     mark(c, st, 0);
     launch_preprocess_fwd(sv, vb, pv, ptr<uint32_t>(c->ntiles), ptr<uint2>(c->rect), c->status,
-                          c->hp.strict_nonfinite, st);
+                          c->hp.strict_nonfinite, st, ptr<uint4>(c->rmask), c->hp.alpha_min);
     mark(c, st, 1);
     if (c->frag_cap == 0) {
         // first call on this context: size the fragment buffers from an exact count
@@ -989,7 +989,7 @@ gs_status gs_train_step(gs_ctx *c, gs_scene *p, gs_scene *g, gs_scene *m, gs_sce
                               ptr<unsigned long long>(c->total), c->scan_tmp.p, st);
         uint64_t F = 0;
         if ((r = read_total(c, st, &F)) != GS_OK) return r;
-        uint64_t cap = F + F / 4 + 4096;
+        uint64_t cap = 2 * F + 4096;   // the culled count; growth during training stays inside
         if (cap > GS_MAX_FRAGMENTS) cap = GS_MAX_FRAGMENTS;
         c->frag_cap = cap;
         if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;
@@ -1080,14 +1080,14 @@ gs_status gs_render(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int
     gs_proj pr{ptr<float>(c->xy), ptr<float>(c->conic_o), ptr<float>(c->rgb_d), ptr<int32_t>(c->radius), N, B, 0};
     const ProjView pv = proj_of(&pr);
     launch_preprocess_fwd(view_of(scene), vb, pv, ptr<uint32_t>(c->ntiles), ptr<uint2>(c->rect), c->status,
-                          c->hp.strict_nonfinite, st);
+                          c->hp.strict_nonfinite, st, ptr<uint4>(c->rmask), c->hp.alpha_min);
     if (c->frag_cap == 0) {
         if ((r = ensure(c, c->scan_tmp, scan_temp_bytes(n))) || (r = ensure(c, c->total, 64))) return r;
         launch_exclusive_scan(ptr<uint32_t>(c->ntiles), ptr<uint32_t>(c->offsets), n,
                               ptr<unsigned long long>(c->total), c->scan_tmp.p, st);
         uint64_t F = 0;
         if ((r = read_total(c, st, &F)) != GS_OK) return r;
-        uint64_t cap = F + F / 4 + 4096;
+        uint64_t cap = 2 * F + 4096;   // the culled count; growth during training stays inside
         if (cap > GS_MAX_FRAGMENTS) cap = GS_MAX_FRAGMENTS;
         c->frag_cap = cap;
         if ((r = ensure_iter(c, N, vb, c->frag_cap)) != GS_OK) return r;

@@ -106,8 +106,13 @@ void count_launches(int n);
 // Launchers (all asynchronous on `st`).
 // ntiles[i]: tiles covered by pair i; rect[i] (optional): its packed tile
 // rectangle (pack_rect, the same arithmetic as the binning's).
+// rm (optional, with rect): also cull each pair's rectangle against the
+// alpha >= cull_alpha ellipse (row_interval_mask, rectangles of at most
+// TILE_CULL_MAX_AREA tiles): rm[i] = (rectangle words, kept-tile bits low,
+// high) for every pair with tiles, and ntiles[i] = the kept count.
 void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, uint32_t *ntiles,
-                           uint2 *rect, DevStatus *status, int strict, cudaStream_t st);
+                           uint2 *rect, DevStatus *status, int strict, cudaStream_t st, uint4 *rm = nullptr,
+                           float cull_alpha = 0.f);
 // g holds the blending backward's moments (GradView) unless grads_ready.
 // vis (optional): vis[g] = 1 if some view has the Gaussian's radius > 0,
 // else 0; with vis the rows of unseen Gaussians are not written.
@@ -193,6 +198,68 @@ __device__ __forceinline__ bool ellipse_box_hits(const float4 &co, float u, floa
 // rectangle); larger ones keep every tile.
 constexpr uint32_t TILE_CULL_MAX_AREA = 64;
 
+// Tiles of a footprint rectangle culled against the alpha >= cull_alpha
+// ellipse (the transformation kernel does it per pair in a training step or
+// a render).  With f(d) = a dx^2 +
+// 2 b dx dy + c dy^2 the ellipse is f <= L (L = the widened threshold of
+// ellipse_terms).  Per tile row, the pixel-centre rows of the row give a band
+// dy in [dy0, dy1]; the ellipse meets the band where |dy| <= Y = sqrt(a L /
+// det), and there its x-range is the interval between
+//   xl(dy) = (-b dy - sqrt(a L - det dy^2)) / a  and
+//   xr(dy) = (-b dy + sqrt(a L - det dy^2)) / a.
+// xr is concave in dy with its maximum at dy_r = -b sqrt(L / (c det)) (the
+// ellipse's rightmost point) and xl convex with its minimum at -dy_r, so the
+// band's x-range is [xl(clamp(-dy_r)), xr(clamp(dy_r))], each clamped into the
+// band.  A tile of the row is kept when its pixel-centre columns meet that
+// range.  This is the box test of ellipse_box_hits done once per tile row
+// instead of once per tile; the band limits, the range and Y are widened by
+// 1e-3 relative plus 1e-2 pixel, above the rounding of the square roots and
+// divisions (the threshold L already carries ellipse_terms' margin), so a
+// tile is never dropped where the per-pixel test could blend.
+// Returns the kept-tile bits (row-major in the rectangle [x0, x1] x [y0, y1]
+// of tiles of edge T; at most TILE_CULL_MAX_AREA tiles).
+// sqrt(x) for x >= 0 from the approximate reciprocal square root (0 at 0).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    return x > 0.f ? x * rsqrtf(x) : 0.f;
+}
+
+__device__ __forceinline__ uint64_t row_interval_mask(const float4 &co, const float4 &te, float u, float v,
+                                                      uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1, float T)
+{
+    if (!(te.x >= 0.f)) return 0ull;                     // alpha never reaches the cut
+    const uint32_t w = x1 - x0 + 1u;
+    const uint32_t ra = w * (y1 - y0 + 1u);
+    const uint64_t all = ra >= 64u ? ~0ull : ((1ull << ra) - 1ull);
+    if (te.x == INFINITY) return all;                     // not positive definite: keep every tile
+    const float a = co.x, b = co.y, L = te.x, det = te.w;
+    constexpr float REL = 1e-3f, ABS = 1e-2f;
+    const float aL = a * L;
+    const float Y = sqrt_approx(__fdividef(aL, det)) * (1.f + REL) + ABS;   // |dy| reach of the ellipse
+    const float dyr = -b * sqrt_approx(L * te.z / det);                       // dy of the rightmost point (te.z = 1/c)
+    const float ia = te.y;                                                     // 1/a
+    const float iT = 1.f / T;                                                  // exact: T is a power of two
+    uint64_t mask = 0ull;
+    for (uint32_t ty = y0; ty <= y1; ++ty) {
+        const float py0 = (float)ty * T + 0.5f - v;               // the row's pixel-centre dy range
+        const float lo = fmaxf(py0 - ABS, -Y), hi = fminf(py0 + (T - 1.f) + ABS, Y);
+        if (!(lo <= hi)) continue;
+        const float dr = fminf(fmaxf(dyr, lo), hi), dl = fminf(fmaxf(-dyr, lo), hi);
+        const float sr = sqrt_approx(aL - det * dr * dr), sl = sqrt_approx(aL - det * dl * dl);
+        float xr = (sr - b * dr) * ia, xl = -(sl + b * dl) * ia;
+        const float m = (xr - xl) * REL + ABS;
+        xr = u + xr + m;
+        xl = u + xl - m;
+        // tiles whose pixel-centre columns [tx T + 0.5, tx T + T - 0.5] meet [xl, xr]
+        const float fl = ceilf((xl - (T - 0.5f)) * iT), fh = floorf((xr - 0.5f) * iT);
+        const int tl = (int)fmaxf(fl, (float)x0), th = (int)fminf(fh, (float)x1);
+        if (tl > th) continue;
+        const uint32_t s = (ty - y0) * w + ((uint32_t)tl - x0), len = (uint32_t)(th - tl) + 1u;
+        mask |= (~0ull >> (64u - len)) << s;
+    }
+    return mask & all;
+}
+
 // A footprint's tile rectangle packed as {x0 | x1 << 16, y0 | y1 << 16}
 // (tile coordinates fit 16 bits); (1, 0) is the empty rectangle.
 __host__ __device__ __forceinline__ uint2 pack_rect(uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1)
@@ -218,12 +285,6 @@ uint32_t *launch_depth_order(const ViewBatch &vb, const ProjView &p, bool rect_r
                              uint32_t *keys, uint32_t *order, uint32_t *keys_alt, uint32_t *order_alt,
                              uint32_t *pos, uint32_t *n_vis, unsigned long long *total, void *scan_tmp,
                              void *sort_tmp, DevStatus *status, cudaStream_t st);
-// Training steps cull footprint tiles against the alpha >= cull_alpha ellipse
-// (rectangles of at most TILE_CULL_MAX_AREA tiles; ellipse_box_hits on each
-// tile's pixel-centre box): rm[i] = (rectangle words, kept-tile bits, row-major
-// in the rectangle), area[i] = the kept count.
-void launch_cull_tiles(const ViewBatch &vb, const ProjView &p, const uint2 *rect, uint32_t *area, float cull_alpha,
-                       uint4 *rm, cudaStream_t st);
 // For pair order[j], j < *n_vis: rx / ry its rectangle words and counts its
 // tile count; with rm (culled) also keep[j] = its kept-tile bits, else counts
 // come from area[].

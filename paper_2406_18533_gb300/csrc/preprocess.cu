@@ -200,7 +200,8 @@ __device__ __forceinline__ float view_depth(const ViewCam &c, float x, float y, 
 // the latency of the scattered per-view stores better (measured: C3 5.0 ->
 // 4.3 ms).
 __global__ void __launch_bounds__(128, 6) k_preprocess_fwd(SceneView s, ViewBatch vb, ProjView p, uint32_t *ntiles,
-                                                        uint2 *rect, DevStatus *status, int strict)
+                                                        uint2 *rect, DevStatus *status, int strict, uint4 *rm,
+                                                        float cull_alpha)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= s.N) return;
@@ -289,9 +290,19 @@ __global__ void __launch_bounds__(128, 6) k_preprocess_fwd(SceneView s, ViewBatc
                             if (k < nk) acc += shf[3 * k + ch] * Y[k];
                         rgb[ch] = fmaxf(acc + 0.5f, 0.f);
                     }
+                    const float4 co = make_float4(Cc * idet, -Bc * idet, A * idet, G.o);
                     p.xy[idx] = make_float2(u, vv);
-                    p.conic_o[idx] = make_float4(Cc * idet, -Bc * idet, A * idet, G.o);
+                    p.conic_o[idx] = co;
                     p.rgb_d[idx] = make_float4(rgb[0], rgb[1], rgb[2], pz);
+                    if (rm) {                      // cull the rectangle's tiles against the alpha ellipse
+                        uint64_t keep = ~0ull;
+                        if (area <= TILE_CULL_MAX_AREA) {
+                            keep = row_interval_mask(co, ellipse_terms(co, cull_alpha), u, vv, (uint32_t)x0,
+                                                     (uint32_t)x1, (uint32_t)y0, (uint32_t)y1, (float)vb.tile);
+                            area = (uint32_t)__popcll(keep);
+                        }
+                        rm[idx] = make_uint4(rc.x, rc.y, (uint32_t)keep, (uint32_t)(keep >> 32));
+                    }
                 }
             }
         }
@@ -544,12 +555,13 @@ __global__ void __launch_bounds__(128, 4) k_preprocess_bwd(SceneView s, ViewBatc
 }  // namespace
 
 void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, uint32_t *ntiles,
-                           uint2 *rect, DevStatus *status, int strict, cudaStream_t st)
+                           uint2 *rect, DevStatus *status, int strict, cudaStream_t st, uint4 *rm, float cull_alpha)
 {
     if (s.N == 0) return;
     const int threads = 128;
     const int64_t blocks = (s.N + threads - 1) / threads;
-    k_preprocess_fwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, ntiles, rect, status, strict);
+    k_preprocess_fwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, ntiles, rect, status, strict,
+                                                           rect ? rm : nullptr, cull_alpha);
     count_launches(1);
 }
 
