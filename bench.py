@@ -261,11 +261,11 @@ def run_reference(args, rank):
 # DRAM bytes (read + write) of one k_blend_bwd launch per walked (pixel, list
 # position) pair, from an ncu capture of the kernel on a C2-shaped case (4M
 # Gaussians in Morton storage order, 2 of the 16 views at 1080p, tile 16, 64
-# entries, 2 pixels per thread; summary under profiles/): 1.750 GB over
+# entries, 2 pixels per thread; summary under profiles/): 1.741 GB over
 # 843.81M walked pairs.  Per-view records, per-view gradient accumulators and
 # walked pairs all grow with the views, so a launch's traffic is taken as
 # this times its walked count.
-BLEND_BWD_DRAM_BYTES_PER_WALKED = 2.07
+BLEND_BWD_DRAM_BYTES_PER_WALKED = 2.06
 
 
 def stage_traffic(stage, counters):
