@@ -12,10 +12,16 @@
 // preserved), and walks the buffer when another round could overflow it.  So
 // a warp spends nothing on list entries that cannot reach its pixels, and
 // finishes as soon as its own pixels do (no block-wide barrier at all).  The staged record holds
-// the exponent below which alpha < alpha_min, so most (pixel, Gaussian) pairs
-// are rejected before the exponential.
-// Forward: a lane stops once its pixel saturates; the warp stops refilling
-// when all its lanes have (early termination on transmittance).
+// the midpoint of the exponent interval [cut, 0] outside which alpha <
+// alpha_min (or the pixel is off the quadratic form), so most (pixel,
+// Gaussian) pairs are rejected before the exponential.
+// With more than one pixel per thread, a lane's k-th pixels form row k of
+// the warp's block: for each staged entry both passes evaluate every pixel's
+// exponent, vote per row whether any lane passes, and run the blending
+// arithmetic only for those rows, without per-pixel branches (a pixel that
+// does not blend takes alpha 0 or weight 0).
+// Forward: a pixel stops once it would saturate; the warp stops refilling
+// when all its pixels have (early termination on transmittance).
 // Backward: each warp walks back to front from its own largest n_contrib,
 // recovers the transmittance before each contributor by division from
 // T_final (no per-fragment state is stored), accumulates per Gaussian the
