@@ -292,11 +292,65 @@ __device__ __forceinline__ uint32_t select_bit64(uint32_t lo, uint32_t hi, uint3
 // Emits the fragments of pair order[j] at offsets[j]: key = global tile id,
 // value = Gaussian index.  Visiting the pairs in depth order puts every
 // tile's fragments in (depth, index) order, so a stable sort on the tile id
-// alone finishes the job.  A warp expands its 32 pairs together: output slot
-// f of the warp's range goes to lane f mod 32, which finds its pair by binary
-// search over the lanes' offsets, so consecutive lanes store consecutive
-// addresses.  Thread 0 publishes F (status, count_out); nothing is written
-// past capacity.
+// alone finishes the job.  The work is split by output slots, not by pairs:
+// warp w writes fragments [w S, (w + 1) S) (S = EMIT_SLOTS).  It finds the
+// pair holding its first slot by a 32-way search of the offsets, then keeps
+// a window of 32 consecutive pairs (lane l holds pair p + l) and writes 32
+// slots per round, slot f by lane f mod 32 (coalesced stores), each lane
+// finding its slot's pair in the window by binary search over the lanes'
+// offsets; the window moves on when a round runs past it.  Since every pair
+// in the depth order has at least one fragment, a window that starts at the
+// pair holding a round's first slot covers the round; a slot past the window
+// (only after a failed pair sort) is looked up in the offsets directly.  A
+// pair that covers many tiles (a large Gaussian near a camera) is thus
+// shared by many warps instead of holding up one.  Thread 0 publishes F
+// (status, count_out); nothing is written past capacity.
+constexpr uint32_t EMIT_SLOTS = 512;
+
+// One pair of the depth order, as a lane of the emission window sees it.
+struct EmitPair {
+    uint32_t start, count, corner, wdt, tx_row, g, mlo, mhi;
+};
+
+__device__ __forceinline__ EmitPair emit_pair(const ViewBatch &vb, int64_t N, int64_t nb, int64_t n, int64_t p,
+                                              const uint32_t *order, const uint32_t *rx, const uint32_t *ry,
+                                              const uint2 *keep, const uint32_t *offsets, uint32_t F,
+                                              float cull_alpha)
+{
+    EmitPair e{F, 0u, 0u, 1u, 0u, 0u, 0xffffffffu, 0xffffffffu};
+    if (p < 0 || p >= n) return e;
+    e.start = offsets[p];
+    const int64_t i = (int64_t)order[p];
+    const uint2 rc = make_uint2(rx[p], ry[p]);
+    uint32_t area = rect_area(rc);
+    if (area && i < nb) {                        // i >= B * N only after a failed (timed-out) pair sort
+        const int v = (int)(i / N);
+        e.g = (uint32_t)(i - (int64_t)v * N);
+        const uint32_t x0 = rc.x & 0xffffu;
+        e.wdt = (rc.x >> 16) - x0 + 1u;
+        e.tx_row = (uint32_t)vb.v[v].TX;
+        e.corner = vb.v[v].tile_base + (rc.y & 0xffffu) * e.tx_row + x0;   // tile (x0, y0)
+        if (cull_alpha > 0.f && area <= TILE_CULL_MAX_AREA) {
+            const uint2 k = keep[p];
+            e.mlo = k.x;
+            e.mhi = k.y;
+        }
+    } else {
+        area = 0u;
+    }
+    // a whole rectangle (mask all ones) or the set bits of a culled one's mask
+    e.count = (e.mlo & e.mhi) == 0xffffffffu ? area : (uint32_t)(__popc(e.mlo) + __popc(e.mhi));
+    return e;
+}
+
+// The tile of the local-th kept tile of a pair.
+__device__ __forceinline__ uint32_t emit_tile(const EmitPair &e, uint32_t local)
+{
+    const uint32_t slot = (e.mlo & e.mhi) == 0xffffffffu ? local : select_bit64(e.mlo, e.mhi, local);
+    const uint32_t dy = slot / e.wdt, dx = slot - dy * e.wdt;
+    return e.corner + dy * e.tx_row + dx;
+}
+
 __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, const uint32_t *n_vis,
                                                    const uint32_t *order, const uint32_t *rx, const uint32_t *ry,
                                                    const uint2 *keep, const uint32_t *offsets, uint32_t *keys,
@@ -307,10 +361,9 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
     const int64_t nb = (int64_t)vb.B * N;
     const int64_t n = (int64_t)*n_vis < nb ? (int64_t)*n_vis : nb;   // pairs in depth order
     const int lane = threadIdx.x & 31;
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t j0 = j - lane;                 // the warp's first pair
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long F = *total;
-    if (j == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         status->needed = F;
         status->counters[0] = F;
         status->counters[1] = 0ull;
@@ -324,65 +377,63 @@ __global__ void __launch_bounds__(256) k_emit_keys(ViewBatch vb, int64_t N, cons
             *count_out = (uint32_t)F;
         }
     }
-    if (F > capacity || j0 >= n) return;         // uniform over the warp
-    uint32_t start = 0u, area = 0u, g = 0u, corner = 0u, wdt = 1u, tx_row = 0u, mlo = 0xffffffffu,
-             mhi = 0xffffffffu;
-    if (j < n) {
-        start = offsets[j];
-        const int64_t i = (int64_t)order[j];
-        const uint2 rc = make_uint2(rx[j], ry[j]);
-        area = rect_area(rc);
-        if (area && i < nb) {                    // i >= B * N only after a failed (timed-out) pair sort
-            const int v = (int)(i / N);
-            g = (uint32_t)(i - (int64_t)v * N);
-            const uint32_t x0 = rc.x & 0xffffu;
-            wdt = (rc.x >> 16) - x0 + 1u;
-            tx_row = (uint32_t)vb.v[v].TX;
-            corner = vb.v[v].tile_base + (rc.y & 0xffffu) * tx_row + x0;   // tile (x0, y0)
-            if (cull_alpha > 0.f && area <= TILE_CULL_MAX_AREA) {
-                const uint2 k = keep[j];
-                mlo = k.x;
-                mhi = k.y;
-            }
-        } else {
-            area = 0u;
+    const uint64_t f_begin = warp * EMIT_SLOTS;
+    if (F > capacity || f_begin >= F || n <= 0) return;   // uniform over the warp
+    const uint32_t f_end = (uint32_t)(f_begin + EMIT_SLOTS < F ? f_begin + EMIT_SLOTS : F);
+    const uint32_t fb = (uint32_t)f_begin, F32 = (uint32_t)F;
+    // the pair holding slot fb: the last p < n with offsets[p] <= fb (offsets[0] = 0)
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t q = lo + lane * step;
+        const uint32_t b = __ballot_sync(0xffffffffu, q < hi && offsets[q] <= fb);
+        lo += (int64_t)(31 - __clz(b)) * step;   // lane 0 (q = lo) always qualifies
+        hi = lo + step < hi ? lo + step : hi;
+    }
+    {
+        const uint32_t b = __ballot_sync(0xffffffffu, lo + lane < hi && offsets[lo + lane] <= fb);
+        lo += 31 - __clz(b);
+    }
+    int64_t pw = lo;
+    EmitPair e = emit_pair(vb, N, nb, n, pw + lane, order, rx, ry, keep, offsets, F32, cull_alpha);
+    for (uint32_t fr = fb; fr < f_end; fr += 32) {
+        const uint32_t last = fr + 31 < f_end ? fr + 31 : f_end - 1;
+        const uint32_t wend = __shfl_sync(0xffffffffu, e.start + e.count, 31);
+        if (last >= wend) {                      // move the window to the pair holding fr
+            const uint32_t b = __ballot_sync(0xffffffffu, e.start <= fr);
+            pw += 31 - __clz(b);
+            e = emit_pair(vb, N, nb, n, pw + lane, order, rx, ry, keep, offsets, F32, cull_alpha);
         }
-    }
-    // the lanes' kept tiles laid end to end: a whole rectangle (mask all ones),
-    // or the set bits of a culled one's mask (bits past its area are clear)
-    const bool whole = (mlo & mhi) == 0xffffffffu;
-    const uint32_t kept = whole ? area : (uint32_t)(__popc(mlo) + __popc(mhi));
-    uint32_t incl = kept;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const uint32_t rel = incl - kept;            // lanes past n: rel = span, never matched
-    const uint32_t span = __shfl_sync(0xffffffffu, incl, 31);
-    const uint32_t base = __shfl_sync(0xffffffffu, start, 0);
-    for (uint32_t r0 = 0; r0 < span; r0 += 32) {
-        const uint32_t f = r0 + lane;
-        int L = 0;                               // last lane with rel <= f
+        const uint32_t f = fr + lane;
+        int L = 0;                               // last lane of the window with start <= f
 #pragma unroll
         for (int step = 16; step >= 1; step >>= 1) {
-            const uint32_t s = __shfl_sync(0xffffffffu, rel, L + step);
+            const uint32_t s = __shfl_sync(0xffffffffu, e.start, L + step);
             if (s <= f) L += step;
         }
-        const uint32_t lrel = __shfl_sync(0xffffffffu, rel, L);
-        const uint32_t lw = __shfl_sync(0xffffffffu, wdt, L);
-        const uint32_t ltx = __shfl_sync(0xffffffffu, tx_row, L);
-        const uint32_t lc = __shfl_sync(0xffffffffu, corner, L);
-        const uint32_t lg = __shfl_sync(0xffffffffu, g, L);
-        const uint32_t llo = __shfl_sync(0xffffffffu, mlo, L), lhi = __shfl_sync(0xffffffffu, mhi, L);
-        const uint32_t local = f - lrel;         // the pair's local-th kept tile
-        const uint32_t slot = (llo & lhi) == 0xffffffffu ? local : select_bit64(llo, lhi, local);
-        const uint32_t dy = slot / lw, dx = slot - dy * lw;
-        const uint64_t o = (uint64_t)base + f;
-        if (f < span && o < F) {                 // the kept tiles match the counts by construction
-            keys[o] = lc + dy * ltx + dx;
-            vals[o] = lg;
+        EmitPair h;
+        h.start = __shfl_sync(0xffffffffu, e.start, L);
+        h.count = __shfl_sync(0xffffffffu, e.count, L);
+        h.corner = __shfl_sync(0xffffffffu, e.corner, L);
+        h.wdt = __shfl_sync(0xffffffffu, e.wdt, L);
+        h.tx_row = __shfl_sync(0xffffffffu, e.tx_row, L);
+        h.g = __shfl_sync(0xffffffffu, e.g, L);
+        h.mlo = __shfl_sync(0xffffffffu, e.mlo, L);
+        h.mhi = __shfl_sync(0xffffffffu, e.mhi, L);
+        if (f >= f_end) continue;
+        if (f - h.start >= h.count) {
+            // past the window (pairs without fragments, only after a failed pair
+            // sort): the last pair with offsets <= f, found directly
+            int64_t a = pw, c = n;
+            while (c - a > 1) {
+                const int64_t m = (a + c) >> 1;
+                if (offsets[m] <= f) a = m; else c = m;
+            }
+            h = emit_pair(vb, N, nb, n, a, order, rx, ry, keep, offsets, F32, cull_alpha);
+            if (f - h.start >= h.count) continue;
         }
+        keys[f] = emit_tile(h, f - h.start);
+        vals[f] = h.g;
     }
 }
 
@@ -889,8 +940,9 @@ void launch_emit_keys(const ViewBatch &vb, int64_t N, const uint32_t *n_vis, con
                       uint32_t *keys, uint32_t *vals, uint64_t capacity, const unsigned long long *total,
                       DevStatus *status, uint32_t *count_out, float cull_alpha, cudaStream_t st)
 {
-    const int64_t n = (int64_t)vb.B * N;
-    const int64_t blocks = n > 0 ? (n + 255) / 256 : 1;
+    // one warp per EMIT_SLOTS output slots of the capacity (warps past F return at once)
+    const uint64_t warps = (capacity + EMIT_SLOTS - 1) / EMIT_SLOTS;
+    const uint64_t blocks = warps > 0 ? (warps + 7) / 8 : 1;
     k_emit_keys<<<(unsigned)blocks, 256, 0, st>>>(vb, N, n_vis, order, rx, ry, keep, offsets, keys, vals, capacity,
                                                  total, status, count_out, cull_alpha);
     count_launches(1);
