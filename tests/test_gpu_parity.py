@@ -89,6 +89,36 @@ def test_bin_bit_exact(eng, oracle, tile, Bv, W, H):
     assert tot == F and int(bins.count.item()) == F
 
 
+def test_bin_bit_exact_with_huge_nearest_footprints(eng, oracle):
+    """The 64 nearest Gaussians of each view cover the whole image (1,200
+    tiles each) and come first in the depth order, so a few pairs hold most of
+    the fragments: the emission splits them across warps by output slot and
+    the result must still be the oracle's lists bit for bit."""
+    W, H, tile, Bv = 640, 480, 16, 2
+    cams = [synth.test_camera(W, H)] * Bv
+    pjs = []
+    for s in range(Bv):
+        pj = synth.synthetic_proj(3000, W, H, seed=90 + s, ties=100)
+        near = np.argsort(pj["rgb_d"][:, 3], kind="stable")[:64]
+        pj["radius"][near] = 800
+        pjs.append(pj)
+    ctx = eng.Context(tile=tile)
+    bins = ctx.bin(upload_proj(eng, pjs), cams)
+    F = bins.F
+    keys = bins.keys[:F].cpu().numpy().view(np.uint64)
+    vals = bins.vals[:F].cpu().numpy().view(np.uint32)
+    tpv = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
+    tot = 0
+    for v in range(Bv):
+        toff, gidx = oracle_lists(oracle, pjs[v], W, H, tile)
+        lo = tot
+        assert np.array_equal(vals[lo:lo + len(gidx)], gidx.astype(np.uint32))
+        tile_ids = np.repeat(np.arange(tpv, dtype=np.uint64) + v * tpv, np.diff(toff))
+        assert np.array_equal(keys[lo:lo + len(gidx)] >> np.uint64(32), tile_ids)
+        tot += len(gidx)
+    assert tot == F and F > 2 * 64 * tpv
+
+
 def test_bin_capacity_overflow_reports_needed(eng, oracle):
     from paper_2406_18533_gb300 import binding as b
     W, H = 64, 48
