@@ -339,6 +339,18 @@ gs_status gs_preprocess_bwd(gs_ctx *ctx, const gs_scene *scene, const gs_camera 
                             const gs_proj *proj, const gs_proj_grad *dproj, gs_scene *grad, void *stream);
 
 /*
+ * gs_preprocess_bwd with an explicit factor: grad = scale * (sum over the B
+ * views of the per-view chain rule).  scale = 1/B is gs_preprocess_bwd (the
+ * paper's batch mean, Sec. 4); scale = 1 gives the sum, the gradient of a
+ * loss that adds the views' losses (what an autograd engine expects from a
+ * function of B images).  scale must be finite and >= 0, else
+ * GS_ERR_INVALID_ARG.
+ */
+gs_status gs_preprocess_bwd_scaled(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cams, int32_t B,
+                                   const gs_proj *proj, const gs_proj_grad *dproj, gs_scene *grad, float scale,
+                                   void *stream);
+
+/*
  * Sec. 2.1 step 3: loss = (1 - l) mean|I - I*| + l (1 - mean SSIM(I, I*)),
  * SSIM with an 11x11 Gaussian window (sigma 1.5), zero padding, per view.
  * img, target, d_img: [B][3][H][W]; loss_out: [B] float (device).  d_img is

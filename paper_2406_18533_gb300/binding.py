@@ -87,6 +87,8 @@ SIGNATURES = {
     "gs_render_fwd": [_vp, P(gs_proj), P(gs_bins), P(gs_camera), _i32, _vp, _vp, _vp, _vp],
     "gs_render_bwd": [_vp, P(gs_proj), P(gs_bins), P(gs_camera), _i32, _vp, _vp, _vp, P(gs_proj_grad), _vp],
     "gs_preprocess_bwd": [_vp, P(gs_scene), P(gs_camera), _i32, P(gs_proj), P(gs_proj_grad), P(gs_scene), _vp],
+    "gs_preprocess_bwd_scaled": [_vp, P(gs_scene), P(gs_camera), _i32, P(gs_proj), P(gs_proj_grad), P(gs_scene),
+                                 ctypes.c_float, _vp],
     "gs_loss": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
     "gs_spatial_order": [_vp, P(gs_scene), _vp, _vp],
     "gs_division_points": [_vp, _vp, _i64, _i32, _vp, _vp],

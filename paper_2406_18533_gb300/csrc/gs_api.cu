@@ -801,6 +801,16 @@ gs_status gs_preprocess_bwd(gs_ctx *c, const gs_scene *scene, const gs_camera *c
                             const gs_proj_grad *dproj, gs_scene *grad, void *stream)
 {
     if (!c) return GS_ERR_INVALID_ARG;
+    if (B < 1) return fail(c, GS_ERR_INVALID_ARG, "B < 1");
+    return gs_preprocess_bwd_scaled(c, scene, cams, B, proj, dproj, grad, 1.f / (float)B, stream);
+}
+
+gs_status gs_preprocess_bwd_scaled(gs_ctx *c, const gs_scene *scene, const gs_camera *cams, int32_t B,
+                                   const gs_proj *proj, const gs_proj_grad *dproj, gs_scene *grad, float scale,
+                                   void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!(scale >= 0.f) || scale == INFINITY) return fail(c, GS_ERR_INVALID_ARG, "scale must be finite and >= 0");
     if (!scene_ok(scene) || !scene_ok(grad) || grad->N != scene->N)
         return fail(c, GS_ERR_INVALID_ARG, "bad scene or gradient planes");
     if (!proj || proj->B != B || proj->N != scene->N || !dproj) return fail(c, GS_ERR_INVALID_ARG, "bad gs_proj");
@@ -809,7 +819,8 @@ gs_status gs_preprocess_bwd(gs_ctx *c, const gs_scene *scene, const gs_camera *c
     if (r != GS_OK) return r;
     GradView gv{reinterpret_cast<float4 *>(dproj->d_xy_o), reinterpret_cast<float4 *>(dproj->d_conic),
                 reinterpret_cast<float4 *>(dproj->d_rgb)};
-    launch_preprocess_bwd(view_of(scene), vb, proj_of(proj), gv, true, mut_of(grad), nullptr, S(stream));
+    launch_preprocess_bwd(view_of(scene), vb, proj_of(proj), gv, true, mut_of(grad), nullptr, S(stream), nullptr,
+                          nullptr, nullptr, scale);
     return cuda_check(c, "gs_preprocess_bwd");
 }
 

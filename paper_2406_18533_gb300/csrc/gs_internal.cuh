@@ -120,9 +120,11 @@ void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjVi
 // the Gaussian is visible, |dL_v/d(u, v)| is added to dacc[g] and 1 to dcnt[g],
 // unless status holds GS_ERR_CAPACITY or GS_ERR_TIMEOUT (status is read only
 // with dacc).
+// scale (negative: 1/B, the batch mean) multiplies the sum over the views.
 void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
                            bool grads_ready, const SceneMut &out, uint8_t *vis, cudaStream_t st,
-                           float *dacc = nullptr, uint32_t *dcnt = nullptr, const DevStatus *status = nullptr);
+                           float *dacc = nullptr, uint32_t *dcnt = nullptr, const DevStatus *status = nullptr,
+                           float scale = -1.f);
 // In place: the moments of n entries -> gradients (moments_to_grads).
 void launch_moments_to_grads(const ProjView &p, int64_t n, const GradView &g, cudaStream_t st);
 

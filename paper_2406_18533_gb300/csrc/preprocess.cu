@@ -332,14 +332,15 @@ __global__ void __launch_bounds__(256) k_moments_to_grads(ProjView p, int64_t n,
 // 5 and 6 blocks spill 224 and 360 bytes.
 __global__ void __launch_bounds__(128, 4) k_preprocess_bwd(SceneView s, ViewBatch vb, ProjView p, GradView gv,
                                                         bool grads_ready, SceneMut out, uint8_t *vis,
-                                                        float *dacc, uint32_t *dcnt, const DevStatus *status)
+                                                        float *dacc, uint32_t *dcnt, const DevStatus *status,
+                                                        float scale)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= s.N) return;
     const int nk = (s.deg + 1) * (s.deg + 1);
     bool any = false;
     for (int v = 0; v < vb.B; ++v) any |= p.radius[(int64_t)v * s.N + g] > 0;
-    const float invB = 1.f / (float)vb.B;
+    const float invB = scale;                    // 1/B: the batch mean (Sec. 4); 1: the sum over views
     if (vis) {                                   // visible-only Adam: unseen rows stay unwritten
         vis[g] = any ? 1 : 0;
         if (!any) return;
@@ -567,12 +568,14 @@ void launch_preprocess_fwd(const SceneView &s, const ViewBatch &vb, const ProjVi
 
 void launch_preprocess_bwd(const SceneView &s, const ViewBatch &vb, const ProjView &p, const GradView &g,
                            bool grads_ready, const SceneMut &out, uint8_t *vis, cudaStream_t st, float *dacc,
-                           uint32_t *dcnt, const DevStatus *status)
+                           uint32_t *dcnt, const DevStatus *status, float scale)
 {
     if (s.N == 0) return;
     const int threads = 128;
     const int64_t blocks = (s.N + threads - 1) / threads;
-    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, g, grads_ready, out, vis, dacc, dcnt, status);
+    if (scale < 0.f) scale = 1.f / (float)vb.B;
+    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, st>>>(s, vb, p, g, grads_ready, out, vis, dacc, dcnt, status,
+                                                           scale);
     count_launches(1);
 }
 

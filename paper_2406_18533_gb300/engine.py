@@ -211,11 +211,19 @@ class Context:
                 _ptr(nc), _ptr(dimg), ctypes.byref(gs), _stream())
         return g
 
-    def preprocess_bwd(self, scene: DeviceScene, cams, proj: Proj, pg: ProjGrad, out: DeviceScene | None = None):
+    def preprocess_bwd(self, scene: DeviceScene, cams, proj: Proj, pg: ProjGrad, out: DeviceScene | None = None,
+                       scale: float | None = None):
+        """Gradients of the parameters; the views' contributions are averaged
+        (the paper's batch gradient) unless ``scale`` is given, which then
+        multiplies their sum (scale=1: the sum)."""
         out = out or scene.zeros_like()
         s, p, g, o = scene.struct(), proj.struct(), pg.struct(), out.struct()
-        self._c("gs_preprocess_bwd", self.h, ctypes.byref(s), B.camera_array(cams), len(cams), ctypes.byref(p),
-                ctypes.byref(g), ctypes.byref(o), _stream())
+        if scale is None:
+            self._c("gs_preprocess_bwd", self.h, ctypes.byref(s), B.camera_array(cams), len(cams), ctypes.byref(p),
+                    ctypes.byref(g), ctypes.byref(o), _stream())
+        else:
+            self._c("gs_preprocess_bwd_scaled", self.h, ctypes.byref(s), B.camera_array(cams), len(cams),
+                    ctypes.byref(p), ctypes.byref(g), ctypes.byref(o), float(scale), _stream())
         return out
 
     def loss(self, img: torch.Tensor, target: torch.Tensor):
@@ -443,17 +451,21 @@ def train_from_host(ctx: Context, p: DeviceScene, g: DeviceScene, m: DeviceScene
 
 
 class RasterizeGaussians(torch.autograd.Function):
-    """image[B,3,H,W] = render(params) with a hand-written backward.
+    """image[B,3,H,W] = render(params) with a hand-written backward, for B
+    views of one size.
 
     Forward: gs_preprocess -> gs_bin -> gs_render_fwd.  Saved for backward:
     the per-(view, Gaussian) screen-space state, the sorted fragments and the
     per-pixel T_final / n_contrib; no per-fragment state.  Backward:
-    gs_render_bwd -> gs_preprocess_bwd (mean over the views)."""
+    gs_render_bwd -> gs_preprocess_bwd_scaled with scale 1, so the parameter
+    gradient is the sum of the views' contributions (the autograd contract
+    for a function with B outputs stacked); Context.train_step applies the
+    paper's batch mean instead."""
 
     @staticmethod
     def forward(ctx, mo, ls, q, sh, gsctx: Context, cams, sh_degree: int):
-        if len(cams) != 1:
-            raise ValueError("the autograd path renders one view; batches go through Context.train_step")
+        if len(cams) < 1 or any((c.W, c.H) != (cams[0].W, cams[0].H) for c in cams):
+            raise ValueError("the autograd path renders one or more views of one size")
         scene = DeviceScene(mo.detach().contiguous(), ls.detach().contiguous(), q.detach().contiguous(),
                             sh.detach().contiguous(), sh_degree)
         proj = gsctx.preprocess(scene, cams)
@@ -467,7 +479,7 @@ class RasterizeGaussians(torch.autograd.Function):
     def backward(ctx, dimg):
         T, nc = ctx.saved_tensors
         pg = ctx.gsctx.render_bwd(ctx.proj, ctx.bins, ctx.cams, T, nc, dimg.contiguous())
-        g = ctx.gsctx.preprocess_bwd(ctx.scene, ctx.cams, ctx.proj, pg)
+        g = ctx.gsctx.preprocess_bwd(ctx.scene, ctx.cams, ctx.proj, pg, scale=1.0)
         return g.mo, g.ls, g.q, g.sh, None, None, None
 
 

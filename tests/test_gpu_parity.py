@@ -463,6 +463,38 @@ def test_end_to_end_c0_autograd(eng, oracle):
         assert rel_l2(grad[:, s], ref[:, s]) < GRAD_TOL, name
 
 
+def test_autograd_two_views_sum_of_view_gradients(eng, oracle):
+    """The autograd Function over two views of one size: images per view
+    against the oracle, and the parameter gradient equal to the sum of the two
+    views' oracle gradients (autograd's contract for stacked outputs; the
+    training step takes the paper's batch mean instead)."""
+    sc, cams, dimg = synth.workload_c0(N=4000)
+    cam0 = cams[0]
+    cam1 = synth.camera_look_at((0.6, -0.3, 3.6), (0.05, 0.0, 0.0), (0, 1, 0), cam0.W, cam0.H, 55.0)
+    views = [cam0, cam1]
+    ctx = eng.Context()
+    ds = eng.DeviceScene.from_host(sc)
+    params = [t.clone().requires_grad_(True) for t in (ds.mo, ds.ls, ds.q, ds.sh)]
+    img = eng.rasterize(params, ctx, views)
+    assert img.shape == (2, 3, cam0.H, cam0.W)
+    rng = np.random.default_rng(3)
+    ds_up, ref = [], np.zeros((sc.N, 60))
+    for v, cam in enumerate(views):
+        fw = oracle.render_admissible(sc, cam)
+        flag = _check_image(fw, img.detach()[v].cpu().numpy(), f"view {v}")
+        d = rng.standard_normal((3, cam.H, cam.W)).astype(np.float32)
+        d[:, flag] = 0
+        ds_up.append(d)
+        ref += oracle.grad_view(sc, cam, d)[0]
+    img.backward(torch.from_numpy(np.stack(ds_up)).cuda())
+    grad = np.concatenate([params[0].grad.cpu().numpy(), params[1].grad.cpu().numpy(), params[2].grad.cpu().numpy(),
+                           params[3].grad.permute(1, 0, 2).reshape(sc.N, 48).cpu().numpy()], 1)
+    groups = dict(mean=slice(0, 3), opacity=slice(3, 4), scale=slice(4, 7), quat=slice(8, 12),
+                  sh_dc=slice(12, 15), sh_rest=slice(15, 60))
+    for name, s in groups.items():
+        assert rel_l2(grad[:, s], ref[:, s]) < GRAD_TOL, name
+
+
 @pytest.mark.parametrize("N", [0, 1, 7])
 def test_degenerate_scenes(eng, oracle, N):
     sc = synth.tiny_scene(max(N, 1), seed=N, spread=0.2)
