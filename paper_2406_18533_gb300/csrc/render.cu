@@ -1021,11 +1021,12 @@ int sm_count()
 bool tile_order_pays(uint32_t total_tiles)
 {
     // measured on GB300: 1M Gaussians at 1080p (8,160 tiles, 54 per SM) gains
-    // 13 % per training step; 130,560 tiles (859 per SM) lose 2 % (neighbouring
-    // tiles no longer run together, so their shared Gaussians leave L2) and
-    // 256 tiles lose to the ordering's own launches
+    // 13 % per training step, 16 views at 1080p (130,560 tiles, 859 per SM)
+    // 1.1 % with the per-row-vote blending kernels (the long lists of a dense
+    // region no longer start last), and 256 tiles lose to the ordering's own
+    // launches; above 2,000 tiles per SM nothing was measured
     const uint32_t sms = (uint32_t)sm_count();
-    return total_tiles >= 4u * sms && total_tiles <= 112u * sms;
+    return total_tiles >= 4u * sms && total_tiles <= 2000u * sms;
 }
 
 void launch_tile_order(const uint2 *ranges, uint32_t n, uint32_t *order, uint32_t *buckets, cudaStream_t st,
