@@ -555,20 +555,20 @@ def test_batched_render_equals_single_view(eng):
 
 
 def test_tile_launch_order_leaves_results_unchanged(eng):
-    """One 1080p view (8,160 tiles) is blended in heaviest-list-first launch
-    order; three copies of it in one batch (24,480 tiles) in index order.
-    The images are bit-identical (every pixel is computed the same way
-    whatever the launch order) and each copy's 2D gradients equal the single
-    view's up to the order of the atomic adds."""
+    """One 4K view (32,400 tiles) is blended in heaviest-list-first launch
+    order; ten copies of it in one batch (324,000 tiles, above 2,000 per SM)
+    in index order.  The images are bit-identical (every pixel is computed
+    the same way whatever the launch order) and each copy's 2D gradients
+    equal the single view's up to the order of the atomic adds."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    if not (4 * sms <= 8160 <= 112 * sms < 3 * 8160):
+    if not (4 * sms <= 32400 <= 2000 * sms < 10 * 32400):
         pytest.skip("launch-order thresholds do not split these sizes on this GPU")
     sc, rng = synth.aerial_scene(200_000, n_clusters=32, seed=9)
-    cam = synth.ring_cameras(rng, 1, (60.0, 60.0))[0]
+    cam = synth.ring_cameras(rng, 1, (60.0, 60.0), W=3840, H=2160)[0]
     ctx = eng.Context()
     P = eng.DeviceScene.from_host(sc)
     out = {}
-    for cams in ([cam], [cam, cam, cam]):
+    for cams in ([cam], [cam] * 10):
         proj = ctx.preprocess(P, cams)
         bins = ctx.bin(proj, cams)
         img, T, nc = ctx.render_fwd(proj, bins, cams)
@@ -577,11 +577,11 @@ def test_tile_launch_order_leaves_results_unchanged(eng):
         torch.cuda.synchronize()
         out[len(cams)] = (img, g)
     img1, g1 = out[1]
-    img3, g3 = out[3]
-    for b in range(3):
-        assert torch.equal(img3[b], img1[0]), b
+    img10, g10 = out[10]
+    for b in range(10):
+        assert torch.equal(img10[b], img1[0]), b
         for name in ("d_xy_o", "d_conic", "d_rgb"):
-            a, r = getattr(g3, name)[b], getattr(g1, name)[0]
+            a, r = getattr(g10, name)[b], getattr(g1, name)[0]
             assert rel_l2(a.cpu().numpy(), r.cpu().numpy()) < 1e-5, (b, name)
 
 
