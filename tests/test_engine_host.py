@@ -38,3 +38,15 @@ def test_total_tiles_of_a_mixed_batch():
     cams = [synth.test_camera(W=1920, H=1080), synth.test_camera(W=97, H=61)]
     assert engine.total_tiles(cams, 16) == 120 * 68 + 7 * 4
     assert engine.total_tiles(cams, 32) == 60 * 34 + 4 * 2
+
+
+def test_autograd_function_refuses_views_of_different_sizes():
+    """The autograd Function renders views of one size per call (one image
+    tensor [B, 3, H, W]); a mixed batch is refused before any library call."""
+    ds = engine.DeviceScene.from_host(synth.tiny_scene(5, seed=1), device="cpu")
+    params = [t.clone().requires_grad_(True) for t in (ds.mo, ds.ls, ds.q, ds.sh)]
+    cams = [synth.test_camera(W=64, H=48), synth.test_camera(W=32, H=48)]
+    with pytest.raises(ValueError, match="one size"):
+        engine.rasterize(params, None, cams)
+    with pytest.raises(ValueError, match="one size"):
+        engine.rasterize(params, None, [])
