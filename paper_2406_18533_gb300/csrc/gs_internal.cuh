@@ -40,7 +40,7 @@ struct BlendParams {
     float alpha_min, alpha_max, T_min;
     float bg[3];
     uint32_t list_cap;   // entries in the fragment list: a tile range beyond it is refused
-    int32_t count_work;  // nonzero: the backward counts its walked and blended pairs (counters[4], [2])
+    int32_t count_work;  // nonzero: the blending kernels count their work (counters[1], [2], [4], [5])
 };
 
 struct SceneView {     // read-only parameter planes
@@ -200,13 +200,19 @@ __device__ __forceinline__ bool ellipse_box_hits(const float4 &co, float u, floa
 // rectangle); larger ones keep every tile.
 constexpr uint32_t TILE_CULL_MAX_AREA = 64;
 
+// sqrt(x) for x >= 0 from the approximate reciprocal square root (0 at 0).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    return x > 0.f ? x * rsqrtf(x) : 0.f;
+}
+
 // Tiles of a footprint rectangle culled against the alpha >= cull_alpha
 // ellipse (the transformation kernel does it per pair in a training step or
-// a render).  With f(d) = a dx^2 +
-// 2 b dx dy + c dy^2 the ellipse is f <= L (L = the widened threshold of
-// ellipse_terms).  Per tile row, the pixel-centre rows of the row give a band
-// dy in [dy0, dy1]; the ellipse meets the band where |dy| <= Y = sqrt(a L /
-// det), and there its x-range is the interval between
+// a render).  With f(d) = a dx^2 + 2 b dx dy + c dy^2 the ellipse is f <= L
+// (L = the widened threshold of ellipse_terms).  Per tile row, the
+// pixel-centre rows of the row give a band dy in [dy0, dy1]; the ellipse
+// meets the band where |dy| <= Y = sqrt(a L / det), and there its x-range is
+// the interval between
 //   xl(dy) = (-b dy - sqrt(a L - det dy^2)) / a  and
 //   xr(dy) = (-b dy + sqrt(a L - det dy^2)) / a.
 // xr is concave in dy with its maximum at dy_r = -b sqrt(L / (c det)) (the
@@ -215,17 +221,11 @@ constexpr uint32_t TILE_CULL_MAX_AREA = 64;
 // band.  A tile of the row is kept when its pixel-centre columns meet that
 // range.  This is the box test of ellipse_box_hits done once per tile row
 // instead of once per tile; the band limits, the range and Y are widened by
-// 1e-3 relative plus 1e-2 pixel, above the rounding of the square roots and
-// divisions (the threshold L already carries ellipse_terms' margin), so a
-// tile is never dropped where the per-pixel test could blend.
+// 1e-3 relative plus 1e-2 pixel, above the rounding of the approximate square
+// roots and reciprocals (the threshold L already carries ellipse_terms'
+// margin), so a tile is never dropped where the per-pixel test could blend.
 // Returns the kept-tile bits (row-major in the rectangle [x0, x1] x [y0, y1]
 // of tiles of edge T; at most TILE_CULL_MAX_AREA tiles).
-// sqrt(x) for x >= 0 from the approximate reciprocal square root (0 at 0).
-__device__ __forceinline__ float sqrt_approx(float x)
-{
-    return x > 0.f ? x * rsqrtf(x) : 0.f;
-}
-
 __device__ __forceinline__ uint64_t row_interval_mask(const float4 &co, const float4 &te, float u, float v,
                                                       uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1, float T)
 {
