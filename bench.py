@@ -450,8 +450,7 @@ def run_ours(args, rank, world, local_rank):
     binding.call("gs_trace_read", ctx.h, buf, ctypes.byref(nst), ctx=ctx.h)
     binding.call("gs_trace_enable", ctx.h, 0, ctx=ctx.h)
     arr = np.frombuffer(buf, dtype=np.float32).reshape(nstep_tr, binding.GS_TRACE_STAGES)[:nst.value]
-    # median over the traced steps: a step whose host launches fell behind
-    # the GPU shows the gap in one stage, and the median leaves it out
+    # median over the traced steps, which one disturbed step does not move
     stage_ms = {s: float(np.median(arr[:, i])) for i, s in enumerate(binding.TRACE_STAGES)}
     # the backward's work counters (walked and blended pairs) from one more
     # step with counting on; the timed and traced steps ran without it
