@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 4
+#define GS_ABI_VERSION 5   /* 5: gs_count_work, gs_preprocess_bwd_scaled; work counters on request */
 #define GS_MAX_VIEWS 32   /* views per call (training batch or render batch) */
 #define GS_MAX_FRAGMENTS 1073741823ull  /* 2^30 - 1: largest fragment capacity of one call */
 

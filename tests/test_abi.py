@@ -37,7 +37,7 @@ def test_binding_covers_every_entry_point(libgs):
 
 def test_abi_version_and_defaults(libgs):
     from paper_2406_18533_gb300 import binding
-    assert libgs.gs_abi_version() == 4
+    assert libgs.gs_abi_version() == 5
     hp = binding.default_hparams()
     assert hp.tile == 16 and hp.smem_batch == 64 and hp.px_per_thread == 1
     assert abs(hp.alpha_min - 1 / 255) < 1e-9 and abs(hp.alpha_max - 0.99) < 1e-7 and abs(hp.T_min - 1e-4) < 1e-10
